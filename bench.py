@@ -1,0 +1,409 @@
+"""Throughput bench of the Fireflies hot path on GB300.
+
+One bench step = one whole run of the 4M-particle Lorenz workload: re-seed both
+particle groups (3,145,728 forward, 1,048,576 backward in time), then 100 frames
+of 200 RK4 steps (dt = 0.001) each followed by the x-z projection and count splat
+into a cleared 1920x1080 image.  Metric: particle-RK4-steps per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own shard (the full workload with rank-distinct
+seeds: weak scaling, no data-path collective); value = particles of all ranks x
+steps / max-over-ranks time.  ``--impl reference`` times the FP64 CPU oracle on
+a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1505_00344_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle-RK4-steps/sec"
+UNIT = "particle-steps/s"
+# FP32 instructions / flops of one RK4 step of one Lorenz particle, counted from Eq. 3-5 with
+# FMA = 2 flops: RHS 6 instructions (8 flops) x 4 stages, 9 stage updates (18 flops), weighted
+# sum + update 12 instructions (21 flops).
+LORENZ_RK4_FLOPS = 71
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="lorenz_4M")
+    ap.add_argument("--ppt", type=int, default=1)
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--kahan", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def total_particles(w):
+    return sum(g["count"] for g in w["groups"])
+
+
+def total_steps(w):
+    return w["steps_per_frame"] * w["frames"]
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index, enabled=True):
+        self.proc = None
+        self.device_index = device_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        if not enabled:
+            return
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def traffic_from_profile(kernel_src_hash):
+    """Per-launch DRAM bytes of the integrator from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "integrate_lorenz_4M_ncu.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_src_hash:
+        return None
+    return float(m.group(1))
+
+
+def kernel_source_hash():
+    path = os.path.join(ROOT, "paper_1505_00344_gb300", "csrc", "ff_device.cuh")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1505_00344_gb300 as ff
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    w = W.shard(W.workload(args.workload), rank, world)
+    P = total_particles(w)
+    view = ff.make_view(**w["view"])
+    H, Wd = w["view"]["height"], w["view"]["width"]
+    sysobj = ff.System.from_workload(w, kahan=args.kahan, stream=stream)
+    sysobj.set_launch(args.ppt, args.block, args.blocks_per_sm, 0)
+    image = torch.zeros((H, Wd), dtype=torch.int32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > 129 MB L2
+    every = w.get("splat_every_frame", False)
+    schedule = {int(k): v for k, v in w.get("schedule", {}).items()}
+    base_params = list(w["params"])
+
+    def job(events=None):
+        """One whole workload run; returns the number of our kernel launches enqueued."""
+        sysobj.reset()
+        sysobj.set_params(base_params)
+        launches = len(w["groups"])
+        for f in range(w["frames"]):
+            if f in schedule:
+                sysobj.set_params(schedule[f])
+            if events is not None:
+                events.append(("int0", torch.cuda.Event(enable_timing=True)))
+                events[-1][1].record()
+            sysobj.step(w["steps_per_frame"], w["dt"])
+            launches += 1
+            if events is not None:
+                events.append(("int1", torch.cuda.Event(enable_timing=True)))
+                events[-1][1].record()
+            if every or f == w["frames"] - 1:
+                sysobj.project_splat(view, image)
+                launches += 1
+        return launches
+
+    for _ in range(args.warmup):
+        job()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local, enabled=not args.no_clocks)
+    step_ms, int_ms = [], []
+    launches = 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()  # evict the state and image from L2 between timed steps
+        ev = []
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        launches += job(ev)
+        s1.record()
+        torch.cuda.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        for (_, a), (_, b) in zip(ev[0::2], ev[1::2]):
+            int_ms.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    steps_per_job = total_steps(w)
+    value = world * P * steps_per_job / (ms_per_step / 1e3)
+
+    # roofline of the integrator (dominant kernel)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = measured_peaks()
+    max_mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    avg_int_ms = statistics.mean(int_ms)
+    n_work = (P + 3) // 4 * 4
+    flops_per_launch = LORENZ_RK4_FLOPS * n_work * w["steps_per_frame"] if w["rhs"] == "lorenz" else None
+    roof = None
+    if flops_per_launch:
+        achieved = flops_per_launch / (avg_int_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
+                "frac": round(achieved / peak_tflops, 4),
+                "traffic": traffic_from_profile(kernel_source_hash()),
+                "kernel": "integrate_kernel<Lorenz,RK4>",
+                "peak_basis": f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
+                "algorithmic_bytes_per_launch": 24 * n_work,
+                "avg_launch_ms": round(avg_int_ms, 4)}
+        if clk:
+            roof["frac_at_sampled_clock"] = round(achieved / (sms * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12), 4)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "particles_per_gpu": P, "groups": [
+            {"count": g["count"], "direction": g["direction"]} for g in w["groups"]],
+            "rk4_steps_per_job": steps_per_job, "frames": w["frames"], "steps_per_frame": w["steps_per_frame"],
+            "dt": w["dt"], "image": f"{Wd}x{H}", "kahan": bool(args.kahan),
+            "l2": "flushed (256 MB write) before every timed step", "parallelism": "dp%d-weak-shards" % world,
+            "launch": {"particles_per_thread": args.ppt, "block": args.block, "blocks_per_sm": args.blocks_per_sm}},
+        "frames_per_s": w["frames"] / (ms_per_step / 1e3),
+        "gpu_launches": launches,
+        "wall_s_timed_region": wall,
+    }
+    if roof:
+        result["roofline"] = roof
+    if clk:
+        result["clocks"] = clk
+
+    if not args.no_e2e:
+        result["e2e"] = e2e_ours(args, sysobj, w, view, image, P, world, dev)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w)
+    sysobj.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return result
+
+
+def e2e_ours(args, sysobj, w, view, image, P, world, dev):
+    """Same metric through the public API with host buffers: each step uploads the initial state
+    from pinned host memory (ff_set_state) and reads the final image back to pinned host memory
+    (ff_project_splat with a host image)."""
+    import torch
+
+    dim = w["dim"]
+    H, Wd = w["view"]["height"], w["view"]["width"]
+    sysobj.reset()
+    x0 = torch.empty((dim, P), dtype=torch.float32, pin_memory=True)
+    sysobj.get_state(x0.numpy())
+    host_img = torch.zeros((H, Wd), dtype=torch.int32, pin_memory=True)
+    every = w.get("splat_every_frame", False)
+    schedule = {int(k): v for k, v in w.get("schedule", {}).items()}
+
+    def job():
+        sysobj.set_state(x0)  # upload the initial state (also clears the Kahan compensation)
+        sysobj.set_params(w["params"])
+        for f in range(w["frames"]):
+            if f in schedule:
+                sysobj.set_params(schedule[f])
+            sysobj.step(w["steps_per_frame"], w["dt"])
+            last = f == w["frames"] - 1
+            if last:
+                sysobj.project_splat(view, host_img.numpy())
+            elif every:
+                sysobj.project_splat(view, image)
+
+    job()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(max(1, min(args.steps, 5))):
+        t0 = time.perf_counter()
+        job()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    t = statistics.mean(times)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return {"value": world * P * total_steps(w) / t, "unit": UNIT, "h2d_bytes_per_step": 4 * dim * P,
+            "d2h_bytes_per_step": 4 * H * Wd, "steps": len(times)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+def oracle_sample_run(w, particles, steps, threads=None):
+    """FP64 oracle on a bounded sample: the first particles of each group (proportional),
+    `steps` RK4 steps, then the x-z splat. Returns (particle-steps, seconds, threads)."""
+    import oracle
+
+    ws = W.scaled(w, particles)
+    x0 = np.concatenate([oracle.seed_group(ws["dim"], g["lo"], g["hi"], g["seed"], count=g["count"])
+                         for g in ws["groups"]], axis=1)
+    h = np.concatenate([np.full(g["count"], g["direction"] * ws["dt"]) for g in ws["groups"]])
+    n = x0.shape[1]
+    rid = W.RHS_IDS[ws["rhs"]]
+    v = ws["view"]
+    t0 = time.perf_counter()
+    x, used = oracle.integrate_parallel(rid, x0, ws["params"], h, steps, threads=threads)
+    xf = x.astype(np.float32)
+    if v["ndim_view"] == 2 and max(v["axes"]) < ws["dim"]:
+        oracle.splat2d(xf[v["axes"][0]], xf[v["axes"][1]], v["lo"], v["hi"], v["width"], v["height"])
+    dt = time.perf_counter() - t0
+    return n * steps, dt, used
+
+
+def cpu_baseline(w):
+    threads = os.cpu_count() or 1
+    # a quick probe sizes the sample to about 15 s of total CPU work
+    work, t, _ = oracle_sample_run(w, 4096, 200, threads=1)
+    rate1 = work / t
+    steps = w["steps_per_frame"]
+    particles = int(min(4_194_304, max(threads * 4096, 15.0 * rate1 / steps)))
+    work, t, used = oracle_sample_run(w, particles, steps, threads=threads)
+    return {"value": work / t, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{particles} particles of {w['name']} (groups in proportion) x {steps} RK4 steps "
+                      f"+ x-z splat, FP64 oracle, {used} threads on disjoint particle ranges"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w = W.workload(args.workload)
+    threads = os.cpu_count() or 1
+    steps = w["steps_per_frame"]
+    particles = min(total_particles(w), 262_144)
+    for _ in range(args.warmup):
+        oracle_sample_run(w, particles // 8, steps, threads=threads)
+    times = []
+    work = 0
+    for _ in range(args.steps):
+        work, t, used = oracle_sample_run(w, particles, steps, threads=threads)
+        times.append(t)
+    value = work / statistics.mean(times)
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["name"], "sample_particles": particles,
+                                            "rk4_steps_per_step": steps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                             "sample": f"{particles} particles x {steps} RK4 steps + splat per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * ff.h -- C ABI of the GB300 Fireflies hot path.
+ *
+ * Fireflies (Merrison-Hort, arXiv 1505.00344) visualises an N-dimensional ODE
+ * by integrating millions of independent trajectories ("particles") with a
+ * constant-step fourth-order Runge-Kutta method and drawing each particle's
+ * current state as a point of light.  This library is that data-parallel path
+ * on one GPU: seed particle groups, step them forward or backward in time,
+ * change parameters between steps, project onto a 2D or 3D view and splat into
+ * a point-density image.  Every step runs in hand-written CUDA kernels for
+ * sm_103a.
+ *
+ * Conventions that hold for every entry point:
+ *   - Return value: FF_OK, or an error code with a message available from
+ *     ff_last_error() (per thread).  Arguments are checked on the host before
+ *     anything is enqueued; a rejected call changes nothing.
+ *   - Ownership: a system owns its particle state and group tables (device
+ *     memory allocated by ff_create_system).  Buffers passed in by the caller
+ *     (images, state copies, parameter vectors) stay owned by the caller and
+ *     are only borrowed for the duration of the call.
+ *   - Streams: all device work of a system is enqueued on the CUDA stream
+ *     given at creation (NULL = the legacy default stream).  Calls return after
+ *     enqueueing unless documented as synchronising.
+ *   - Device: a system is bound to the device that was current when it was
+ *     created; every call makes that device current for its own work and
+ *     restores the caller's device before returning.
+ *   - Threads: a system must not be used from two threads at once.
+ *   - Numerics: state is single precision (the paper's choice, Appendix A);
+ *     parameters are accepted in double and rounded to float for the kernels;
+ *     simulated time is accumulated in double on the host.
+ */
+#ifndef FF_H
+#define FF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ff_status {
+    FF_OK = 0,
+    FF_ERR_INVALID_ARG = 1,  /* a pointer, size, index or value is out of range */
+    FF_ERR_CUDA = 2,         /* a CUDA call or kernel launch failed */
+    FF_ERR_OOM = 3,          /* device or host allocation failed */
+    FF_ERR_STATE = 4,        /* the call is not allowed in the system's current state */
+    FF_ERR_UNSUPPORTED = 5,  /* valid request that this build does not implement */
+    FF_ERR_TIMEOUT = 6       /* a bounded device wait gave up */
+} ff_status;
+
+/* Right-hand sides f(x, p).  Parameter vectors (length n_params) in order:
+ *   FF_RHS_LINEAR        dim 1..8, dx/dt = A x, p = A row-major (dim*dim).
+ *   FF_RHS_HARMONIC      dim 2, (x, v): dx = v, dv = -w^2 x; p = [w].
+ *   FF_RHS_WILSON_COWAN  dim 2, paper Eq. 1-2 as an E-I pair:
+ *                        tauE dE = -E + S(wEE E - wEI I + P),
+ *                        tauI dI = -I + S(wIE E - wII I + Q),
+ *                        S(a) = 1 / (1 + exp(-gain (a - threshold)));
+ *                        p = [wEE, wEI, wIE, wII, P, Q, tauE, tauI, gain, threshold].
+ *   FF_RHS_LORENZ        dim 3, paper Eq. 3-5; p = [sigma, r, beta].
+ *   FF_RHS_HH3           dim 15, three Hodgkin-Huxley neurons (paper Eq. 6-11)
+ *                        with state (V, m, h, n, s) per neuron, rate functions
+ *                        of Hodgkin & Huxley 1952 with rest near -65 mV and
+ *                        all-to-all synaptic coupling sum_{j != i} s_j;
+ *                        p = [C, gNa, gK, gL, ENa, EK, EL, gsyn, Esyn, I1, I2, I3,
+ *                             tau_r, tau_d, sig, theta]. */
+enum { FF_RHS_LINEAR = 0, FF_RHS_HARMONIC = 1, FF_RHS_WILSON_COWAN = 2, FF_RHS_LORENZ = 3,
+       FF_RHS_HH3 = 4 };
+
+/* Time steppers: classical RK4 (the paper's solver, Sec. 2.1) or explicit Euler. */
+enum { FF_RK4 = 0, FF_EULER = 1 };
+
+/* ff_create_system flags. */
+#define FF_FLAG_KAHAN 1u  /* compensated (Kahan) summation of the state update */
+
+#define FF_MAX_DIM 16
+#define FF_MAX_PARAMS 64
+#define FF_MAX_GROUPS 16
+
+typedef struct ff_system ff_system;
+
+/* A render technique (paper Appendix A): which state variables are drawn and
+ * how they map to pixels.
+ *   ndim_view = 2: column = floor((x[axes[0]] - lo[0]) * (width  / (hi[0]-lo[0]))),
+ *                  row    = floor((x[axes[1]] - lo[1]) * (height / (hi[1]-lo[1]))),
+ *                  the scale factors formed in double and rounded to float,
+ *                  every other operation in float with its own rounding.
+ *   ndim_view = 3: clip = M [x[axes[0]], x[axes[1]], x[axes[2]], 1] with M the
+ *                  column-major Model-View-Projection matrix mvp (element
+ *                  (row j, col c) at mvp[4c + j], each row summed left to
+ *                  right); particles with clip.w <= 0 are dropped; otherwise
+ *                  (clip.x / clip.w, clip.y / clip.w) in [-1, 1) maps to the
+ *                  image with the 2D rule.
+ * A particle is drawn iff its pixel lies inside the image (this also drops
+ * non-finite coordinates).  Row 0 is the bottom of the view (lo[1] / ndc -1).
+ * An axis index equal to the system's dim selects the per-particle parameter
+ * (the paper's extra state variable with zero time derivative).
+ * group_mask bit g selects group g; accumulate = 0 clears the image first. */
+typedef struct ff_view {
+    int ndim_view;
+    int axes[3];
+    double lo[2];
+    double hi[2];
+    float mvp[16];
+    int width;
+    int height;
+    uint32_t group_mask;
+    int accumulate;
+} ff_view;
+
+/* Create a system: its right-hand side, parameter vector, stepper and room
+ * for `capacity` particles (paper Appendix A, "Initialization": an array of
+ * N * P single-precision values).  The state is stored structure-of-arrays,
+ * one plane of `pitch` floats per state variable, pitch = capacity rounded up
+ * to a multiple of 256.  cuda_stream is a cudaStream_t (or NULL).
+ * Errors: FF_ERR_INVALID_ARG for an unknown rhs_id/method, a dim or n_params
+ * that does not fit rhs_id, capacity < 1, non-finite parameters or unknown
+ * flags; FF_ERR_OOM if device memory runs out. */
+ff_status ff_create_system(int rhs_id, int dim, const double* params, int n_params, int method,
+                           unsigned flags, int64_t capacity, void* cuda_stream, ff_system** out);
+
+/* Release the system and its device memory (synchronises its stream). NULL is a no-op. */
+ff_status ff_destroy_system(ff_system* sys);
+
+/* Append a particle group (paper Appendix A, "Particle Group"): `count`
+ * particles with initial conditions uniform in the box [lo[k], hi[k]) of each
+ * state variable, integrated forward (direction +1) or backward (-1) in time.
+ * Group particle j, state variable k takes draw n = j*dim + k + 1 of the
+ * SplitMix64 stream seeded with `seed`; the top 24 bits give u in [0, 1) and
+ * x = lo + (hi - lo) * u is formed in double and rounded to float.  Groups
+ * occupy consecutive index ranges in creation order.  *group_id_out (may be
+ * NULL) receives the group's index.
+ * Errors: FF_ERR_STATE after the first ff_step (until ff_reset) or with
+ * FF_MAX_GROUPS groups; FF_ERR_INVALID_ARG for count < 1, more particles than
+ * the capacity, lo/hi NULL, non-finite or lo > hi, direction not +-1. */
+ff_status ff_seed_particles(ff_system* sys, int64_t count, const double* lo, const double* hi,
+                            int direction, uint64_t seed, int* group_id_out);
+
+/* Restart: re-seed every group from its box and seed, clear the Kahan
+ * compensation and simulated times (the paper re-initialises the GPU when a
+ * system is modified, Appendix A). Per-particle parameters are kept. */
+ff_status ff_reset(ff_system* sys);
+
+/* Dynamic bifurcation diagram (paper Sec. 2.1 and 2.2, last paragraphs):
+ * parameter `param_index` becomes a per-particle value, particle i of the P
+ * particles seeded so far getting lo + (hi - lo) * (i / (P - 1)) (double,
+ * rounded to float; lo for P = 1).  param_index = -1 switches it off.
+ * Errors: FF_ERR_INVALID_ARG for an index out of range or non-finite bounds;
+ * FF_ERR_STATE if no particles are seeded. */
+ff_status ff_set_particle_param(ff_system* sys, int param_index, double lo, double hi);
+
+/* Same, with caller-supplied per-particle values (P floats, host or device). */
+ff_status ff_set_particle_param_values(ff_system* sys, int param_index, const float* values,
+                                       int values_is_device);
+
+/* Copy the per-particle parameter values out (P floats, host or device; a
+ * host copy synchronises).  *param_index_out (may be NULL) receives the
+ * parameter they replace, -1 if none.  Errors: FF_ERR_STATE if no per-particle
+ * parameter was ever set. */
+ff_status ff_get_particle_param(ff_system* sys, float* dst, int dst_is_device, int* param_index_out);
+
+/* Advance every particle by n_steps constant steps (RK4 or Euler) of size
+ * direction_g * dt (paper Sec. 2.1; Appendix A "Running the Simulation":
+ * negative steps integrate backward).  The integrator keeps each particle's
+ * state in registers for all n_steps steps of a launch.  n_steps = 0 is a
+ * no-op.  Errors: FF_ERR_INVALID_ARG for n_steps < 0 or non-finite dt;
+ * FF_ERR_STATE if no particles are seeded; FF_ERR_CUDA on a launch failure. */
+ff_status ff_step(ff_system* sys, int64_t n_steps, double dt);
+
+/* Replace the system parameter vector between steps (paper Sec. 2.1 and
+ * Appendix A: sliders write the parameter values; the change is seen by the
+ * next step).  Ordered with ff_step on the system's stream.  A per-particle
+ * parameter keeps overriding its entry.
+ * Errors: FF_ERR_INVALID_ARG for a wrong n_params or non-finite values. */
+ff_status ff_set_params(ff_system* sys, const double* params, int n_params);
+
+/* Project every selected particle through `view` and add one count to its
+ * pixel of the uint32 image [height][width] (paper Appendix A, vertex,
+ * geometry and fragment shaders with additive blending).  image is a device
+ * pointer (image_is_device = 1) or host memory (0; the call then stages the
+ * image on the device and synchronises).
+ * Errors: FF_ERR_INVALID_ARG for a NULL image/view, ndim_view not 2 or 3, an
+ * axis out of range (or equal to dim without a per-particle parameter),
+ * width/height < 1 or width*height >= 2^31, lo >= hi or non-finite bounds. */
+ff_status ff_project_splat(ff_system* sys, const ff_view* view, uint32_t* image,
+                           int image_is_device);
+
+/* Copy the state out, SoA [dim][P] with P the number of seeded particles
+ * (dst holds dim*P floats; host or device).  A host copy synchronises. */
+ff_status ff_get_state(ff_system* sys, float* dst, int dst_is_device);
+
+/* Overwrite the state of all P seeded particles from SoA [dim][P] (host or
+ * device), e.g. to resume a checkpoint.  Clears the Kahan compensation. */
+ff_status ff_set_state(ff_system* sys, const float* src, int src_is_device);
+
+/* Statistics (synchronises): number of escaped particles (some component
+ * non-finite or above 1e30 in magnitude), and the simulated time of the
+ * forward and backward groups.  Any output pointer may be NULL. */
+ff_status ff_stats(ff_system* sys, int64_t* n_escaped, double* t_fwd, double* t_bwd);
+
+/* Size information: seeded particles, plane pitch, dim, groups (NULL-able). */
+ff_status ff_system_info(ff_system* sys, int64_t* n_particles, int64_t* pitch, int* dim,
+                         int* n_groups);
+
+/* Launch shape of the integrator: particles per thread (1, 2 or 4; 16-byte
+ * SoA loads at 4), threads per block (a multiple of 32, 32..1024), resident
+ * blocks per SM used for the persistent grid (0 = as many as fit), and the
+ * most steps per launch (0 = all steps of an ff_step call in one launch).
+ * Errors: FF_ERR_INVALID_ARG for values out of range. */
+ff_status ff_set_launch(ff_system* sys, int particles_per_thread, int block, int blocks_per_sm,
+                        int64_t max_steps_per_launch);
+
+/* Gradients through the integration (not part of the paper).  Not built yet:
+ * returns FF_ERR_UNSUPPORTED. */
+ff_status ff_backward(ff_system* sys, const float* dL_dxT_dev, float* dL_dx0_dev,
+                      double* dL_dp_host);
+
+/* Message describing the last error returned on the calling thread. */
+const char* ff_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FF_H */

@@ -1,1 +1,333 @@
-"""GB300-native Fireflies hot path (binding is loaded lazily)."""
+"""GB300-native Fireflies hot path: ctypes binding of ``libff.so`` (include/ff.h).
+
+Argument marshalling only -- every step of the path (seeding, integration,
+projection, splatting, statistics) runs in the CUDA kernels of ``libff.so``.
+There is no CPU fallback: if the library is not built or cannot be loaded,
+every call raises.
+
+Functions carry the C names (``ff_create_system``, ``ff_seed_particles``,
+``ff_step``, ``ff_set_params``, ``ff_project_splat``, ...).  Buffers may be
+torch CUDA tensors (device), numpy arrays (host) or raw integer device
+pointers.  ``System`` is a small convenience wrapper over the same calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (inputs only; no arithmetic of the method)
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libff.so")
+
+FF_OK, FF_ERR_INVALID_ARG, FF_ERR_CUDA, FF_ERR_OOM, FF_ERR_STATE, FF_ERR_UNSUPPORTED, FF_ERR_TIMEOUT = range(7)
+FF_RHS_LINEAR, FF_RHS_HARMONIC, FF_RHS_WILSON_COWAN, FF_RHS_LORENZ, FF_RHS_HH3 = range(5)
+FF_RK4, FF_EULER = 0, 1
+FF_FLAG_KAHAN = 1
+FF_MAX_DIM, FF_MAX_PARAMS, FF_MAX_GROUPS = 16, 64, 16
+
+RHS_BY_NAME = {"linear": FF_RHS_LINEAR, "harmonic": FF_RHS_HARMONIC, "wilson_cowan": FF_RHS_WILSON_COWAN,
+               "lorenz": FF_RHS_LORENZ, "hh3": FF_RHS_HH3}
+METHOD_BY_NAME = {"rk4": FF_RK4, "euler": FF_EULER}
+
+
+class FFError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"[ff status {status}] {message}")
+        self.status = status
+
+
+class ff_view(ctypes.Structure):
+    _fields_ = [("ndim_view", ctypes.c_int), ("axes", ctypes.c_int * 3), ("lo", ctypes.c_double * 2),
+                ("hi", ctypes.c_double * 2), ("mvp", ctypes.c_float * 16), ("width", ctypes.c_int),
+                ("height", ctypes.c_int), ("group_mask", ctypes.c_uint32), ("accumulate", ctypes.c_int)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGS = {
+    "ff_create_system": [ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, ctypes.c_uint, _I64, _P,
+                         ctypes.POINTER(_P)],
+    "ff_destroy_system": [_P],
+    "ff_seed_particles": [_P, _I64, _P, _P, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)],
+    "ff_reset": [_P],
+    "ff_set_particle_param": [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double],
+    "ff_set_particle_param_values": [_P, ctypes.c_int, _P, ctypes.c_int],
+    "ff_get_particle_param": [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "ff_step": [_P, _I64, ctypes.c_double],
+    "ff_set_params": [_P, _P, ctypes.c_int],
+    "ff_project_splat": [_P, ctypes.POINTER(ff_view), _P, ctypes.c_int],
+    "ff_get_state": [_P, _P, ctypes.c_int],
+    "ff_set_state": [_P, _P, ctypes.c_int],
+    "ff_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "ff_system_info": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_int)],
+    "ff_set_launch": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64],
+    "ff_backward": [_P, _P, _P, _P],
+}
+
+
+def lib():
+    """The loaded ``libff.so``; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() "
+                               "(or python -m paper_1505_00344_gb300._build)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.ff_last_error.argtypes = []
+        L.ff_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != FF_OK:
+        raise FFError(status, lib().ff_last_error().decode(errors="replace"))
+
+
+def _buf(obj, dtype=None):
+    """(pointer, is_device, keepalive) of a torch tensor, numpy array or int device pointer."""
+    if obj is None:
+        return None, 0, None
+    if isinstance(obj, int):
+        return obj, 1, None
+    if isinstance(obj, np.ndarray):
+        if not obj.flags.c_contiguous:
+            raise ValueError("host arrays must be C-contiguous")
+        if dtype is not None and obj.dtype != dtype:
+            raise ValueError(f"expected dtype {dtype}, got {obj.dtype}")
+        return obj.ctypes.data, 0, obj
+    # torch tensor (duck-typed so torch stays optional for host-only callers)
+    if hasattr(obj, "data_ptr") and hasattr(obj, "is_cuda"):
+        if not obj.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return obj.data_ptr(), 1 if obj.is_cuda else 0, obj
+    raise TypeError(f"unsupported buffer type {type(obj)}")
+
+
+def _dbl(v):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1))
+    return a, a.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return getattr(stream, "cuda_stream", None) or None
+
+
+def ff_create_system(rhs_id, dim, params, method=FF_RK4, flags=0, capacity=1, stream=None):
+    p, pp = _dbl(params)
+    out = _P()
+    _check(lib().ff_create_system(int(rhs_id), int(dim), pp, p.size, int(method), int(flags), int(capacity),
+                                  _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def ff_destroy_system(sys):
+    _check(lib().ff_destroy_system(sys))
+
+
+def ff_seed_particles(sys, count, lo, hi, direction, seed):
+    lo_a, lo_p = _dbl(lo)
+    hi_a, hi_p = _dbl(hi)
+    gid = ctypes.c_int(-1)
+    _check(lib().ff_seed_particles(sys, int(count), lo_p, hi_p, int(direction), int(seed) & (2**64 - 1),
+                                   ctypes.byref(gid)))
+    return gid.value
+
+
+def ff_reset(sys):
+    _check(lib().ff_reset(sys))
+
+
+def ff_set_particle_param(sys, param_index, lo=0.0, hi=0.0):
+    _check(lib().ff_set_particle_param(sys, int(param_index), float(lo), float(hi)))
+
+
+def ff_set_particle_param_values(sys, param_index, values):
+    ptr, dev, _keep = _buf(values, np.float32)
+    _check(lib().ff_set_particle_param_values(sys, int(param_index), ptr, dev))
+
+
+def ff_get_particle_param(sys, dst):
+    ptr, dev, _keep = _buf(dst, np.float32)
+    idx = ctypes.c_int(-1)
+    _check(lib().ff_get_particle_param(sys, ptr, dev, ctypes.byref(idx)))
+    return idx.value
+
+
+def ff_step(sys, n_steps, dt):
+    _check(lib().ff_step(sys, int(n_steps), float(dt)))
+
+
+def ff_set_params(sys, params):
+    p, pp = _dbl(params)
+    _check(lib().ff_set_params(sys, pp, p.size))
+
+
+def make_view(ndim_view=2, axes=(0, 1), lo=(0.0, 0.0), hi=(1.0, 1.0), mvp=None, width=256, height=256,
+              group_mask=0xFFFFFFFF, accumulate=0, **_ignored):
+    v = ff_view()
+    v.ndim_view = int(ndim_view)
+    ax = list(axes) + [0] * (3 - len(axes))
+    for q in range(3):
+        v.axes[q] = int(ax[q])
+    if ndim_view == 2:
+        for q in range(2):
+            v.lo[q] = float(lo[q])
+            v.hi[q] = float(hi[q])
+    m = np.eye(4, dtype=np.float32).reshape(16) if mvp is None else np.asarray(mvp, np.float32).reshape(16)
+    for q in range(16):
+        v.mvp[q] = float(m[q])
+    v.width, v.height = int(width), int(height)
+    v.group_mask = int(group_mask) & 0xFFFFFFFF
+    v.accumulate = int(accumulate)
+    return v
+
+
+def ff_project_splat(sys, view, image):
+    if isinstance(view, dict):
+        view = make_view(**view)
+    ptr, dev, _keep = _buf(image)
+    _check(lib().ff_project_splat(sys, ctypes.byref(view), ptr, dev))
+
+
+def ff_get_state(sys, dst):
+    ptr, dev, _keep = _buf(dst, np.float32)
+    _check(lib().ff_get_state(sys, ptr, dev))
+
+
+def ff_set_state(sys, src):
+    ptr, dev, _keep = _buf(src, np.float32)
+    _check(lib().ff_set_state(sys, ptr, dev))
+
+
+def ff_stats(sys):
+    n = _I64(0)
+    tf = ctypes.c_double(0)
+    tb = ctypes.c_double(0)
+    _check(lib().ff_stats(sys, ctypes.byref(n), ctypes.byref(tf), ctypes.byref(tb)))
+    return n.value, tf.value, tb.value
+
+
+def ff_system_info(sys):
+    n = _I64(0)
+    pitch = _I64(0)
+    dim = ctypes.c_int(0)
+    ng = ctypes.c_int(0)
+    _check(lib().ff_system_info(sys, ctypes.byref(n), ctypes.byref(pitch), ctypes.byref(dim), ctypes.byref(ng)))
+    return n.value, pitch.value, dim.value, ng.value
+
+
+def ff_set_launch(sys, particles_per_thread=1, block=256, blocks_per_sm=0, max_steps_per_launch=0):
+    _check(lib().ff_set_launch(sys, int(particles_per_thread), int(block), int(blocks_per_sm),
+                               int(max_steps_per_launch)))
+
+
+def ff_backward(sys, dL_dxT, dL_dx0, dL_dp):
+    a, _, _ka = _buf(dL_dxT)
+    b, _, _kb = _buf(dL_dx0)
+    c, _, _kc = _buf(dL_dp, np.float64)
+    _check(lib().ff_backward(sys, a, b, c))
+
+
+def ff_last_error():
+    return lib().ff_last_error().decode(errors="replace")
+
+
+class System:
+    """Owning handle over one ``ff_system`` (thin wrapper over the ff_* calls)."""
+
+    def __init__(self, rhs, params, capacity, dim=None, method="rk4", kahan=False, stream=None):
+        rhs_id = RHS_BY_NAME[rhs] if isinstance(rhs, str) else int(rhs)
+        if dim is None:
+            dim = {FF_RHS_HARMONIC: 2, FF_RHS_WILSON_COWAN: 2, FF_RHS_LORENZ: 3, FF_RHS_HH3: 15}.get(rhs_id)
+            if dim is None:
+                dim = int(round(np.sqrt(len(params))))
+        meth = METHOD_BY_NAME[method] if isinstance(method, str) else int(method)
+        self.dim = dim
+        self.handle = ff_create_system(rhs_id, dim, params, meth, FF_FLAG_KAHAN if kahan else 0, capacity, stream)
+
+    @classmethod
+    def from_workload(cls, w, kahan=False, stream=None, capacity=None):
+        """Create and seed a system from a ``workloads`` description."""
+        total = sum(g["count"] for g in w["groups"])
+        s = cls(w["rhs"], w["params"], capacity or total, dim=w["dim"], method=w.get("method", "rk4"),
+                kahan=kahan, stream=stream)
+        for g in w["groups"]:
+            s.seed(g["count"], g["lo"], g["hi"], g["direction"], g["seed"])
+        if "pparam" in w:
+            pp = w["pparam"]
+            s.set_particle_param(pp["index"], pp["lo"], pp["hi"])
+        return s
+
+    def seed(self, count, lo, hi, direction, seed):
+        return ff_seed_particles(self.handle, count, lo, hi, direction, seed)
+
+    def reset(self):
+        ff_reset(self.handle)
+
+    def set_particle_param(self, index, lo=0.0, hi=0.0):
+        ff_set_particle_param(self.handle, index, lo, hi)
+
+    def set_particle_param_values(self, index, values):
+        ff_set_particle_param_values(self.handle, index, values)
+
+    def get_particle_param(self, dst):
+        return ff_get_particle_param(self.handle, dst)
+
+    def step(self, n_steps, dt):
+        ff_step(self.handle, n_steps, dt)
+
+    def set_params(self, params):
+        ff_set_params(self.handle, params)
+
+    def project_splat(self, view, image):
+        ff_project_splat(self.handle, view, image)
+
+    def get_state(self, dst):
+        ff_get_state(self.handle, dst)
+
+    def set_state(self, src):
+        ff_set_state(self.handle, src)
+
+    def stats(self):
+        return ff_stats(self.handle)
+
+    def info(self):
+        return ff_system_info(self.handle)
+
+    def set_launch(self, particles_per_thread=1, block=256, blocks_per_sm=0, max_steps_per_launch=0):
+        ff_set_launch(self.handle, particles_per_thread, block, blocks_per_sm, max_steps_per_launch)
+
+    @property
+    def n_particles(self):
+        return self.info()[0]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ff_destroy_system(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,541 @@
+// ff_api.cu -- the C ABI declared in include/ff.h: system ownership, argument
+// checks, group tables, simulated time, and the launches of the hot-path
+// kernels on the system's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "ff.h"
+#include "ff_aux.h"
+#include "ff_device.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ff_status fail(ff_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+ff_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(FF_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(FF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct Group {
+    int64_t start, count;
+    int direction;
+    uint64_t seed;
+    double lo[FF_MAX_DIM], hi[FF_MAX_DIM];
+};
+
+// Makes the system's device current for the lifetime of the object.
+struct DeviceScope {
+    int prev = -1;
+    bool changed = false;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceScope(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) {
+            err = cudaSetDevice(dev);
+            changed = (err == cudaSuccess);
+        }
+    }
+    ~DeviceScope() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+bool all_finite(const double* v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+int rhs_dim_ok(int rhs_id, int dim, int n_params) {
+    switch (rhs_id) {
+    case FF_RHS_LINEAR: return dim >= 1 && dim <= 8 && n_params == dim * dim;
+    case FF_RHS_HARMONIC: return dim == 2 && n_params == 1;
+    case FF_RHS_WILSON_COWAN: return dim == 2 && n_params == 10;
+    case FF_RHS_LORENZ: return dim == 3 && n_params == 3;
+    case FF_RHS_HH3: return dim == 15 && n_params == 16;
+    default: return 0;
+    }
+}
+
+}  // namespace
+
+struct ff_system {
+    int device = 0;
+    int num_sms = 1;
+    cudaStream_t stream = nullptr;
+    int rhs_id = 0, dim = 0, method = 0;
+    unsigned flags = 0;
+    int n_params = 0;
+    double params[FF_MAX_PARAMS] = {};
+    int64_t capacity = 0, pitch = 0, n_particles = 0;
+    float* d_state = nullptr;
+    float* d_comp = nullptr;
+    float* d_pparam = nullptr;
+    int pparam_index = -1;
+    int n_groups = 0;
+    Group groups[FF_MAX_GROUPS] = {};
+    bool stepped = false;
+    double t_fwd = 0, t_bwd = 0, c_fwd = 0, c_bwd = 0;  // Kahan-summed simulated time
+    unsigned long long* d_counter = nullptr;
+    uint32_t* d_stage = nullptr;  // device copy of a host image
+    size_t stage_bytes = 0;
+    // launch shape
+    int ppt = 1, block = 256, blocks_per_sm = 0;
+    int64_t max_steps = 0;
+};
+
+namespace {
+
+// Kernel index of parameter q of the user's vector (LINEAR is padded to 8x8).
+int kernel_param_index(const ff_system* s, int q) {
+    if (s->rhs_id == FF_RHS_LINEAR) return (q / s->dim) * 8 + (q % s->dim);
+    return q;
+}
+
+void kahan_add(double& sum, double& comp, double v) {
+    double y = v - comp;
+    double t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+ff_status seed_group(ff_system* s, const Group& g) {
+    ff::SeedArgs a{};
+    a.x = s->d_state;
+    a.pitch = s->pitch;
+    a.start = g.start;
+    a.count = g.count;
+    a.seed = g.seed;
+    a.dim = s->dim;
+    for (int k = 0; k < s->dim; ++k) {
+        a.lo[k] = g.lo[k];
+        a.width[k] = g.hi[k] - g.lo[k];
+    }
+    cudaError_t e = ff::launch_seed(a, s->num_sms, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "seed kernel launch");
+    return FF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ff_last_error(void) { return g_last_error.c_str(); }
+
+ff_status ff_create_system(int rhs_id, int dim, const double* params, int n_params, int method,
+                           unsigned flags, int64_t capacity, void* cuda_stream, ff_system** out) {
+    if (!out) return fail(FF_ERR_INVALID_ARG, "ff_create_system: out is NULL");
+    *out = nullptr;
+    if (!rhs_dim_ok(rhs_id, dim, n_params))
+        return fail(FF_ERR_INVALID_ARG, "ff_create_system: rhs_id %d does not take dim %d with %d params",
+                    rhs_id, dim, n_params);
+    if (method != FF_RK4 && method != FF_EULER)
+        return fail(FF_ERR_INVALID_ARG, "ff_create_system: unknown method %d", method);
+    if (flags & ~FF_FLAG_KAHAN) return fail(FF_ERR_INVALID_ARG, "ff_create_system: unknown flags 0x%x", flags);
+    if (!params || !all_finite(params, n_params))
+        return fail(FF_ERR_INVALID_ARG, "ff_create_system: params NULL or not finite");
+    if (capacity < 1 || capacity > ((int64_t)1 << 40))
+        return fail(FF_ERR_INVALID_ARG, "ff_create_system: capacity %lld out of range", (long long)capacity);
+    ff_system* s = new (std::nothrow) ff_system();
+    if (!s) return fail(FF_ERR_OOM, "ff_create_system: host allocation failed");
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "ff_create_system: no usable CUDA device");
+    }
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    s->rhs_id = rhs_id;
+    s->dim = dim;
+    s->method = method;
+    s->flags = flags;
+    s->n_params = n_params;
+    memcpy(s->params, params, sizeof(double) * n_params);
+    s->capacity = capacity;
+    s->pitch = (capacity + 255) / 256 * 256;
+    const size_t plane_bytes = sizeof(float) * (size_t)s->pitch;
+    e = cudaMalloc(&s->d_state, plane_bytes * dim);
+    if (e == cudaSuccess && (flags & FF_FLAG_KAHAN)) e = cudaMalloc(&s->d_comp, plane_bytes * dim);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_state, 0, plane_bytes * dim, s->stream);
+    if (e == cudaSuccess && s->d_comp) e = cudaMemsetAsync(s->d_comp, 0, plane_bytes * dim, s->stream);
+    if (e != cudaSuccess) {
+        ff_status st = cuda_fail(e, "ff_create_system: device allocation");
+        ff_destroy_system(s);
+        return st;
+    }
+    // defaults: one particle per thread for the big systems, two for 2-3 dimensional ones
+    s->ppt = 1;
+    *out = s;
+    return FF_OK;
+}
+
+ff_status ff_destroy_system(ff_system* s) {
+    if (!s) return FF_OK;
+    DeviceScope dev(s->device);
+    cudaStreamSynchronize(s->stream);
+    cudaFree(s->d_state);
+    cudaFree(s->d_comp);
+    cudaFree(s->d_pparam);
+    cudaFree(s->d_counter);
+    cudaFree(s->d_stage);
+    delete s;
+    return FF_OK;
+}
+
+ff_status ff_seed_particles(ff_system* s, int64_t count, const double* lo, const double* hi,
+                            int direction, uint64_t seed, int* group_id_out) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_seed_particles: system is NULL");
+    if (s->stepped) return fail(FF_ERR_STATE, "ff_seed_particles: system already stepped (call ff_reset first)");
+    if (s->n_groups >= FF_MAX_GROUPS) return fail(FF_ERR_STATE, "ff_seed_particles: already %d groups", FF_MAX_GROUPS);
+    if (count < 1) return fail(FF_ERR_INVALID_ARG, "ff_seed_particles: count %lld < 1", (long long)count);
+    if (count > s->capacity - s->n_particles)
+        return fail(FF_ERR_INVALID_ARG, "ff_seed_particles: %lld particles exceed the remaining capacity %lld",
+                    (long long)count, (long long)(s->capacity - s->n_particles));
+    if (!lo || !hi) return fail(FF_ERR_INVALID_ARG, "ff_seed_particles: lo/hi NULL");
+    if (!all_finite(lo, s->dim) || !all_finite(hi, s->dim))
+        return fail(FF_ERR_INVALID_ARG, "ff_seed_particles: non-finite box");
+    for (int k = 0; k < s->dim; ++k)
+        if (lo[k] > hi[k]) return fail(FF_ERR_INVALID_ARG, "ff_seed_particles: lo[%d] > hi[%d]", k, k);
+    if (direction != 1 && direction != -1)
+        return fail(FF_ERR_INVALID_ARG, "ff_seed_particles: direction %d is not +1 or -1", direction);
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_seed_particles: set device");
+    Group g{};
+    g.start = s->n_particles;
+    g.count = count;
+    g.direction = direction;
+    g.seed = seed;
+    for (int k = 0; k < s->dim; ++k) {
+        g.lo[k] = lo[k];
+        g.hi[k] = hi[k];
+    }
+    ff_status st = seed_group(s, g);
+    if (st != FF_OK) return st;
+    s->groups[s->n_groups] = g;
+    if (group_id_out) *group_id_out = s->n_groups;
+    s->n_groups++;
+    s->n_particles += count;
+    return FF_OK;
+}
+
+ff_status ff_reset(ff_system* s) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_reset: system is NULL");
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_reset: set device");
+    for (int g = 0; g < s->n_groups; ++g) {
+        ff_status st = seed_group(s, s->groups[g]);
+        if (st != FF_OK) return st;
+    }
+    if (s->d_comp) {
+        cudaError_t e = cudaMemsetAsync(s->d_comp, 0, sizeof(float) * (size_t)s->pitch * s->dim, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "ff_reset: clear compensation");
+    }
+    s->t_fwd = s->t_bwd = s->c_fwd = s->c_bwd = 0.0;
+    s->stepped = false;
+    return FF_OK;
+}
+
+static ff_status ensure_pparam(ff_system* s) {
+    if (s->d_pparam) return FF_OK;
+    cudaError_t e = cudaMalloc(&s->d_pparam, sizeof(float) * (size_t)s->pitch);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_pparam, 0, sizeof(float) * (size_t)s->pitch, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "per-particle parameter allocation");
+    return FF_OK;
+}
+
+ff_status ff_set_particle_param(ff_system* s, int param_index, double lo, double hi) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param: system is NULL");
+    if (param_index == -1) {
+        s->pparam_index = -1;
+        return FF_OK;
+    }
+    if (param_index < 0 || param_index >= s->n_params)
+        return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param: index %d out of range", param_index);
+    if (!std::isfinite(lo) || !std::isfinite(hi))
+        return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param: non-finite bounds");
+    if (s->n_particles < 1) return fail(FF_ERR_STATE, "ff_set_particle_param: no particles seeded");
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_set_particle_param: set device");
+    ff_status st = ensure_pparam(s);
+    if (st != FF_OK) return st;
+    cudaError_t e = ff::launch_linspace(s->d_pparam, s->n_particles, lo, hi, s->num_sms, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "linspace kernel launch");
+    s->pparam_index = param_index;
+    return FF_OK;
+}
+
+ff_status ff_set_particle_param_values(ff_system* s, int param_index, const float* values,
+                                       int values_is_device) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param_values: system is NULL");
+    if (param_index < 0 || param_index >= s->n_params)
+        return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param_values: index %d out of range", param_index);
+    if (!values) return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param_values: values is NULL");
+    if (s->n_particles < 1) return fail(FF_ERR_STATE, "ff_set_particle_param_values: no particles seeded");
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_set_particle_param_values: set device");
+    ff_status st = ensure_pparam(s);
+    if (st != FF_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(s->d_pparam, values, sizeof(float) * (size_t)s->n_particles,
+                                    values_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    s->stream);
+    if (e == cudaSuccess && !values_is_device) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_set_particle_param_values: copy");
+    s->pparam_index = param_index;
+    return FF_OK;
+}
+
+ff_status ff_get_particle_param(ff_system* s, float* dst, int dst_is_device, int* param_index_out) {
+    if (!s || !dst) return fail(FF_ERR_INVALID_ARG, "ff_get_particle_param: NULL argument");
+    if (!s->d_pparam) return fail(FF_ERR_STATE, "ff_get_particle_param: no per-particle parameter set");
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_get_particle_param: set device");
+    cudaError_t e = cudaMemcpyAsync(dst, s->d_pparam, sizeof(float) * (size_t)s->n_particles,
+                                    dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess && !dst_is_device) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_get_particle_param: copy");
+    if (param_index_out) *param_index_out = s->pparam_index;
+    return FF_OK;
+}
+
+ff_status ff_set_params(ff_system* s, const double* params, int n_params) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_set_params: system is NULL");
+    if (!params || n_params != s->n_params)
+        return fail(FF_ERR_INVALID_ARG, "ff_set_params: expected %d params", s->n_params);
+    if (!all_finite(params, n_params)) return fail(FF_ERR_INVALID_ARG, "ff_set_params: non-finite values");
+    // Parameters travel by value in each launch's argument block, so the new
+    // values are seen exactly by the launches enqueued after this call.
+    memcpy(s->params, params, sizeof(double) * n_params);
+    return FF_OK;
+}
+
+ff_status ff_set_launch(ff_system* s, int ppt, int block, int blocks_per_sm, int64_t max_steps) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: system is NULL");
+    if (ppt != 1 && ppt != 2 && ppt != 4) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: ppt %d not 1, 2 or 4", ppt);
+    if (ppt != 1 && s->dim > 4 && s->rhs_id != FF_RHS_LINEAR)
+        return fail(FF_ERR_INVALID_ARG, "ff_set_launch: ppt > 1 needs dim <= 4");
+    if (ppt != 1 && s->rhs_id == FF_RHS_LINEAR) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: LINEAR runs ppt 1");
+    if (block < 32 || block > 1024 || block % 32) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: block %d", block);
+    if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: blocks_per_sm %d", blocks_per_sm);
+    if (max_steps < 0) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: max_steps < 0");
+    s->ppt = ppt;
+    s->block = block;
+    s->blocks_per_sm = blocks_per_sm;
+    s->max_steps = max_steps;
+    return FF_OK;
+}
+
+ff_status ff_step(ff_system* s, int64_t n_steps, double dt) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_step: system is NULL");
+    if (n_steps < 0) return fail(FF_ERR_INVALID_ARG, "ff_step: n_steps %lld < 0", (long long)n_steps);
+    if (!std::isfinite(dt)) return fail(FF_ERR_INVALID_ARG, "ff_step: dt not finite");
+    if (s->n_particles < 1) return fail(FF_ERR_STATE, "ff_step: no particles seeded");
+    if (n_steps == 0) return FF_OK;
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_step: set device");
+
+    ff::IntegrateArgs a{};
+    a.x = s->d_state;
+    a.comp = s->d_comp;
+    a.pparam = s->d_pparam;
+    a.pitch = s->pitch;
+    a.dim = s->dim;
+    a.n_groups = s->n_groups;
+    a.pidx = s->pparam_index >= 0 ? kernel_param_index(s, s->pparam_index) : -1;
+    for (int g = 0; g < s->n_groups; ++g) {
+        a.gstart[g] = s->groups[g].start;
+        a.gh[g] = (float)(s->groups[g].direction * dt);
+    }
+    for (int q = 0; q < s->n_params; ++q) a.p[kernel_param_index(s, q)] = (float)s->params[q];
+    // all processed particles are a multiple of 4 (<= pitch): every vector access stays in bounds
+    const int64_t n_work = (s->n_particles + 3) / 4 * 4;
+    const int ppt = s->ppt;
+    a.n_vec = n_work / ppt;
+    ff::LaunchShape shape{ppt, s->block, s->blocks_per_sm, s->num_sms};
+    const bool kahan = (s->flags & FF_FLAG_KAHAN) != 0;
+    const bool pp = s->pparam_index >= 0;
+    int64_t left = n_steps;
+    while (left > 0) {
+        const int64_t chunk = (s->max_steps > 0 && left > s->max_steps) ? s->max_steps : left;
+        a.n_steps = chunk;
+        cudaError_t e = ff::launch_integrate(s->rhs_id, s->method, kahan, pp, a, shape, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "integrator launch");
+        left -= chunk;
+    }
+    bool any_fwd = false, any_bwd = false;
+    for (int g = 0; g < s->n_groups; ++g) (s->groups[g].direction > 0 ? any_fwd : any_bwd) = true;
+    const double span = (double)n_steps * dt;
+    if (any_fwd) kahan_add(s->t_fwd, s->c_fwd, span);
+    if (any_bwd) kahan_add(s->t_bwd, s->c_bwd, -span);
+    s->stepped = true;
+    return FF_OK;
+}
+
+ff_status ff_project_splat(ff_system* s, const ff_view* v, uint32_t* image, int image_is_device) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_project_splat: system is NULL");
+    if (!v || !image) return fail(FF_ERR_INVALID_ARG, "ff_project_splat: view or image is NULL");
+    if (v->ndim_view != 2 && v->ndim_view != 3)
+        return fail(FF_ERR_INVALID_ARG, "ff_project_splat: ndim_view %d not 2 or 3", v->ndim_view);
+    if (v->width < 1 || v->height < 1 || (int64_t)v->width * v->height >= ((int64_t)1 << 31))
+        return fail(FF_ERR_INVALID_ARG, "ff_project_splat: image %d x %d out of range", v->width, v->height);
+    ff::SplatArgs a{};
+    for (int q = 0; q < v->ndim_view; ++q) {
+        const int ax = v->axes[q];
+        if (ax < 0 || ax > s->dim || (ax == s->dim && s->pparam_index < 0))
+            return fail(FF_ERR_INVALID_ARG, "ff_project_splat: axis %d out of range", ax);
+        a.ax[q] = (ax == s->dim) ? s->d_pparam : s->d_state + (int64_t)ax * s->pitch;
+    }
+    a.W = v->width;
+    a.H = v->height;
+    a.Wf = (float)v->width;
+    a.Hf = (float)v->height;
+    if (v->ndim_view == 2) {
+        for (int q = 0; q < 2; ++q)
+            if (!std::isfinite(v->lo[q]) || !std::isfinite(v->hi[q]) || !(v->lo[q] < v->hi[q]))
+                return fail(FF_ERR_INVALID_ARG, "ff_project_splat: window axis %d needs finite lo < hi", q);
+        a.lo0 = (float)v->lo[0];
+        a.lo1 = (float)v->lo[1];
+        a.s0 = (float)((double)v->width / (v->hi[0] - v->lo[0]));
+        a.s1 = (float)((double)v->height / (v->hi[1] - v->lo[1]));
+    } else {
+        for (int q = 0; q < 16; ++q) {
+            if (!std::isfinite(v->mvp[q])) return fail(FF_ERR_INVALID_ARG, "ff_project_splat: non-finite mvp");
+            a.m[q] = v->mvp[q];
+        }
+        a.lo0 = a.lo1 = -1.0f;
+        a.s0 = (float)((double)v->width / 2.0);
+        a.s1 = (float)((double)v->height / 2.0);
+    }
+    a.n = s->n_particles;
+    a.n_groups = s->n_groups;
+    uint32_t all = (s->n_groups >= 32) ? 0xffffffffu : ((1u << s->n_groups) - 1u);
+    a.mask = v->group_mask & all;
+    for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
+    const bool masked = a.mask != all;
+
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_project_splat: set device");
+    const size_t bytes = sizeof(uint32_t) * (size_t)v->width * v->height;
+    uint32_t* target = image;
+    cudaError_t e = cudaSuccess;
+    if (!image_is_device) {
+        if (s->stage_bytes < bytes) {
+            cudaFree(s->d_stage);
+            s->d_stage = nullptr;
+            s->stage_bytes = 0;
+            e = cudaMalloc(&s->d_stage, bytes);
+            if (e != cudaSuccess) return cuda_fail(e, "ff_project_splat: staging image");
+            s->stage_bytes = bytes;
+        }
+        target = s->d_stage;
+        if (v->accumulate) e = cudaMemcpyAsync(target, image, bytes, cudaMemcpyHostToDevice, s->stream);
+    }
+    if (e == cudaSuccess && !v->accumulate) e = cudaMemsetAsync(target, 0, bytes, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_project_splat: image clear/upload");
+    a.image = target;
+    if (s->n_particles > 0 && a.mask != 0) {
+        e = ff::launch_splat(a, v->ndim_view, masked, s->num_sms, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "splat kernel launch");
+    }
+    if (!image_is_device) {
+        e = cudaMemcpyAsync(image, target, bytes, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "ff_project_splat: image download");
+    }
+    return FF_OK;
+}
+
+ff_status ff_get_state(ff_system* s, float* dst, int dst_is_device) {
+    if (!s || !dst) return fail(FF_ERR_INVALID_ARG, "ff_get_state: NULL argument");
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_get_state: set device");
+    if (s->n_particles == 0) return FF_OK;
+    cudaError_t e = cudaMemcpy2DAsync(dst, sizeof(float) * s->n_particles, s->d_state, sizeof(float) * s->pitch,
+                                      sizeof(float) * s->n_particles, s->dim,
+                                      dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                      s->stream);
+    if (e == cudaSuccess && !dst_is_device) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_get_state: copy");
+    return FF_OK;
+}
+
+ff_status ff_set_state(ff_system* s, const float* src, int src_is_device) {
+    if (!s || !src) return fail(FF_ERR_INVALID_ARG, "ff_set_state: NULL argument");
+    if (s->n_particles < 1) return fail(FF_ERR_STATE, "ff_set_state: no particles seeded");
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_set_state: set device");
+    cudaError_t e = cudaMemcpy2DAsync(s->d_state, sizeof(float) * s->pitch, src, sizeof(float) * s->n_particles,
+                                      sizeof(float) * s->n_particles, s->dim,
+                                      src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                      s->stream);
+    if (e == cudaSuccess && s->d_comp)
+        e = cudaMemsetAsync(s->d_comp, 0, sizeof(float) * (size_t)s->pitch * s->dim, s->stream);
+    if (e == cudaSuccess && !src_is_device) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_set_state: copy");
+    return FF_OK;
+}
+
+ff_status ff_stats(ff_system* s, int64_t* n_escaped, double* t_fwd, double* t_bwd) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_stats: system is NULL");
+    if (t_fwd) *t_fwd = s->t_fwd;
+    if (t_bwd) *t_bwd = s->t_bwd;
+    if (!n_escaped) return FF_OK;
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_stats: set device");
+    cudaError_t e = ff::launch_escape_count(s->d_state, s->pitch, s->dim, s->n_particles, s->d_counter,
+                                            s->num_sms, s->stream);
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, s->d_counter, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_stats: escape count");
+    *n_escaped = (int64_t)h;
+    return FF_OK;
+}
+
+ff_status ff_system_info(ff_system* s, int64_t* n_particles, int64_t* pitch, int* dim, int* n_groups) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_system_info: system is NULL");
+    if (n_particles) *n_particles = s->n_particles;
+    if (pitch) *pitch = s->pitch;
+    if (dim) *dim = s->dim;
+    if (n_groups) *n_groups = s->n_groups;
+    return FF_OK;
+}
+
+ff_status ff_backward(ff_system* s, const float* dL_dxT_dev, float* dL_dx0_dev, double* dL_dp_host) {
+    (void)s; (void)dL_dxT_dev; (void)dL_dx0_dev; (void)dL_dp_host;
+    return fail(FF_ERR_UNSUPPORTED, "ff_backward: the adjoint integrator is not built yet");
+}
+
+}  // extern "C"
+
+namespace ff {
+cudaError_t launch_integrate(int rhs_id, int method, bool kahan, bool pp, const IntegrateArgs& a,
+                             const LaunchShape& shape, cudaStream_t stream) {
+    switch (rhs_id) {
+    case FF_RHS_LORENZ: return launch_integrate_lorenz(method, kahan, pp, a, shape, stream);
+    case FF_RHS_WILSON_COWAN: return launch_integrate_wc(method, kahan, pp, a, shape, stream);
+    case FF_RHS_HH3: return launch_integrate_hh3(method, kahan, pp, a, shape, stream);
+    case FF_RHS_LINEAR:
+    case FF_RHS_HARMONIC: return launch_integrate_linear(rhs_id, method, kahan, pp, a, shape, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace ff

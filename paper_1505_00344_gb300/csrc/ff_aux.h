@@ -1,0 +1,49 @@
+// ff_aux.h -- argument blocks and host launchers of the non-integrator kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ff.h"
+
+namespace ff {
+
+struct SeedArgs {
+    float* x;        // state planes
+    int64_t pitch;
+    int64_t start;   // first particle of the group
+    int64_t count;
+    uint64_t seed;
+    int dim;
+    int pad_;
+    double lo[FF_MAX_DIM];
+    double width[FF_MAX_DIM];  // hi - lo, formed in double on the host
+};
+
+constexpr int kSplatBlock = 256;
+constexpr int kSplatPerThread = 16;
+constexpr int kSplatChunk = kSplatBlock * kSplatPerThread;
+constexpr int kSplatBins = 8192;  // 32 KB shared-memory histogram
+
+struct SplatArgs {
+    const float* ax[3];  // planes of the view axes
+    int64_t n;           // particles
+    uint32_t* image;
+    int W, H;
+    float Wf, Hf;
+    float lo0, s0, lo1, s1;  // 2D window (3D: lo = -1, s = W/2, H/2)
+    float m[16];             // 3D Model-View-Projection, column-major
+    int n_groups;
+    uint32_t mask;
+    int64_t gstart[FF_MAX_GROUPS];
+};
+
+cudaError_t launch_seed(const SeedArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_linspace(float* out, int64_t P, double lo, double hi, int num_sms,
+                            cudaStream_t s);
+cudaError_t launch_splat(const SplatArgs& a, int ndim_view, bool masked, int num_sms,
+                         cudaStream_t s);
+cudaError_t launch_escape_count(const float* x, int64_t pitch, int dim, int64_t n,
+                                unsigned long long* counter, int num_sms, cudaStream_t s);
+
+}  // namespace ff

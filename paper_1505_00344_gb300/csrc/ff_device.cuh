@@ -1,0 +1,427 @@
+// ff_device.cuh -- device code of the integrator: kernel arguments, the
+// per-system right-hand sides f(x, p) in FP32, the RK4 / Euler steppers and the
+// persistent integration kernel template.
+//
+// Layout: state is structure-of-arrays, plane k (state variable k) at
+// x + k * pitch, pitch a multiple of 256 floats, so a thread owning PPT
+// consecutive particles reads and writes each plane with one PPT*4-byte vector
+// access (16 bytes at PPT = 4).  Each thread keeps its particles' state in
+// registers for all steps of a launch: the only global traffic of an
+// n-step launch is one read and one write of the state (plus the Kahan
+// compensation and the per-particle parameter when enabled).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ff.h"
+
+namespace ff {
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+struct IntegrateArgs {
+    float* x;              // state planes
+    float* comp;           // Kahan compensation planes (KAHAN only)
+    const float* pparam;   // per-particle parameter values (PP only)
+    int64_t n_vec;         // work items = particles processed / PPT
+    int64_t pitch;         // floats between planes
+    int64_t n_steps;       // steps in this launch
+    int dim;               // planes actually stored (LINEAR may use fewer than its DIM)
+    int n_groups;
+    int pidx;              // parameter replaced by pparam (PP only)
+    int pad_;
+    int64_t gstart[FF_MAX_GROUPS];  // first particle of each group
+    float gh[FF_MAX_GROUPS];        // signed step of each group
+    float p[FF_MAX_PARAMS];         // system parameters (FP32)
+};
+
+// ---------------------------------------------------------------------------
+// Right-hand sides.  Each has DIM (registers per particle state), NP (params)
+// and f(x, p, dx).  All arithmetic in FP32; exp via exp2f with the log2(e)
+// factor folded into the argument, quotients via __fdividef.
+// ---------------------------------------------------------------------------
+
+// Linear test system dx/dt = A x, A padded to 8x8 (row-major) by the host;
+// unused rows/columns are zero so padded components stay zero.
+struct Linear {
+    static constexpr int DIM = 8;
+    static constexpr int NP = 64;
+    __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) s = fmaf(p[i * DIM + j], x[j], s);
+            dx[i] = s;
+        }
+    }
+};
+
+// Harmonic oscillator: dx = v, dv = -w^2 x.
+struct Harmonic {
+    static constexpr int DIM = 2;
+    static constexpr int NP = 1;
+    __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
+        dx[0] = x[1];
+        dx[1] = -(p[0] * p[0]) * x[0];
+    }
+};
+
+// Wilson-Cowan E-I pair (paper Eq. 1-2):
+//   tauE dE = -E + S(wEE E - wEI I + P),  tauI dI = -I + S(wIE E - wII I + Q),
+//   S(a) = 1 / (1 + exp(-gain (a - threshold))).
+struct WilsonCowan {
+    static constexpr int DIM = 2;
+    static constexpr int NP = 10;
+    __device__ __forceinline__ static float S(float a, float g2, float g2th) {
+        // exp(-gain (a - th)) = 2^(g2 th - g2 a) with g2 = gain * log2(e)
+        float e = exp2f(fmaf(-g2, a, g2th));
+        return __fdividef(1.0f, 1.0f + e);
+    }
+    __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
+        const float E = x[0], I = x[1];
+        const float g2 = p[8] * kLog2e, g2th = g2 * p[9];
+        const float aE = fmaf(p[0], E, fmaf(-p[1], I, p[4]));
+        const float aI = fmaf(p[2], E, fmaf(-p[3], I, p[5]));
+        dx[0] = __fdividef(S(aE, g2, g2th) - E, p[6]);
+        dx[1] = __fdividef(S(aI, g2, g2th) - I, p[7]);
+    }
+};
+
+// Lorenz (paper Eq. 3-5): dx = sigma (y - x), dy = x (r - z) - y, dz = x y - beta z.
+struct Lorenz {
+    static constexpr int DIM = 3;
+    static constexpr int NP = 3;
+    __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
+        dx[0] = p[0] * (x[1] - x[0]);
+        dx[1] = fmaf(x[0], p[1] - x[2], -x[1]);
+        dx[2] = fmaf(x[0], x[1], -(p[2] * x[2]));
+    }
+};
+
+// v / (1 - exp(-v/10)), the shape of alpha_m and alpha_n.  Near v = 0 the FP32
+// difference 1 - exp(-y) cancels, so for |y| < 0.1 (y = v/10) the Bernoulli
+// series 10 (1 + y/2 + y^2/12 - y^4/720) is used (truncation < 4e-11).
+__device__ __forceinline__ float hh_vtrap(float v) {
+    const float y = v * 0.1f;
+    const float e = exp2f(-y * kLog2e);
+    const float direct = __fdividef(v, 1.0f - e);
+    const float y2 = y * y;
+    const float series = 10.0f * fmaf(y2, fmaf(y2, -1.0f / 720.0f, 1.0f / 12.0f), fmaf(0.5f, y, 1.0f));
+    return fabsf(y) < 0.1f ? series : direct;
+}
+
+// Three Hodgkin-Huxley neurons (paper Eq. 6-11), state (V, m, h, n, s) per
+// neuron, all-to-all synapses; rates of Hodgkin & Huxley 1952, rest near -65 mV.
+struct HH3 {
+    static constexpr int DIM = 15;
+    static constexpr int NP = 16;
+    __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
+        const float C = p[0], gNa = p[1], gK = p[2], gL = p[3];
+        const float ENa = p[4], EK = p[5], EL = p[6], gsyn = p[7], Esyn = p[8];
+        const float inv_tr = __fdividef(1.0f, p[12]), inv_td = __fdividef(1.0f, p[13]);
+        const float sig2 = p[14] * kLog2e, theta = p[15];
+        const float invC = __fdividef(1.0f, C);
+        const float s_sum = x[4] + x[9] + x[14];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float V = x[5 * i], m = x[5 * i + 1], h = x[5 * i + 2], n = x[5 * i + 3];
+            const float s = x[5 * i + 4];
+            const float u = V + 65.0f;
+            const float am = 0.1f * hh_vtrap(V + 40.0f);
+            const float bm = 4.0f * exp2f(u * (-kLog2e / 18.0f));
+            const float ah = 0.07f * exp2f(u * (-kLog2e / 20.0f));
+            const float bh = __fdividef(1.0f, 1.0f + exp2f((V + 35.0f) * (-kLog2e / 10.0f)));
+            const float an = 0.01f * hh_vtrap(V + 55.0f);
+            const float bn = 0.125f * exp2f(u * (-kLog2e / 80.0f));
+            const float m3h = m * m * m * h;
+            const float n2 = n * n;
+            const float n4 = n2 * n2;
+            const float others = s_sum - s;
+            float I = gL * (EL - V);
+            I = fmaf(gNa * m3h, ENa - V, I);
+            I = fmaf(gK * n4, EK - V, I);
+            I = fmaf(gsyn * others, Esyn - V, I);
+            I = I + p[9 + i];
+            dx[5 * i] = I * invC;
+            dx[5 * i + 1] = fmaf(am, 1.0f - m, -bm * m);
+            dx[5 * i + 2] = fmaf(ah, 1.0f - h, -bh * h);
+            dx[5 * i + 3] = fmaf(an, 1.0f - n, -bn * n);
+            const float act = __fdividef(1.0f, 1.0f + exp2f(sig2 * (theta - V)));
+            dx[5 * i + 4] = fmaf(act * inv_tr, 1.0f - s, -s * inv_td);
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Steppers.  acc() returns the stage-weighted sum a and its scale sc so that
+// the step is x += sc * a; the update (plain or compensated) is applied by the
+// kernel.  RK4: k1 = f(x), k2 = f(x + h/2 k1), k3 = f(x + h/2 k2),
+// k4 = f(x + h k3), a = k1 + 2 k2 + 2 k3 + k4, sc = h/6.  Euler: a = f(x), sc = h.
+// ---------------------------------------------------------------------------
+
+template <class R>
+struct GenericRK4 {
+    static constexpr int D = R::DIM;
+    float h1, h2, h6;
+    const float* p;
+    __device__ __forceinline__ void init(float h, const float* prm) {
+        h1 = h;
+        h2 = 0.5f * h;
+        h6 = h * (1.0f / 6.0f);
+        p = prm;
+    }
+    __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
+        float k[D], xs[D];
+        R::f(x, p, k);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { a[i] = k[i]; xs[i] = fmaf(h2, k[i], x[i]); }
+        R::f(xs, p, k);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { a[i] = fmaf(2.0f, k[i], a[i]); xs[i] = fmaf(h2, k[i], x[i]); }
+        R::f(xs, p, k);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { a[i] = fmaf(2.0f, k[i], a[i]); xs[i] = fmaf(h1, k[i], x[i]); }
+        R::f(xs, p, k);
+#pragma unroll
+        for (int i = 0; i < D; ++i) { a[i] = a[i] + k[i]; sc[i] = h6; }
+    }
+};
+
+template <class R>
+struct GenericEuler {
+    static constexpr int D = R::DIM;
+    float h1;
+    const float* p;
+    __device__ __forceinline__ void init(float h, const float* prm) { h1 = h; p = prm; }
+    __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
+        R::f(x, p, a);
+#pragma unroll
+        for (int i = 0; i < D; ++i) sc[i] = h1;
+    }
+};
+
+// RK4 on Lorenz with sigma folded into the x-component's stage and final
+// scales: with d = y - x, k_x = sigma d, so x + c h k_x = x + (c h sigma) d and
+// the x-part of the weighted sum is carried in units of d.  Same arithmetic
+// as the generic stepper up to rounding, 41 instead of 45 FP32 instructions.
+struct LorenzRK4 {
+    static constexpr int D = 3;
+    float h1, h2, h6, sh1, sh2, sh6, r, b;
+    __device__ __forceinline__ void init(float h, const float* prm) {
+        const float s = prm[0];
+        r = prm[1];
+        b = prm[2];
+        h1 = h;
+        h2 = 0.5f * h;
+        h6 = h * (1.0f / 6.0f);
+        sh1 = s * h1;
+        sh2 = s * h2;
+        sh6 = s * h6;
+    }
+    __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
+        float d, ky, kz, X, Y, Z;
+        // stage 1
+        d = x[1] - x[0];
+        ky = fmaf(x[0], r - x[2], -x[1]);
+        kz = fmaf(x[0], x[1], -(b * x[2]));
+        a[0] = d; a[1] = ky; a[2] = kz;
+        X = fmaf(sh2, d, x[0]); Y = fmaf(h2, ky, x[1]); Z = fmaf(h2, kz, x[2]);
+        // stage 2
+        d = Y - X;
+        ky = fmaf(X, r - Z, -Y);
+        kz = fmaf(X, Y, -(b * Z));
+        a[0] = fmaf(2.0f, d, a[0]); a[1] = fmaf(2.0f, ky, a[1]); a[2] = fmaf(2.0f, kz, a[2]);
+        X = fmaf(sh2, d, x[0]); Y = fmaf(h2, ky, x[1]); Z = fmaf(h2, kz, x[2]);
+        // stage 3
+        d = Y - X;
+        ky = fmaf(X, r - Z, -Y);
+        kz = fmaf(X, Y, -(b * Z));
+        a[0] = fmaf(2.0f, d, a[0]); a[1] = fmaf(2.0f, ky, a[1]); a[2] = fmaf(2.0f, kz, a[2]);
+        X = fmaf(sh1, d, x[0]); Y = fmaf(h1, ky, x[1]); Z = fmaf(h1, kz, x[2]);
+        // stage 4
+        d = Y - X;
+        ky = fmaf(X, r - Z, -Y);
+        kz = fmaf(X, Y, -(b * Z));
+        a[0] = a[0] + d; a[1] = a[1] + ky; a[2] = a[2] + kz;
+        sc[0] = sh6; sc[1] = h6; sc[2] = h6;
+    }
+};
+
+template <class R, int METHOD> struct StepperFor { using type = GenericRK4<R>; };
+template <class R> struct StepperFor<R, FF_EULER> { using type = GenericEuler<R>; };
+template <> struct StepperFor<Lorenz, FF_RK4> { using type = LorenzRK4; };
+
+// ---------------------------------------------------------------------------
+// Vector access of PPT consecutive floats.
+// ---------------------------------------------------------------------------
+template <int PPT> struct Vec;
+template <> struct Vec<1> {
+    __device__ __forceinline__ static void load(const float* p, float (&v)[1]) { v[0] = __ldcs(p); }
+    __device__ __forceinline__ static void store(float* p, const float (&v)[1]) { __stcs(p, v[0]); }
+};
+template <> struct Vec<2> {
+    __device__ __forceinline__ static void load(const float* p, float (&v)[2]) {
+        float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+        v[0] = t.x; v[1] = t.y;
+    }
+    __device__ __forceinline__ static void store(float* p, const float (&v)[2]) {
+        __stcs(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+    }
+};
+template <> struct Vec<4> {
+    __device__ __forceinline__ static void load(const float* p, float (&v)[4]) {
+        float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ __forceinline__ static void store(float* p, const float (&v)[4]) {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// The persistent integrator.  Grid-stride over work items of PPT consecutive
+// particles; each work item loads its state once, runs n_steps steps with the
+// state in registers and stores it once.
+// ---------------------------------------------------------------------------
+template <class R, int METHOD, bool KAHAN, bool PP, int PPT>
+__global__ void __launch_bounds__(1024) integrate_kernel(const __grid_constant__ IntegrateArgs a) {
+    constexpr int D = R::DIM;
+    using Stepper = typename StepperFor<R, METHOD>::type;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_vec; t += stride) {
+        const int64_t i0 = t * PPT;
+        float x[PPT][D];
+        float c[PPT][D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            float v[PPT], w[PPT];
+            if (k < a.dim) {
+                Vec<PPT>::load(a.x + k * a.pitch + i0, v);
+                if (KAHAN) Vec<PPT>::load(a.comp + k * a.pitch + i0, w);
+            } else {
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) { v[j] = 0.f; w[j] = 0.f; }
+            }
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                x[j][k] = v[j];
+                c[j][k] = KAHAN ? w[j] : 0.f;
+            }
+        }
+        float prm[PPT][R::NP];
+        Stepper st[PPT];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const int64_t i = i0 + j;
+            float h = a.gh[0];
+#pragma unroll
+            for (int g = 1; g < FF_MAX_GROUPS; ++g)
+                if (g < a.n_groups && i >= a.gstart[g]) h = a.gh[g];
+            float pv = 0.f;
+            if (PP) pv = a.pparam[i];
+#pragma unroll
+            for (int q = 0; q < R::NP; ++q) prm[j][q] = (PP && q == a.pidx) ? pv : a.p[q];
+            st[j].init(h, prm[j]);
+        }
+#pragma unroll 2
+        for (int64_t s = 0; s < a.n_steps; ++s) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                float acc[D], sc[D];
+                st[j].acc(x[j], acc, sc);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    if (KAHAN) {
+                        const float y = fmaf(sc[k], acc[k], -c[j][k]);
+                        const float tt = __fadd_rn(x[j][k], y);
+                        c[j][k] = __fsub_rn(__fsub_rn(tt, x[j][k]), y);
+                        x[j][k] = tt;
+                    } else {
+                        x[j][k] = fmaf(sc[k], acc[k], x[j][k]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (k < a.dim) {
+                float v[PPT], w[PPT];
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) { v[j] = x[j][k]; w[j] = c[j][k]; }
+                Vec<PPT>::store(a.x + k * a.pitch + i0, v);
+                if (KAHAN) Vec<PPT>::store(a.comp + k * a.pitch + i0, w);
+            }
+        }
+    }
+}
+
+// Host-side launch of one integrator variant (defined per system in its own
+// translation unit so the variants compile in parallel).
+struct LaunchShape {
+    int ppt;
+    int block;
+    int blocks_per_sm;  // 0 = occupancy limit
+    int num_sms;
+};
+
+cudaError_t launch_integrate(int rhs_id, int method, bool kahan, bool pp, const IntegrateArgs& a,
+                             const LaunchShape& shape, cudaStream_t stream);
+cudaError_t launch_integrate_lorenz(int method, bool kahan, bool pp, const IntegrateArgs& a,
+                                    const LaunchShape& shape, cudaStream_t stream);
+cudaError_t launch_integrate_wc(int method, bool kahan, bool pp, const IntegrateArgs& a,
+                                const LaunchShape& shape, cudaStream_t stream);
+cudaError_t launch_integrate_hh3(int method, bool kahan, bool pp, const IntegrateArgs& a,
+                                 const LaunchShape& shape, cudaStream_t stream);
+cudaError_t launch_integrate_linear(int rhs_id, int method, bool kahan, bool pp,
+                                    const IntegrateArgs& a, const LaunchShape& shape,
+                                    cudaStream_t stream);
+
+// Grid for a persistent launch: enough blocks to cover the work, at most
+// blocks_per_sm (or the occupancy limit) per SM.
+template <class Kernel>
+inline cudaError_t persistent_launch(Kernel kernel, const IntegrateArgs& a, const LaunchShape& s,
+                                     cudaStream_t stream) {
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, s.block, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int per_sm = (s.blocks_per_sm > 0 && s.blocks_per_sm < occ) ? s.blocks_per_sm : occ;
+    const int64_t need = (a.n_vec + s.block - 1) / s.block;
+    const int64_t cap = (int64_t)per_sm * s.num_sms;
+    const int grid = (int)(need < cap ? need : cap);
+    if (grid < 1) return cudaSuccess;
+    kernel<<<grid, s.block, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+// Dispatch over (method, Kahan, per-particle parameter, particles per thread).
+template <class R, int METHOD, bool KAHAN, bool PP>
+inline cudaError_t launch_ppt(const IntegrateArgs& a, const LaunchShape& s, cudaStream_t st) {
+    if constexpr (R::DIM <= 4) {
+        switch (s.ppt) {
+        case 1: return persistent_launch(integrate_kernel<R, METHOD, KAHAN, PP, 1>, a, s, st);
+        case 2: return persistent_launch(integrate_kernel<R, METHOD, KAHAN, PP, 2>, a, s, st);
+        case 4: return persistent_launch(integrate_kernel<R, METHOD, KAHAN, PP, 4>, a, s, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    else {
+        if (s.ppt != 1) return cudaErrorInvalidValue;
+        return persistent_launch(integrate_kernel<R, METHOD, KAHAN, PP, 1>, a, s, st);
+    }
+}
+
+template <class R>
+inline cudaError_t launch_variants(int method, bool kahan, bool pp, const IntegrateArgs& a,
+                                   const LaunchShape& s, cudaStream_t st) {
+    if (method == FF_RK4) {
+        if (kahan) return pp ? launch_ppt<R, FF_RK4, true, true>(a, s, st) : launch_ppt<R, FF_RK4, true, false>(a, s, st);
+        return pp ? launch_ppt<R, FF_RK4, false, true>(a, s, st) : launch_ppt<R, FF_RK4, false, false>(a, s, st);
+    }
+    if (kahan) return pp ? launch_ppt<R, FF_EULER, true, true>(a, s, st) : launch_ppt<R, FF_EULER, true, false>(a, s, st);
+    return pp ? launch_ppt<R, FF_EULER, false, true>(a, s, st) : launch_ppt<R, FF_EULER, false, false>(a, s, st);
+}
+
+}  // namespace ff

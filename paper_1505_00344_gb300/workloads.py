@@ -88,7 +88,7 @@ def _wc_4k():
         groups=[dict(count=2048, direction=+1, seed=group_seed(0, 0), **box),
                 dict(count=2048, direction=-1, seed=group_seed(0, 1), **box)],
         dt=0.01, steps_per_frame=1000, frames=1,
-        view=dict(ndim=2, axes=(0, 1), lo=(0.0, 0.0), hi=(1.0, 1.0), width=256, height=256),
+        view=dict(ndim_view=2, axes=(0, 1), lo=(0.0, 0.0), hi=(1.0, 1.0), width=256, height=256),
     )
 
 
@@ -98,8 +98,8 @@ def _lorenz_4M():
         name="lorenz_4M", index=1, rhs="lorenz", dim=3, params=list(LORENZ_PARAMS), method="rk4",
         groups=[dict(count=3145728, direction=+1, seed=group_seed(1, 0), **box),
                 dict(count=1048576, direction=-1, seed=group_seed(1, 1), **box)],
-        dt=0.001, steps_per_frame=200, frames=100,
-        view=dict(ndim=2, axes=(0, 2), lo=(-30.0, 0.0), hi=(30.0, 60.0), width=1920, height=1080),
+        dt=0.001, steps_per_frame=200, frames=100, splat_every_frame=True,
+        view=dict(ndim_view=2, axes=(0, 2), lo=(-30.0, 0.0), hi=(30.0, 60.0), width=1920, height=1080),
     )
 
 
@@ -114,7 +114,7 @@ def _lorenz_bif_8M():
         # parameter changes applied before the given frame: beta -> 2.0 after 10,000 steps
         schedule={1: [10.0, 28.0, 2.0]},
         # axis 3 (== dim) is the per-particle parameter r
-        view=dict(ndim=2, axes=(3, 2), lo=(0.0, 0.0), hi=(200.0, 400.0), width=2048, height=1024),
+        view=dict(ndim_view=2, axes=(3, 2), lo=(0.0, 0.0), hi=(200.0, 400.0), width=2048, height=1024),
     )
 
 
@@ -130,7 +130,7 @@ def _hh3_1M():
         name="hh3_1M", index=3, rhs="hh3", dim=15, params=hh3_params(), method="rk4",
         groups=[dict(count=1048576, direction=+1, seed=group_seed(3, 0), lo=lo, hi=hi)],
         dt=0.01, steps_per_frame=50000, frames=1,
-        view=dict(ndim=3, axes=(0, 5, 10), mvp=mvp, width=1024, height=1024),
+        view=dict(ndim_view=3, axes=(0, 5, 10), mvp=mvp, width=1024, height=1024),
     )
 
 

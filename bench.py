@@ -47,14 +47,27 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lorenz_4M")
-    ap.add_argument("--ppt", type=int, default=1)
-    ap.add_argument("--block", type=int, default=256)
+    # launch shape (default: the library's default for the system)
+    ap.add_argument("--ppt", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--kahan", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    # profiling cases only (a line taken with these is not the workload's number)
+    ap.add_argument("--particles", type=int, default=0, help="scale the workload to this many particles")
+    ap.add_argument("--frames", type=int, default=0, help="run only this many frames per step")
     return ap.parse_args()
+
+
+def workload_for(args, rank, world):
+    w = W.shard(W.workload(args.workload), rank, world)
+    if args.particles:
+        w = W.scaled(w, args.particles)
+    if args.frames:
+        w = dict(w, frames=args.frames)
+    return w
 
 
 def dist_env():
@@ -163,12 +176,13 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream().cuda_stream
-    w = W.shard(W.workload(args.workload), rank, world)
+    w = workload_for(args, rank, world)
     P = total_particles(w)
     view = ff.make_view(**w["view"])
     H, Wd = w["view"]["height"], w["view"]["width"]
     sysobj = ff.System.from_workload(w, kahan=args.kahan, stream=stream)
-    sysobj.set_launch(args.ppt, args.block, args.blocks_per_sm, 0)
+    if args.ppt or args.block or args.blocks_per_sm:
+        sysobj.set_launch(args.ppt or 1, args.block or 256, args.blocks_per_sm, 0)
     image = torch.zeros((H, Wd), dtype=torch.int32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > 129 MB L2
     every = w.get("splat_every_frame", False)
@@ -250,7 +264,7 @@ def run_ours(args, rank, world, local):
         roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / peak_tflops, 4),
                 "traffic": traffic_from_profile(kernel_source_hash()),
-                "kernel": "integrate_kernel<Lorenz,RK4>",
+                "kernel": "lorenz_rk4_x2_kernel" if (args.ppt or 4) in (2, 4) and not args.kahan else "integrate_kernel<Lorenz,RK4>",
                 "peak_basis": f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
                 "algorithmic_bytes_per_launch": 24 * n_work,
                 "avg_launch_ms": round(avg_int_ms, 4)}
@@ -265,8 +279,10 @@ def run_ours(args, rank, world, local):
             {"count": g["count"], "direction": g["direction"]} for g in w["groups"]],
             "rk4_steps_per_job": steps_per_job, "frames": w["frames"], "steps_per_frame": w["steps_per_frame"],
             "dt": w["dt"], "image": f"{Wd}x{H}", "kahan": bool(args.kahan),
+            "profiling_case": bool(args.particles or args.frames),
             "l2": "flushed (256 MB write) before every timed step", "parallelism": "dp%d-weak-shards" % world,
-            "launch": {"particles_per_thread": args.ppt, "block": args.block, "blocks_per_sm": args.blocks_per_sm}},
+            "launch": {"particles_per_thread": args.ppt or "library default", "block": args.block or "library default",
+                       "blocks_per_sm": args.blocks_per_sm}},
         "frames_per_s": w["frames"] / (ms_per_step / 1e3),
         "gpu_launches": launches,
         "wall_s_timed_region": wall,

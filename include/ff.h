@@ -201,11 +201,14 @@ ff_status ff_stats(ff_system* sys, int64_t* n_escaped, double* t_fwd, double* t_
 ff_status ff_system_info(ff_system* sys, int64_t* n_particles, int64_t* pitch, int* dim,
                          int* n_groups);
 
-/* Launch shape of the integrator: particles per thread (1, 2 or 4; 16-byte
- * SoA loads at 4), threads per block (a multiple of 32, 32..1024), resident
- * blocks per SM used for the persistent grid (0 = as many as fit), and the
- * most steps per launch (0 = all steps of an ff_step call in one launch).
- * Errors: FF_ERR_INVALID_ARG for values out of range. */
+/* Launch shape of the integrator: particles per thread (1, 2 or 4; at 2 and 4
+ * each plane is read with one 8- or 16-byte access, and plain RK4 on Lorenz
+ * then runs two particles per packed f32x2 instruction), threads per block (a
+ * multiple of 32 up to 1024; clamped to the kernel's maximum, 512 for the 2-
+ * and 3-dimensional systems and 256 for LINEAR and HH3), resident blocks per
+ * SM of the persistent grid (0 = as many as fit), and the most steps per
+ * launch (0 = all steps of an ff_step call in one launch; launches are also
+ * split at 2^30 steps).  Errors: FF_ERR_INVALID_ARG for values out of range. */
 ff_status ff_set_launch(ff_system* sys, int particles_per_thread, int block, int blocks_per_sm,
                         int64_t max_steps_per_launch);
 

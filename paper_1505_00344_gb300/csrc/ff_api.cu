@@ -182,8 +182,9 @@ ff_status ff_create_system(int rhs_id, int dim, const double* params, int n_para
         ff_destroy_system(s);
         return st;
     }
-    // defaults: one particle per thread for the big systems, two for 2-3 dimensional ones
-    s->ppt = 1;
+    // default launch shape: plain RK4 on Lorenz runs packed pairs, 4 particles per thread
+    s->ppt = (rhs_id == FF_RHS_LORENZ && method == FF_RK4 && !(flags & FF_FLAG_KAHAN)) ? 4 : 1;
+    s->block = 256;
     *out = s;
     return FF_OK;
 }
@@ -374,7 +375,8 @@ ff_status ff_step(ff_system* s, int64_t n_steps, double dt) {
     const bool pp = s->pparam_index >= 0;
     int64_t left = n_steps;
     while (left > 0) {
-        const int64_t chunk = (s->max_steps > 0 && left > s->max_steps) ? s->max_steps : left;
+        int64_t chunk = (s->max_steps > 0 && left > s->max_steps) ? s->max_steps : left;
+        if (chunk > ((int64_t)1 << 30)) chunk = (int64_t)1 << 30;  // kernels count steps in 32 bits
         a.n_steps = chunk;
         cudaError_t e = ff::launch_integrate(s->rhs_id, s->method, kahan, pp, a, shape, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "integrator launch");

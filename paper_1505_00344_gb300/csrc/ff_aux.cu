@@ -175,7 +175,8 @@ __global__ void escape_count_kernel(const float* x, int64_t pitch, int dim, int6
     unsigned long long mine = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         bool esc = false;
-        for (int k = 0; k < dim; ++k) esc |= !(fabsf(x[k * pitch + i]) <= 1e30f);
+        // compared in double (float -> double is exact), the same test as for FP64 states
+        for (int k = 0; k < dim; ++k) esc |= !((double)fabsf(x[k * pitch + i]) <= 1e30);
         mine += esc ? 1ull : 0ull;
     }
     // warp sum, then one atomic per warp

@@ -47,6 +47,7 @@ struct IntegrateArgs {
 struct Linear {
     static constexpr int DIM = 8;
     static constexpr int NP = 64;
+    static constexpr int MAX_BLOCK = 256;  // room for 64 parameters in registers
     __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
@@ -62,6 +63,7 @@ struct Linear {
 struct Harmonic {
     static constexpr int DIM = 2;
     static constexpr int NP = 1;
+    static constexpr int MAX_BLOCK = 512;
     __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
         dx[0] = x[1];
         dx[1] = -(p[0] * p[0]) * x[0];
@@ -74,6 +76,7 @@ struct Harmonic {
 struct WilsonCowan {
     static constexpr int DIM = 2;
     static constexpr int NP = 10;
+    static constexpr int MAX_BLOCK = 512;
     __device__ __forceinline__ static float S(float a, float g2, float g2th) {
         // exp(-gain (a - th)) = 2^(g2 th - g2 a) with g2 = gain * log2(e)
         float e = exp2f(fmaf(-g2, a, g2th));
@@ -93,6 +96,7 @@ struct WilsonCowan {
 struct Lorenz {
     static constexpr int DIM = 3;
     static constexpr int NP = 3;
+    static constexpr int MAX_BLOCK = 512;
     __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
         dx[0] = p[0] * (x[1] - x[0]);
         dx[1] = fmaf(x[0], p[1] - x[2], -x[1]);
@@ -117,6 +121,7 @@ __device__ __forceinline__ float hh_vtrap(float v) {
 struct HH3 {
     static constexpr int DIM = 15;
     static constexpr int NP = 16;
+    static constexpr int MAX_BLOCK = 256;  // 15-dimensional state, stages and rates in registers
     __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
         const float C = p[0], gNa = p[1], gK = p[2], gL = p[3];
         const float ENa = p[4], EK = p[5], EL = p[6], gsyn = p[7], Esyn = p[8];
@@ -172,6 +177,8 @@ struct GenericRK4 {
         h6 = h * (1.0f / 6.0f);
         p = prm;
     }
+    __device__ __forceinline__ void to_internal(float (&)[D]) const {}
+    __device__ __forceinline__ void from_internal(float (&)[D]) const {}
     __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
         float k[D], xs[D];
         R::f(x, p, k);
@@ -195,6 +202,8 @@ struct GenericEuler {
     float h1;
     const float* p;
     __device__ __forceinline__ void init(float h, const float* prm) { h1 = h; p = prm; }
+    __device__ __forceinline__ void to_internal(float (&)[D]) const {}
+    __device__ __forceinline__ void from_internal(float (&)[D]) const {}
     __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
         R::f(x, p, a);
 #pragma unroll
@@ -220,6 +229,8 @@ struct LorenzRK4 {
         sh2 = s * h2;
         sh6 = s * h6;
     }
+    __device__ __forceinline__ void to_internal(float (&)[D]) const {}
+    __device__ __forceinline__ void from_internal(float (&)[D]) const {}
     __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
         float d, ky, kz, X, Y, Z;
         // stage 1
@@ -249,9 +260,63 @@ struct LorenzRK4 {
     }
 };
 
-template <class R, int METHOD> struct StepperFor { using type = GenericRK4<R>; };
-template <class R> struct StepperFor<R, FF_EULER> { using type = GenericEuler<R>; };
-template <> struct StepperFor<Lorenz, FF_RK4> { using type = LorenzRK4; };
+// RK4 on Lorenz in the shifted variable zt = z - r.  RK4 commutes with affine
+// changes of variables, so this is the same map as the unshifted step up to
+// rounding; in zt the RHS reads  dx = sigma d,  dy = -(x zt + y),
+// dzt = x y - beta zt - beta r, which saves the (r - z) subtraction: 37 FP32
+// instructions per step (negations are free operand modifiers).  The shift is
+// applied once per launch on load and undone on store.
+struct LorenzRK4Shift {
+    static constexpr int D = 3;
+    float h1, h2, h6, sh1, sh2, sh6, r, nb, nbr;
+    __device__ __forceinline__ void init(float h, const float* prm) {
+        const float s = prm[0];
+        r = prm[1];
+        nb = -prm[2];
+        nbr = nb * r;
+        h1 = h;
+        h2 = 0.5f * h;
+        h6 = h * (1.0f / 6.0f);
+        sh1 = s * h1;
+        sh2 = s * h2;
+        sh6 = s * h6;
+    }
+    __device__ __forceinline__ void to_internal(float (&x)[D]) const { x[2] = x[2] - r; }
+    __device__ __forceinline__ void from_internal(float (&x)[D]) const { x[2] = x[2] + r; }
+    __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
+        float d, A, kz, X, Y, Z;
+        // stage 1 (A = -k_y)
+        d = x[1] - x[0];
+        A = fmaf(x[0], x[2], x[1]);
+        kz = fmaf(x[0], x[1], fmaf(nb, x[2], nbr));
+        a[0] = d; a[1] = A; a[2] = kz;
+        X = fmaf(sh2, d, x[0]); Y = fmaf(-h2, A, x[1]); Z = fmaf(h2, kz, x[2]);
+        // stage 2
+        d = Y - X;
+        A = fmaf(X, Z, Y);
+        kz = fmaf(X, Y, fmaf(nb, Z, nbr));
+        a[0] = fmaf(2.0f, d, a[0]); a[1] = fmaf(2.0f, A, a[1]); a[2] = fmaf(2.0f, kz, a[2]);
+        X = fmaf(sh2, d, x[0]); Y = fmaf(-h2, A, x[1]); Z = fmaf(h2, kz, x[2]);
+        // stage 3
+        d = Y - X;
+        A = fmaf(X, Z, Y);
+        kz = fmaf(X, Y, fmaf(nb, Z, nbr));
+        a[0] = fmaf(2.0f, d, a[0]); a[1] = fmaf(2.0f, A, a[1]); a[2] = fmaf(2.0f, kz, a[2]);
+        X = fmaf(sh1, d, x[0]); Y = fmaf(-h1, A, x[1]); Z = fmaf(h1, kz, x[2]);
+        // stage 4
+        d = Y - X;
+        A = fmaf(X, Z, Y);
+        kz = fmaf(X, Y, fmaf(nb, Z, nbr));
+        a[0] = a[0] + d; a[1] = a[1] + A; a[2] = a[2] + kz;
+        sc[0] = sh6; sc[1] = -h6; sc[2] = h6;
+    }
+};
+
+template <class R, int METHOD, bool KAHAN> struct StepperFor { using type = GenericRK4<R>; };
+template <class R, bool KAHAN> struct StepperFor<R, FF_EULER, KAHAN> { using type = GenericEuler<R>; };
+// the compensated variant keeps z unshifted so that no rounding escapes the compensation
+template <> struct StepperFor<Lorenz, FF_RK4, true> { using type = LorenzRK4; };
+template <> struct StepperFor<Lorenz, FF_RK4, false> { using type = LorenzRK4Shift; };
 
 // ---------------------------------------------------------------------------
 // Vector access of PPT consecutive floats.
@@ -286,9 +351,9 @@ template <> struct Vec<4> {
 // state in registers and stores it once.
 // ---------------------------------------------------------------------------
 template <class R, int METHOD, bool KAHAN, bool PP, int PPT>
-__global__ void __launch_bounds__(1024) integrate_kernel(const __grid_constant__ IntegrateArgs a) {
+__global__ void __launch_bounds__(R::MAX_BLOCK) integrate_kernel(const __grid_constant__ IntegrateArgs a) {
     constexpr int D = R::DIM;
-    using Stepper = typename StepperFor<R, METHOD>::type;
+    using Stepper = typename StepperFor<R, METHOD, KAHAN>::type;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_vec; t += stride) {
         const int64_t i0 = t * PPT;
@@ -324,9 +389,11 @@ __global__ void __launch_bounds__(1024) integrate_kernel(const __grid_constant__
 #pragma unroll
             for (int q = 0; q < R::NP; ++q) prm[j][q] = (PP && q == a.pidx) ? pv : a.p[q];
             st[j].init(h, prm[j]);
+            st[j].to_internal(x[j]);
         }
-#pragma unroll 2
-        for (int64_t s = 0; s < a.n_steps; ++s) {
+        const int n_steps = (int)a.n_steps;  // the host splits launches at 2^30 steps
+#pragma unroll 4
+        for (int s = 0; s < n_steps; ++s) {
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
                 float acc[D], sc[D];
@@ -345,6 +412,8 @@ __global__ void __launch_bounds__(1024) integrate_kernel(const __grid_constant__
             }
         }
 #pragma unroll
+        for (int j = 0; j < PPT; ++j) st[j].from_internal(x[j]);
+#pragma unroll
         for (int k = 0; k < D; ++k) {
             if (k < a.dim) {
                 float v[PPT], w[PPT];
@@ -354,6 +423,141 @@ __global__ void __launch_bounds__(1024) integrate_kernel(const __grid_constant__
                 if (KAHAN) Vec<PPT>::store(a.comp + k * a.pitch + i0, w);
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Packed-pair RK4 for Lorenz.  Blackwell executes two FP32 lanes per thread
+// with one add/sub/mul/fma.rn.f32x2 instruction, which halves the issue slots
+// the 37 FP32 operations of a step need, so the step is bound by the FP32
+// pipes rather than by instruction issue.  Each f32x2 register holds the same
+// quantity of two consecutive particles.  The arithmetic is the shifted step
+// above (zt = z - r); the f32x2 forms have no operand negation, so the
+// negated step sizes of the y-component are kept as constants.
+// ---------------------------------------------------------------------------
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 pack2(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f2 p, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(p.v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+struct LorenzPairConsts {
+    f2 h1, h2, h6, nh1, nh2, nh6, sh1, sh2, sh6, nb, nbr;
+};
+
+__device__ __forceinline__ void lorenz_rk4_pair(f2& x, f2& y, f2& z, const LorenzPairConsts& c, f2 two) {
+    f2 d, A, kz, X, Y, Z, ad, aA, az;
+    // stage 1 (A = -k_y, z is the shifted zt)
+    d = sub2(y, x);
+    A = fma2(x, z, y);
+    kz = fma2(x, y, fma2(c.nb, z, c.nbr));
+    ad = d; aA = A; az = kz;
+    X = fma2(c.sh2, d, x); Y = fma2(c.nh2, A, y); Z = fma2(c.h2, kz, z);
+    // stage 2
+    d = sub2(Y, X);
+    A = fma2(X, Z, Y);
+    kz = fma2(X, Y, fma2(c.nb, Z, c.nbr));
+    ad = fma2(two, d, ad); aA = fma2(two, A, aA); az = fma2(two, kz, az);
+    X = fma2(c.sh2, d, x); Y = fma2(c.nh2, A, y); Z = fma2(c.h2, kz, z);
+    // stage 3
+    d = sub2(Y, X);
+    A = fma2(X, Z, Y);
+    kz = fma2(X, Y, fma2(c.nb, Z, c.nbr));
+    ad = fma2(two, d, ad); aA = fma2(two, A, aA); az = fma2(two, kz, az);
+    X = fma2(c.sh1, d, x); Y = fma2(c.nh1, A, y); Z = fma2(c.h1, kz, z);
+    // stage 4
+    d = sub2(Y, X);
+    A = fma2(X, Z, Y);
+    kz = fma2(X, Y, fma2(c.nb, Z, c.nbr));
+    ad = add2(ad, d); aA = add2(aA, A); az = add2(az, kz);
+    x = fma2(c.sh6, ad, x); y = fma2(c.nh6, aA, y); z = fma2(c.h6, az, z);
+}
+
+template <bool PP, int NPAIR>
+__global__ void __launch_bounds__(512) lorenz_rk4_x2_kernel(const __grid_constant__ IntegrateArgs a) {
+    constexpr int PPT = 2 * NPAIR;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const f2 two = pack2(2.0f, 2.0f);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_vec; t += stride) {
+        const int64_t i0 = t * PPT;
+        float xs[PPT], ys[PPT], zs[PPT];
+        Vec<PPT>::load(a.x + i0, xs);
+        Vec<PPT>::load(a.x + a.pitch + i0, ys);
+        Vec<PPT>::load(a.x + 2 * a.pitch + i0, zs);
+        float h[PPT], sg[PPT], r[PPT], b[PPT];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const int64_t i = i0 + j;
+            h[j] = a.gh[0];
+#pragma unroll
+            for (int g = 1; g < FF_MAX_GROUPS; ++g)
+                if (g < a.n_groups && i >= a.gstart[g]) h[j] = a.gh[g];
+            const float pv = PP ? a.pparam[i] : 0.0f;
+            sg[j] = (PP && a.pidx == 0) ? pv : a.p[0];
+            r[j] = (PP && a.pidx == 1) ? pv : a.p[1];
+            b[j] = (PP && a.pidx == 2) ? pv : a.p[2];
+        }
+        f2 X[NPAIR], Y[NPAIR], Z[NPAIR];
+        LorenzPairConsts c[NPAIR];
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            const int u = 2 * q, v = 2 * q + 1;
+            X[q] = pack2(xs[u], xs[v]);
+            Y[q] = pack2(ys[u], ys[v]);
+            Z[q] = pack2(zs[u] - r[u], zs[v] - r[v]);
+            const float h2u = 0.5f * h[u], h2v = 0.5f * h[v];
+            const float h6u = h[u] * (1.0f / 6.0f), h6v = h[v] * (1.0f / 6.0f);
+            c[q].h1 = pack2(h[u], h[v]);
+            c[q].h2 = pack2(h2u, h2v);
+            c[q].h6 = pack2(h6u, h6v);
+            c[q].nh1 = pack2(-h[u], -h[v]);
+            c[q].nh2 = pack2(-h2u, -h2v);
+            c[q].nh6 = pack2(-h6u, -h6v);
+            c[q].sh1 = pack2(sg[u] * h[u], sg[v] * h[v]);
+            c[q].sh2 = pack2(sg[u] * h2u, sg[v] * h2v);
+            c[q].sh6 = pack2(sg[u] * h6u, sg[v] * h6v);
+            c[q].nb = pack2(-b[u], -b[v]);
+            c[q].nbr = pack2(-b[u] * r[u], -b[v] * r[v]);
+        }
+        const int n_steps = (int)a.n_steps;
+#pragma unroll 2
+        for (int s = 0; s < n_steps; ++s) {
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) lorenz_rk4_pair(X[q], Y[q], Z[q], c[q], two);
+        }
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            const int u = 2 * q, v = 2 * q + 1;
+            unpack2(X[q], xs[u], xs[v]);
+            unpack2(Y[q], ys[u], ys[v]);
+            unpack2(Z[q], zs[u], zs[v]);
+            zs[u] = zs[u] + r[u];
+            zs[v] = zs[v] + r[v];
+        }
+        Vec<PPT>::store(a.x + i0, xs);
+        Vec<PPT>::store(a.x + a.pitch + i0, ys);
+        Vec<PPT>::store(a.x + 2 * a.pitch + i0, zs);
     }
 }
 
@@ -379,12 +583,18 @@ cudaError_t launch_integrate_linear(int rhs_id, int method, bool kahan, bool pp,
                                     cudaStream_t stream);
 
 // Grid for a persistent launch: enough blocks to cover the work, at most
-// blocks_per_sm (or the occupancy limit) per SM.
+// blocks_per_sm (or the occupancy limit) per SM.  The block size is clamped to
+// the kernel's compiled maximum (its launch bound).
 template <class Kernel>
-inline cudaError_t persistent_launch(Kernel kernel, const IntegrateArgs& a, const LaunchShape& s,
+inline cudaError_t persistent_launch(Kernel kernel, const IntegrateArgs& a, const LaunchShape& s0,
                                      cudaStream_t stream) {
+    LaunchShape s = s0;
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, kernel);
+    if (e != cudaSuccess) return e;
+    if (s.block > attr.maxThreadsPerBlock) s.block = attr.maxThreadsPerBlock / 32 * 32;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, s.block, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, s.block, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int per_sm = (s.blocks_per_sm > 0 && s.blocks_per_sm < occ) ? s.blocks_per_sm : occ;

@@ -217,6 +217,43 @@ ff_status ff_set_launch(ff_system* sys, int particles_per_thread, int block, int
 ff_status ff_backward(ff_system* sys, const float* dL_dxT_dev, float* dL_dx0_dev,
                       double* dL_dp_host);
 
+/* Most groups ff_count_escaped_noalloc accepts (its fixed scratch holds one
+ * 64-bit counter per group: 2 KB per GPU). */
+#define FF_NOALLOC_MAX_GROUPS 256
+
+/* Count escaped particles per group without allocating any memory.  The paper
+ * has no counterpart: this serves callers that may not allocate device memory
+ * when they ask, e.g. a plugin handed device buffers by a host application
+ * that owns the whole memory budget, a render loop that cannot afford the
+ * device synchronisation cudaMalloc may imply, or code whose memory comes
+ * from a fixed pool sized up front.
+ *   state_dev     SoA state on the device, plane k at state_dev + k * pitch
+ *                 (any device buffer, e.g. one filled by ff_get_state).
+ *   dim, n_particles, pitch   planes, particles, floats between planes.
+ *   group_starts  host array of n_groups non-decreasing first indices,
+ *                 group_starts[0] == 0; group g covers [starts[g],
+ *                 starts[g+1]) and the last group ends at n_particles.
+ *   n_groups      1 .. FF_NOALLOC_MAX_GROUPS.
+ *   cuda_stream   stream for the work (NULL = legacy default stream).
+ *   counts_out    host array of n_groups int64: escaped particles per group,
+ *                 with the escape test of ff_stats (a component non-finite or
+ *                 above 1e30 in magnitude).
+ * The call synchronises the stream before returning.  It calls no
+ * cudaMalloc or cudaFree: its only scratch is a fixed device array of
+ * FF_NOALLOC_MAX_GROUPS counters in the library, present on every GPU that
+ * loads the library until the process exits.  The first call on each device
+ * looks up that array's device address (cudaGetSymbolAddress), so make the
+ * first call on a device before any stream capture.  All calls on a device
+ * share the array and each clears the counters it uses: calls that overlap on
+ * the GPU (concurrent streams or threads) race and give wrong counts.
+ * Errors: FF_ERR_INVALID_ARG for NULL pointers, dim outside 1..FF_MAX_DIM,
+ * n_particles < 0, pitch < n_particles, n_groups outside
+ * 1..FF_NOALLOC_MAX_GROUPS, or badly ordered group_starts; FF_ERR_CUDA if a
+ * CUDA call fails. */
+ff_status ff_count_escaped_noalloc(const float* state_dev, int dim, int64_t n_particles, int64_t pitch,
+                                   const int64_t* group_starts, int n_groups, void* cuda_stream,
+                                   int64_t* counts_out);
+
 /* Message describing the last error returned on the calling thread. */
 const char* ff_last_error(void);
 

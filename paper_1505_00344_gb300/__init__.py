@@ -67,6 +67,7 @@ _SIGS = {
                        ctypes.POINTER(ctypes.c_int)],
     "ff_set_launch": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64],
     "ff_backward": [_P, _P, _P, _P],
+    "ff_count_escaped_noalloc": [_P, ctypes.c_int, _I64, _I64, _P, ctypes.c_int, _P, _P],
 }
 
 
@@ -240,6 +241,26 @@ def ff_backward(sys, dL_dxT, dL_dx0, dL_dp):
     b, _, _kb = _buf(dL_dx0)
     c, _, _kc = _buf(dL_dp, np.float64)
     _check(lib().ff_backward(sys, a, b, c))
+
+
+FF_NOALLOC_MAX_GROUPS = 256
+
+
+def ff_count_escaped_noalloc(state, dim, n_particles, pitch, group_starts, stream=None):
+    """Escaped particles per group of a device SoA state, without any device allocation.
+
+    For callers that must not allocate device memory at call time (see
+    include/ff.h); ``state`` is a device buffer (tensor or pointer), the
+    result a host int64 array with one count per group.
+    """
+    ptr, dev, _keep = _buf(state)
+    if not dev:
+        raise ValueError("state must be device memory")
+    starts = np.ascontiguousarray(np.asarray(group_starts, dtype=np.int64).reshape(-1))
+    counts = np.zeros(starts.size, dtype=np.int64)
+    _check(lib().ff_count_escaped_noalloc(ptr, int(dim), int(n_particles), int(pitch), starts.ctypes.data,
+                                          starts.size, _stream_ptr(stream), counts.ctypes.data))
+    return counts
 
 
 def ff_last_error():

@@ -529,6 +529,9 @@ ff_status ff_backward(ff_system* s, const float* dL_dxT_dev, float* dL_dx0_dev, 
 }  // extern "C"
 
 namespace ff {
+// Lets entry points defined in other translation units report through ff_last_error().
+void set_last_error_message(const char* msg) { g_last_error = msg; }
+
 cudaError_t launch_integrate(int rhs_id, int method, bool kahan, bool pp, const IntegrateArgs& a,
                              const LaunchShape& shape, cudaStream_t stream) {
     switch (rhs_id) {

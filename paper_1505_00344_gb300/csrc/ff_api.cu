@@ -361,13 +361,14 @@ ff_status ff_step(ff_system* s, int64_t n_steps, double dt) {
     a.dim = s->dim;
     a.n_groups = s->n_groups;
     a.pidx = s->pparam_index >= 0 ? kernel_param_index(s, s->pparam_index) : -1;
+    // all processed particles are a multiple of 4 (<= pitch): every vector access stays in bounds
+    const int64_t n_work = (s->n_particles + 3) / 4 * 4;
     for (int g = 0; g < s->n_groups; ++g) {
         a.gstart[g] = s->groups[g].start;
+        a.gend[g] = (g + 1 < s->n_groups) ? s->groups[g + 1].start : n_work;
         a.gh[g] = (float)(s->groups[g].direction * dt);
     }
     for (int q = 0; q < s->n_params; ++q) a.p[kernel_param_index(s, q)] = (float)s->params[q];
-    // all processed particles are a multiple of 4 (<= pitch): every vector access stays in bounds
-    const int64_t n_work = (s->n_particles + 3) / 4 * 4;
     const int ppt = s->ppt;
     a.n_vec = n_work / ppt;
     ff::LaunchShape shape{ppt, s->block, s->blocks_per_sm, s->num_sms};

@@ -34,6 +34,8 @@ struct IntegrateArgs {
     int64_t gstart[FF_MAX_GROUPS];  // first particle of each group
     float gh[FF_MAX_GROUPS];        // signed step of each group
     float p[FF_MAX_PARAMS];         // system parameters (FP32)
+    int64_t gend[FF_MAX_GROUPS];    // one past the last processed particle of each group
+    int gblk[FF_MAX_GROUPS + 1];    // group-uniform kernels: first block of each group (prefix)
 };
 
 // ---------------------------------------------------------------------------
@@ -554,6 +556,80 @@ __global__ void __launch_bounds__(512) lorenz_rk4_x2_kernel(const __grid_constan
             unpack2(Z[q], zs[u], zs[v]);
             zs[u] = zs[u] + r[u];
             zs[v] = zs[v] + r[v];
+        }
+        Vec<PPT>::store(a.x + i0, xs);
+        Vec<PPT>::store(a.x + a.pitch + i0, ys);
+        Vec<PPT>::store(a.x + 2 * a.pitch + i0, zs);
+    }
+}
+
+// Group-uniform variant of the packed kernel.  Blocks are dealt out to the
+// groups in proportion to their sizes (gblk), so a block's group -- and with
+// it the step sizes and the sigma/beta constants -- is the same for every
+// thread of the block; those constants are computed once per block from the
+// argument block instead of living in per-thread registers, which leaves room
+// for more resident warps.  Used when every group starts on a multiple of the
+// particles per thread and a per-particle parameter, if any, is r.
+template <bool PP_R, int NPAIR>
+__global__ void __launch_bounds__(512) lorenz_rk4_x2u_kernel(const __grid_constant__ IntegrateArgs a) {
+    constexpr int PPT = 2 * NPAIR;
+    int g = 0;
+#pragma unroll
+    for (int q = 1; q < FF_MAX_GROUPS; ++q)
+        if (q < a.n_groups && (int)blockIdx.x >= a.gblk[q]) g = q;
+    const int64_t nb = a.gblk[g + 1] - a.gblk[g];
+    const int64_t first = a.gstart[g] / PPT, last = a.gend[g] / PPT;
+    const float h = a.gh[g], sg = a.p[0], b = a.p[2];
+    const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
+    LorenzPairConsts c;
+    c.h1 = pack2(h, h);
+    c.h2 = pack2(h2, h2);
+    c.h6 = pack2(h6, h6);
+    c.nh1 = pack2(-h, -h);
+    c.nh2 = pack2(-h2, -h2);
+    c.nh6 = pack2(-h6, -h6);
+    c.sh1 = pack2(sg * h, sg * h);
+    c.sh2 = pack2(sg * h2, sg * h2);
+    c.sh6 = pack2(sg * h6, sg * h6);
+    c.nb = pack2(-b, -b);
+    const float nbr_sys = -b * a.p[1];
+    const f2 two = pack2(2.0f, 2.0f);
+    const int64_t stride = nb * blockDim.x;
+    for (int64_t t = first + (int64_t)(blockIdx.x - a.gblk[g]) * blockDim.x + threadIdx.x; t < last; t += stride) {
+        const int64_t i0 = t * PPT;
+        float xs[PPT], ys[PPT], zs[PPT], r[PPT];
+        Vec<PPT>::load(a.x + i0, xs);
+        Vec<PPT>::load(a.x + a.pitch + i0, ys);
+        Vec<PPT>::load(a.x + 2 * a.pitch + i0, zs);
+        if (PP_R) Vec<PPT>::load(a.pparam + i0, r);
+        f2 X[NPAIR], Y[NPAIR], Z[NPAIR], NBR[NPAIR];
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            const int u = 2 * q, v = 2 * q + 1;
+            const float ru = PP_R ? r[u] : a.p[1], rv = PP_R ? r[v] : a.p[1];
+            X[q] = pack2(xs[u], xs[v]);
+            Y[q] = pack2(ys[u], ys[v]);
+            Z[q] = pack2(zs[u] - ru, zs[v] - rv);
+            NBR[q] = PP_R ? pack2(-b * ru, -b * rv) : pack2(nbr_sys, nbr_sys);
+        }
+        const int n_steps = (int)a.n_steps;
+#pragma unroll 2
+        for (int s = 0; s < n_steps; ++s) {
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) {
+                LorenzPairConsts cq = c;
+                cq.nbr = NBR[q];
+                lorenz_rk4_pair(X[q], Y[q], Z[q], cq, two);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            const int u = 2 * q, v = 2 * q + 1;
+            unpack2(X[q], xs[u], xs[v]);
+            unpack2(Y[q], ys[u], ys[v]);
+            unpack2(Z[q], zs[u], zs[v]);
+            zs[u] = zs[u] + (PP_R ? r[u] : a.p[1]);
+            zs[v] = zs[v] + (PP_R ? r[v] : a.p[1]);
         }
         Vec<PPT>::store(a.x + i0, xs);
         Vec<PPT>::store(a.x + a.pitch + i0, ys);

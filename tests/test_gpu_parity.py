@@ -190,6 +190,24 @@ def test_integrate_parity_vector_width(name, ppt, kahan):
     check_parity(ff.RHS_BY_NAME[rhs], got, want, oracle_seed(groups, dim), params, oracle_h(groups, dt), 100)
 
 
+@pytest.mark.parametrize("ppt", [2, 4])
+@pytest.mark.parametrize("r_per_particle", [False, True])
+def test_lorenz_group_uniform_kernel(ppt, r_per_particle):
+    # every group starts on a multiple of 4: the group-uniform packed kernel runs
+    counts = (4096, 1024, 12, 4, 2000)
+    groups = [G(c, *LZ_BOX, 1 if t % 2 == 0 else -1, 70 + t) for t, c in enumerate(counts)]
+    P = sum(counts)
+    s = make_system("lorenz", LORENZ_PARAMS, groups, 3, ppt=ppt)
+    kw = {}
+    if r_per_particle:
+        s.set_particle_param(1, 0.0, 60.0)
+        kw = dict(pparam_index=1, pparam=oracle.linspace_param(P, 0.0, 60.0).astype(np.float64))
+    s.step(100, 0.001)
+    x0 = oracle_seed(groups, 3)
+    want = oracle.integrate(oracle.LORENZ, x0, LORENZ_PARAMS, oracle_h(groups, 0.001), 100, **kw)
+    check_parity(oracle.LORENZ, get_state(s), want, x0, LORENZ_PARAMS, oracle_h(groups, 0.001), 100, **kw)
+
+
 @pytest.mark.parametrize("ppt", [1, 2, 4])
 @pytest.mark.parametrize("sigma_per_particle", [False, True])
 def test_lorenz_other_per_particle_params(ppt, sigma_per_particle):

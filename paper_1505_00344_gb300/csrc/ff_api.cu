@@ -90,6 +90,7 @@ struct ff_system {
     float* d_comp = nullptr;
     float* d_pparam = nullptr;
     int pparam_index = -1;
+    bool pparam_linspace = false;  // values monotone in the particle index
     int n_groups = 0;
     Group groups[FF_MAX_GROUPS] = {};
     bool stepped = false;
@@ -281,6 +282,7 @@ ff_status ff_set_particle_param(ff_system* s, int param_index, double lo, double
     cudaError_t e = ff::launch_linspace(s->d_pparam, s->n_particles, lo, hi, s->num_sms, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "linspace kernel launch");
     s->pparam_index = param_index;
+    s->pparam_linspace = true;
     return FF_OK;
 }
 
@@ -301,6 +303,7 @@ ff_status ff_set_particle_param_values(ff_system* s, int param_index, const floa
     if (e == cudaSuccess && !values_is_device) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "ff_set_particle_param_values: copy");
     s->pparam_index = param_index;
+    s->pparam_linspace = false;
     return FF_OK;
 }
 
@@ -454,8 +457,10 @@ ff_status ff_project_splat(ff_system* s, const ff_view* v, uint32_t* image, int 
     if (e == cudaSuccess && !v->accumulate) e = cudaMemsetAsync(target, 0, bytes, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "ff_project_splat: image clear/upload");
     a.image = target;
+    bool strip = false;  // a linspace parameter on an axis: consecutive particles share a column or row
+    for (int q = 0; q < v->ndim_view; ++q) strip = strip || (v->axes[q] == s->dim && s->pparam_linspace);
     if (s->n_particles > 0 && a.mask != 0) {
-        e = ff::launch_splat(a, v->ndim_view, masked, s->num_sms, s->stream);
+        e = ff::launch_splat(a, v->ndim_view, masked, strip, s->num_sms, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "splat kernel launch");
     }
     if (!image_is_device) {

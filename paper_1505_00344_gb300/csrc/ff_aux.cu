@@ -51,30 +51,32 @@ __global__ void linspace_kernel(float* out, int64_t P, double lo, double width) 
 // operation is rounded on its own (explicit _rn intrinsics, no contraction)
 // so the pixel decision is reproducible bit for bit.
 // ---------------------------------------------------------------------------
+// Pixel (column fc, row fr as floats) of one projected particle; false if it
+// is not drawn.
 template <int NDV>
-__device__ __forceinline__ int pixel_of(const SplatArgs& a, int64_t i) {
+__device__ __forceinline__ bool pixel_of(const SplatArgs& a, float u, float v, float w, int& col, int& row) {
     float fc, fr;
     if (NDV == 2) {
-        const float u = a.ax[0][i], v = a.ax[1][i];
         fc = floorf(__fmul_rn(__fsub_rn(u, a.lo0), a.s0));
         fr = floorf(__fmul_rn(__fsub_rn(v, a.lo1), a.s1));
     } else {
-        const float x = a.ax[0][i], y = a.ax[1][i], z = a.ax[2][i];
         float cl[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float s = __fadd_rn(__fmul_rn(a.m[j], x), __fmul_rn(a.m[4 + j], y));
-            s = __fadd_rn(s, __fmul_rn(a.m[8 + j], z));
-            cl[j] = __fadd_rn(s, a.m[12 + j]);
+            float t = __fadd_rn(__fmul_rn(a.m[j], u), __fmul_rn(a.m[4 + j], v));
+            t = __fadd_rn(t, __fmul_rn(a.m[8 + j], w));
+            cl[j] = __fadd_rn(t, a.m[12 + j]);
         }
-        if (!(cl[3] > 0.0f)) return -1;
+        if (!(cl[3] > 0.0f)) return false;
         const float nx = __fdiv_rn(cl[0], cl[3]);
         const float ny = __fdiv_rn(cl[1], cl[3]);
         fc = floorf(__fmul_rn(__fsub_rn(nx, -1.0f), a.s0));
         fr = floorf(__fmul_rn(__fsub_rn(ny, -1.0f), a.s1));
     }
-    if (!(fc >= 0.0f && fc < a.Wf && fr >= 0.0f && fr < a.Hf)) return -1;
-    return (int)fr * a.W + (int)fc;
+    if (!(fc >= 0.0f && fc < a.Wf && fr >= 0.0f && fr < a.Hf)) return false;
+    col = (int)fc;
+    row = (int)fr;
+    return true;
 }
 
 __device__ __forceinline__ bool group_selected(const SplatArgs& a, int64_t i) {
@@ -85,80 +87,94 @@ __device__ __forceinline__ bool group_selected(const SplatArgs& a, int64_t i) {
     return (a.mask >> g) & 1u;
 }
 
-// Each block takes chunks of kSplatChunk consecutive particles.  If the
-// chunk's pixels fit a small bounding box (e.g. a bifurcation diagram, where
-// consecutive particles share a parameter column) they are counted in a
-// shared-memory histogram first and each touched bin is flushed with one
-// global atomic; otherwise every warp merges equal pixels (match.any) and one
-// lane per distinct pixel issues the global atomic.
+// Global mode: each thread projects 4 consecutive particles (one 16-byte load
+// per plane) and adds one count per drawn particle with a fire-and-forget
+// global reduction; the image is small enough to stay in L2.
 template <int NDV, bool MASKED>
-__global__ void __launch_bounds__(kSplatBlock) splat_kernel(const __grid_constant__ SplatArgs a) {
+__global__ void __launch_bounds__(kSplatBlock) splat_global_kernel(const __grid_constant__ SplatArgs a) {
+    const int64_t n4 = (a.n + 3) / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += stride) {
+        const int64_t i0 = 4 * t;
+        const float4 u4 = __ldcs(reinterpret_cast<const float4*>(a.ax[0] + i0));
+        const float4 v4 = __ldcs(reinterpret_cast<const float4*>(a.ax[1] + i0));
+        float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (NDV == 3) w4 = __ldcs(reinterpret_cast<const float4*>(a.ax[2] + i0));
+        const float u[4] = {u4.x, u4.y, u4.z, u4.w}, v[4] = {v4.x, v4.y, v4.z, v4.w},
+                    w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t i = i0 + j;
+            int col, row;
+            if (i < a.n && (!MASKED || group_selected(a, i)) && pixel_of<NDV>(a, u[j], v[j], w[j], col, row))
+                atomicAdd(&a.image[(int64_t)row * a.W + col], 1u);
+        }
+    }
+}
+
+// Shared mode, for views where consecutive particles land in a narrow strip of
+// the image (a linspace parameter on one axis: the bifurcation diagram).
+// Each block takes chunks of kSplatChunk consecutive particles, finds their
+// bounding box, counts them in a shared-memory histogram when the box fits and
+// flushes every touched bin with one global atomic; a chunk whose box does not
+// fit adds its counts directly.
+template <int NDV, bool MASKED>
+__global__ void __launch_bounds__(kSplatBlock) splat_shared_kernel(const __grid_constant__ SplatArgs a) {
     __shared__ uint32_t bins[kSplatBins];
     __shared__ int box[4];  // min col, max col, min row, max row
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
     for (int64_t base = (int64_t)blockIdx.x * kSplatChunk; base < a.n;
          base += (int64_t)gridDim.x * kSplatChunk) {
         if (tid == 0) { box[0] = INT32_MAX; box[1] = -1; box[2] = INT32_MAX; box[3] = -1; }
         __syncthreads();
-        int pix[kSplatPerThread];
+        int cols[kSplatPerThread], rows[kSplatPerThread];
         int cmin = INT32_MAX, cmax = -1, rmin = INT32_MAX, rmax = -1;
 #pragma unroll
         for (int q = 0; q < kSplatPerThread; ++q) {
             const int64_t i = base + (int64_t)q * kSplatBlock + tid;
-            int p = -1;
-            if (i < a.n && (!MASKED || group_selected(a, i))) p = pixel_of<NDV>(a, i);
-            pix[q] = p;
-            if (p >= 0) {
-                const int r = p / a.W, c = p - r * a.W;
-                cmin = min(cmin, c); cmax = max(cmax, c);
-                rmin = min(rmin, r); rmax = max(rmax, r);
+            int col = -1, row = -1;
+            if (i < a.n && (!MASKED || group_selected(a, i))) {
+                const float w = NDV == 3 ? a.ax[2][i] : 0.0f;
+                if (!pixel_of<NDV>(a, a.ax[0][i], a.ax[1][i], w, col, row)) col = -1;
+            }
+            cols[q] = col;
+            rows[q] = row;
+            if (col >= 0) {
+                cmin = min(cmin, col); cmax = max(cmax, col);
+                rmin = min(rmin, row); rmax = max(rmax, row);
             }
         }
         cmin = __reduce_min_sync(0xffffffffu, cmin);
         cmax = __reduce_max_sync(0xffffffffu, cmax);
         rmin = __reduce_min_sync(0xffffffffu, rmin);
         rmax = __reduce_max_sync(0xffffffffu, rmax);
-        if (lane == 0 && cmax >= 0) {
+        if ((tid & 31) == 0 && cmax >= 0) {
             atomicMin(&box[0], cmin); atomicMax(&box[1], cmax);
             atomicMin(&box[2], rmin); atomicMax(&box[3], rmax);
         }
         __syncthreads();
         const int bc0 = box[0], bc1 = box[1], br0 = box[2], br1 = box[3];
-        if (bc1 < 0) {  // nothing drawn in this chunk
-            __syncthreads();
-            continue;
-        }
-        const int bw = bc1 - bc0 + 1, bh = br1 - br0 + 1;
-        if ((int64_t)bw * bh <= kSplatBins) {
-            const int area = bw * bh;
-            for (int b = tid; b < area; b += kSplatBlock) bins[b] = 0u;
-            __syncthreads();
+        if (bc1 >= 0) {
+            const int bw = bc1 - bc0 + 1, bh = br1 - br0 + 1;
+            if ((int64_t)bw * bh <= kSplatBins) {
+                const int area = bw * bh;
+                for (int b = tid; b < area; b += kSplatBlock) bins[b] = 0u;
+                __syncthreads();
 #pragma unroll
-            for (int q = 0; q < kSplatPerThread; ++q) {
-                const int p = pix[q];
-                if (p >= 0) {
-                    const int r = p / a.W, c = p - r * a.W;
-                    atomicAdd(&bins[(r - br0) * bw + (c - bc0)], 1u);
+                for (int q = 0; q < kSplatPerThread; ++q)
+                    if (cols[q] >= 0) atomicAdd(&bins[(rows[q] - br0) * bw + (cols[q] - bc0)], 1u);
+                __syncthreads();
+                for (int b = tid; b < area; b += kSplatBlock) {
+                    const uint32_t v = bins[b];
+                    if (v) {
+                        const int r = b / bw;
+                        atomicAdd(&a.image[(int64_t)(br0 + r) * a.W + bc0 + (b - r * bw)], v);
+                    }
                 }
-            }
-            __syncthreads();
-            for (int b = tid; b < area; b += kSplatBlock) {
-                const uint32_t v = bins[b];
-                if (v) {
-                    const int r = br0 + b / bw, c = bc0 + b % bw;
-                    atomicAdd(&a.image[(int64_t)r * a.W + c], v);
-                }
-            }
-        } else {
+            } else {
 #pragma unroll
-            for (int q = 0; q < kSplatPerThread; ++q) {
-                const int p = pix[q];
-                const unsigned drawn = __ballot_sync(0xffffffffu, p >= 0);
-                if (p >= 0) {
-                    const unsigned peers = __match_any_sync(drawn, p);
-                    if (lane == __ffs(peers) - 1) atomicAdd(&a.image[p], (uint32_t)__popc(peers));
-                }
+                for (int q = 0; q < kSplatPerThread; ++q)
+                    if (cols[q] >= 0) atomicAdd(&a.image[(int64_t)rows[q] * a.W + cols[q]], 1u);
             }
         }
         __syncthreads();
@@ -207,18 +223,29 @@ cudaError_t launch_linspace(float* out, int64_t P, double lo, double hi, int num
     return cudaGetLastError();
 }
 
-cudaError_t launch_splat(const SplatArgs& a, int ndim_view, bool masked, int num_sms,
+cudaError_t launch_splat(const SplatArgs& a, int ndim_view, bool masked, bool strip, int num_sms,
                          cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    const int64_t chunks = (a.n + kSplatChunk - 1) / kSplatChunk;
-    const int64_t cap = (int64_t)num_sms * 8;
-    const int grid = (int)(chunks < cap ? chunks : cap);
+    if (strip) {
+        const int64_t chunks = (a.n + kSplatChunk - 1) / kSplatChunk;
+        const int64_t cap = (int64_t)num_sms * 8;
+        const int grid = (int)(chunks < cap ? chunks : cap);
+        if (ndim_view == 2) {
+            if (masked) splat_shared_kernel<2, true><<<grid, kSplatBlock, 0, s>>>(a);
+            else splat_shared_kernel<2, false><<<grid, kSplatBlock, 0, s>>>(a);
+        } else {
+            if (masked) splat_shared_kernel<3, true><<<grid, kSplatBlock, 0, s>>>(a);
+            else splat_shared_kernel<3, false><<<grid, kSplatBlock, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
+    const int grid = grid_for((a.n + 3) / 4, kSplatBlock, num_sms, 8);
     if (ndim_view == 2) {
-        if (masked) splat_kernel<2, true><<<grid, kSplatBlock, 0, s>>>(a);
-        else splat_kernel<2, false><<<grid, kSplatBlock, 0, s>>>(a);
+        if (masked) splat_global_kernel<2, true><<<grid, kSplatBlock, 0, s>>>(a);
+        else splat_global_kernel<2, false><<<grid, kSplatBlock, 0, s>>>(a);
     } else {
-        if (masked) splat_kernel<3, true><<<grid, kSplatBlock, 0, s>>>(a);
-        else splat_kernel<3, false><<<grid, kSplatBlock, 0, s>>>(a);
+        if (masked) splat_global_kernel<3, true><<<grid, kSplatBlock, 0, s>>>(a);
+        else splat_global_kernel<3, false><<<grid, kSplatBlock, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -26,7 +26,7 @@ constexpr int kSplatChunk = kSplatBlock * kSplatPerThread;
 constexpr int kSplatBins = 8192;  // 32 KB shared-memory histogram
 
 struct SplatArgs {
-    const float* ax[3];  // planes of the view axes
+    const float* ax[3];  // planes of the view axes (16-byte aligned; readable up to n rounded to 4)
     int64_t n;           // particles
     uint32_t* image;
     int W, H;
@@ -41,7 +41,9 @@ struct SplatArgs {
 cudaError_t launch_seed(const SeedArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_linspace(float* out, int64_t P, double lo, double hi, int num_sms,
                             cudaStream_t s);
-cudaError_t launch_splat(const SplatArgs& a, int ndim_view, bool masked, int num_sms,
+// strip: consecutive particles map to a narrow strip of the image (a linspace
+// per-particle parameter on a view axis), so the shared-memory histogram pays.
+cudaError_t launch_splat(const SplatArgs& a, int ndim_view, bool masked, bool strip, int num_sms,
                          cudaStream_t s);
 cudaError_t launch_escape_count(const float* x, int64_t pitch, int dim, int64_t n,
                                 unsigned long long* counter, int num_sms, cudaStream_t s);

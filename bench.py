@@ -77,6 +77,17 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def total_particles(w):
     return sum(g["count"] for g in w["groups"])
 
@@ -242,12 +253,7 @@ def run_ours(args, rank, world, local):
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
 
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
     steps_per_job = total_steps(w)
     value = world * P * steps_per_job / (ms_per_step / 1e3)
@@ -341,12 +347,7 @@ def e2e_ours(args, sysobj, w, view, image, P, world, dev):
         job()
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
-    t = statistics.mean(times)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(statistics.mean(times), dev)
     return {"value": world * P * total_steps(w) / t, "unit": UNIT, "h2d_bytes_per_step": 4 * dim * P,
             "d2h_bytes_per_step": 4 * H * Wd, "steps": len(times)}
 

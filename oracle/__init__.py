@@ -59,6 +59,10 @@ def _load():
         lib.ffo_integrate.restype = ctypes.c_int
         lib.ffo_integrate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, P, P,
                                       ctypes.c_int, ctypes.c_int, P, P, i64]
+        lib.ffo_integrate_reset.restype = ctypes.c_int
+        lib.ffo_integrate_reset.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, P, P, ctypes.c_int,
+                                            ctypes.c_int, P, P, i64, i64, ctypes.c_int, P, P, ctypes.c_uint32,
+                                            P, P, P, P, P, P, P]
         lib.ffo_count_escaped.restype = i64
         lib.ffo_count_escaped.argtypes = [ctypes.c_int, i64, i64, P, P]
         lib.ffo_splat2d.restype = None
@@ -175,6 +179,41 @@ def integrate_parallel(rhs_id, state, params, h, n_steps, method=RK4, pparam_ind
     if any(rcs):
         raise ValueError("ffo_integrate: bad arguments")
     return st, threads
+
+
+def integrate_reset(rhs_id, state, params, groups, dt, n_steps, step0=0, check_every=1, bounds=None,
+                    max_age=0, age=None, resets=None, method=RK4, pparam_index=-1, pparam=None):
+    """Integrate with the paper's particle reset (see ffo_integrate_reset).
+
+    ``groups``: list of dicts with count, lo, hi, direction, seed (in particle order);
+    ``bounds``: (lo[dim], hi[dim]) of the valid state box, or None.  Returns
+    (state, age, resets); age/resets start from the given arrays (zeros by default).
+    """
+    st = np.array(state, dtype=np.float64, order="C", copy=True)
+    dim, P = st.shape
+    j = np.concatenate([np.arange(g["count"], dtype=np.int64) for g in groups])
+    cnt = np.concatenate([np.full(g["count"], g["count"], np.int64) for g in groups])
+    sd = np.concatenate([np.full(g["count"], g["seed"] & (2**64 - 1), np.uint64) for g in groups])
+    lo = np.ascontiguousarray(np.concatenate([np.repeat(np.asarray(g["lo"], np.float64)[:, None], g["count"], 1)
+                                              for g in groups], axis=1))
+    hi = np.ascontiguousarray(np.concatenate([np.repeat(np.asarray(g["hi"], np.float64)[:, None], g["count"], 1)
+                                              for g in groups], axis=1))
+    h = np.concatenate([np.full(g["count"], g["direction"] * dt) for g in groups])
+    age = np.zeros(P, np.uint32) if age is None else np.array(age, np.uint32)
+    resets = np.zeros(P, np.uint32) if resets is None else np.array(resets, np.uint32)
+    blo = bhi = None
+    if bounds is not None:
+        blo = np.asarray(bounds[0], np.float32)
+        bhi = np.asarray(bounds[1], np.float32)
+    p = _c(params, np.float64)
+    pp = None if pparam is None else _c(pparam, np.float64)
+    rc = _load().ffo_integrate_reset(rhs_id, method, dim, P, _ptr(st), _ptr(p), p.size, pparam_index, _ptr(pp),
+                                     _ptr(h), int(n_steps), int(step0), int(check_every), _ptr(blo), _ptr(bhi),
+                                     int(max_age), _ptr(j), _ptr(cnt), _ptr(sd), _ptr(lo), _ptr(hi), _ptr(age),
+                                     _ptr(resets))
+    if rc != 0:
+        raise ValueError("ffo_integrate_reset: bad arguments")
+    return st, age, resets
 
 
 def count_escaped(state):

@@ -299,6 +299,71 @@ int ffo_integrate(int rhs_id, int method, int dim, int64_t P, int64_t pitch,
     return 0;
 }
 
+/* Integration with the paper's particle reset (Sec. 2.1: trajectories that
+ * leave the box of valid states, or that have not been reset for more than
+ * T_max, get new random initial conditions; Appendix A: state-variable bounds,
+ * group initial-condition boxes).  The paper resets on the CPU, a batch per
+ * frame; here the rule is applied every check_every steps:
+ *   after each step the particle's age grows by one step; at global step
+ *   numbers (step0 + s + 1) that are multiples of check_every, a particle whose
+ *   state, rounded to float (the state array's precision), lies outside
+ *   [blo_k, bhi_k] for some k (or is not finite), or whose age has reached
+ *   max_age steps (max_age > 0), is re-drawn from its group's box: its r-th
+ *   reset (r = resets + 1) uses draws n = (r * count + j) * dim + k + 1 of the
+ *   group's SplitMix64 stream (j its index in the group, count the group's
+ *   size), i.e. the blocks after the one used for its initial conditions;
+ *   then age = 0 and resets = r.
+ * blo/bhi may be NULL (no bounds).  Per particle: j[i], count[i], seed[i],
+ * box lo/hi in lo[k * P + i], hi[k * P + i].  age/resets are updated in place.
+ * Returns 0, or -1 on a bad argument. */
+int ffo_integrate_reset(int rhs_id, int method, int dim, int64_t P, double *state,
+                        const double *params, int n_params, int pparam_index, const double *pparam,
+                        const double *h, int64_t n_steps, int64_t step0, int check_every,
+                        const float *blo, const float *bhi, uint32_t max_age,
+                        const int64_t *j, const int64_t *count, const uint64_t *seed,
+                        const double *lo, const double *hi, uint32_t *age, uint32_t *resets)
+{
+    if (!rhs_dim_ok(rhs_id, dim, n_params)) return -1;
+    if (method != FFO_RK4 && method != FFO_EULER) return -1;
+    if (pparam_index >= n_params || (pparam_index >= 0 && !pparam)) return -1;
+    if (n_steps < 0 || check_every < 1 || step0 < 0) return -1;
+    if (n_params > 64) return -1;
+    double p[64];
+    for (int64_t i = 0; i < P; ++i) {
+        double x[FFO_MAXD];
+        for (int k = 0; k < dim; ++k) x[k] = state[(int64_t)k * P + i];
+        memcpy(p, params, sizeof(double) * (size_t)n_params);
+        if (pparam_index >= 0) p[pparam_index] = pparam[i];
+        for (int64_t s = 0; s < n_steps; ++s) {
+            if (method == FFO_RK4) rk4_step(rhs_id, dim, x, p, h[i]);
+            else euler_step(rhs_id, dim, x, p, h[i]);
+            age[i] += 1u;
+            if ((step0 + s + 1) % check_every != 0) continue;
+            int out = 0;
+            if (blo && bhi) {
+                for (int k = 0; k < dim; ++k) {
+                    float xf = (float)x[k];
+                    if (!(xf >= blo[k] && xf <= bhi[k])) out = 1;
+                }
+            }
+            if (max_age > 0 && age[i] >= max_age) out = 1;
+            if (!out) continue;
+            uint32_t r = resets[i] + 1u;
+            for (int k = 0; k < dim; ++k) {
+                uint64_t n = ((uint64_t)r * (uint64_t)count[i] + (uint64_t)j[i]) * (uint64_t)dim + (uint64_t)k + 1u;
+                uint64_t z = ffo_splitmix64(seed[i], n);
+                double u = (double)(z >> 40) * (1.0 / 16777216.0);
+                double width = hi[(int64_t)k * P + i] - lo[(int64_t)k * P + i];
+                x[k] = (double)(float)(lo[(int64_t)k * P + i] + width * u);
+            }
+            age[i] = 0u;
+            resets[i] = r;
+        }
+        for (int k = 0; k < dim; ++k) state[(int64_t)k * P + i] = x[k];
+    }
+    return 0;
+}
+
 /* Escaped particle: some component is not finite or exceeds 1e30 in
  * magnitude.  flags[i] (optional) receives 1 for escaped particles. */
 int64_t ffo_count_escaped(int dim, int64_t P, int64_t pitch, const double *state, uint8_t *flags)

@@ -49,6 +49,12 @@ MUTANTS = {
     "mvp_row_major": ("float a = m[0 + j] * x[i];", "float a = m[4 * j] * x[i];"),
     "rows_top_down": ("image[(int64_t)r * W + (int64_t)c] += 1u;\n    }\n}\n\n/* 3D",
                       "image[(int64_t)(H - 1 - (int)r) * W + (int64_t)c] += 1u;\n    }\n}\n\n/* 3D"),
+    "reset_counter_block": ("uint64_t n = ((uint64_t)r * (uint64_t)count[i] + (uint64_t)j[i])",
+                            "uint64_t n = ((uint64_t)(r - 1u) * (uint64_t)count[i] + (uint64_t)j[i])"),
+    "reset_age_kept": ("            age[i] = 0u;\n            resets[i] = r;", "            resets[i] = r;"),
+    "reset_schedule": ("if ((step0 + s + 1) % check_every != 0) continue;", "if ((step0 + s) % check_every != 0) continue;"),
+    "reset_bound_strict": ("if (!(xf >= blo[k] && xf <= bhi[k])) out = 1;", "if (!(xf > blo[k] && xf < bhi[k])) out = 1;"),
+    "reset_age_limit": ("if (max_age > 0 && age[i] >= max_age) out = 1;", "if (max_age > 0 && age[i] > max_age) out = 1;"),
     "escape_threshold": ("if (!(fabs(v) <= 1e30)) esc = 1;", "if (!(fabs(v) < 1e38)) esc = 1;"),
 }
 

@@ -158,6 +158,33 @@ ff_status ff_set_particle_param_values(ff_system* sys, int param_index, const fl
  * parameter was ever set. */
 ff_status ff_get_particle_param(ff_system* sys, float* dst, int dst_is_device, int* param_index_out);
 
+/* Particle reset (paper Sec. 2.1 and Appendix A: a trajectory that leaves the
+ * bounds of any state variable, or has not been reset for more than T_max, is
+ * given new random initial conditions from its group's box).  The paper does
+ * this on the CPU a batch per frame; here the integrator does it in-kernel:
+ * after each step a particle's age grows by one step, and at global step
+ * numbers (steps since the last ff_reset, counted over all ff_step calls) that
+ * are multiples of check_every, a particle whose float state lies outside
+ * [bound_lo[k], bound_hi[k]] for some k (or is not finite), or whose age has
+ * reached ceil(t_max / |dt|) steps, is re-drawn: its r-th reset takes draws
+ * n = (r * count + j) * dim + k + 1 of its group's SplitMix64 stream (j its
+ * index in the group, count the group's size) -- the blocks after its
+ * initial-condition draws -- and its age restarts at 0.
+ *   bound_lo/bound_hi: dim values each (rounded to float), or both NULL for no
+ *   bounds; t_max <= 0: no age limit; check_every >= 1 enables the reset,
+ *   0 disables it.  Ages and reset counts start at 0 and are cleared by ff_reset
+ *   and ff_set_state.  Resetting particles run the scalar integrator (one
+ *   particle per thread).
+ * Errors: FF_ERR_INVALID_ARG for check_every < 0, only one of the bounds
+ * given, non-finite or inverted bounds, non-finite t_max; FF_ERR_OOM. */
+ff_status ff_set_reset(ff_system* sys, const double* bound_lo, const double* bound_hi, double t_max,
+                       int check_every);
+
+/* Copy per-particle ages (steps since the last reset) and reset counts out (P
+ * uint32 each, host or device; either may be NULL; a host copy synchronises).
+ * Errors: FF_ERR_STATE if the reset was never enabled. */
+ff_status ff_get_reset_state(ff_system* sys, uint32_t* age, uint32_t* resets, int dst_is_device);
+
 /* Advance every particle by n_steps constant steps (RK4 or Euler) of size
  * direction_g * dt (paper Sec. 2.1; Appendix A "Running the Simulation":
  * negative steps integrate backward).  The integrator keeps each particle's

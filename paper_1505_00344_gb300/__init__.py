@@ -68,6 +68,8 @@ _SIGS = {
     "ff_set_launch": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64],
     "ff_backward": [_P, _P, _P, _P],
     "ff_count_escaped_noalloc": [_P, ctypes.c_int, _I64, _I64, _P, ctypes.c_int, _P, _P],
+    "ff_set_reset": [_P, _P, _P, ctypes.c_double, ctypes.c_int],
+    "ff_get_reset_state": [_P, _P, _P, ctypes.c_int],
 }
 
 
@@ -166,6 +168,23 @@ def ff_get_particle_param(sys, dst):
     idx = ctypes.c_int(-1)
     _check(lib().ff_get_particle_param(sys, ptr, dev, ctypes.byref(idx)))
     return idx.value
+
+
+def ff_set_reset(sys, bound_lo=None, bound_hi=None, t_max=0.0, check_every=1):
+    lo = hi = None
+    lo_p = hi_p = None
+    if bound_lo is not None:
+        lo, lo_p = _dbl(bound_lo)
+    if bound_hi is not None:
+        hi, hi_p = _dbl(bound_hi)
+    _check(lib().ff_set_reset(sys, lo_p, hi_p, float(t_max), int(check_every)))
+
+
+def ff_get_reset_state(sys, age=None, resets=None):
+    a, dev_a, _ka = _buf(age, np.uint32)
+    r, dev_r, _kr = _buf(resets, np.uint32)
+    dev = dev_a if age is not None else dev_r
+    _check(lib().ff_get_reset_state(sys, a, r, dev))
 
 
 def ff_step(sys, n_steps, dt):
@@ -310,6 +329,12 @@ class System:
 
     def step(self, n_steps, dt):
         ff_step(self.handle, n_steps, dt)
+
+    def set_reset(self, bound_lo=None, bound_hi=None, t_max=0.0, check_every=1):
+        ff_set_reset(self.handle, bound_lo, bound_hi, t_max, check_every)
+
+    def get_reset_state(self, age=None, resets=None):
+        ff_get_reset_state(self.handle, age, resets)
 
     def set_params(self, params):
         ff_set_params(self.handle, params)

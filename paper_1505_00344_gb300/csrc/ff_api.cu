@@ -101,6 +101,17 @@ struct ff_system {
     // launch shape
     int ppt = 1, block = 256, blocks_per_sm = 0;
     int64_t max_steps = 0;
+    // particle reset
+    int64_t steps_total = 0;  // steps since the last ff_reset (global step numbers)
+    int check_every = 0;      // 0 = reset off
+    double t_max = 0.0;
+    bool has_bounds = false;
+    float blo[FF_MAX_DIM] = {}, bhi[FF_MAX_DIM] = {};
+    uint32_t* d_age = nullptr;
+    uint32_t* d_resets = nullptr;
+    ff::ResetTable* d_reset_table = nullptr;
+    ff::ResetTable h_reset_table = {};
+    bool reset_table_dirty = true;
 };
 
 namespace {
@@ -199,6 +210,9 @@ ff_status ff_destroy_system(ff_system* s) {
     cudaFree(s->d_pparam);
     cudaFree(s->d_counter);
     cudaFree(s->d_stage);
+    cudaFree(s->d_age);
+    cudaFree(s->d_resets);
+    cudaFree(s->d_reset_table);
     delete s;
     return FF_OK;
 }
@@ -236,6 +250,15 @@ ff_status ff_seed_particles(ff_system* s, int64_t count, const double* lo, const
     if (group_id_out) *group_id_out = s->n_groups;
     s->n_groups++;
     s->n_particles += count;
+    s->reset_table_dirty = true;
+    return FF_OK;
+}
+
+static ff_status clear_reset_state(ff_system* s) {
+    if (!s->d_age) return FF_OK;
+    cudaError_t e = cudaMemsetAsync(s->d_age, 0, sizeof(uint32_t) * (size_t)s->pitch, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_resets, 0, sizeof(uint32_t) * (size_t)s->pitch, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing particle ages");
     return FF_OK;
 }
 
@@ -253,6 +276,9 @@ ff_status ff_reset(ff_system* s) {
     }
     s->t_fwd = s->t_bwd = s->c_fwd = s->c_bwd = 0.0;
     s->stepped = false;
+    s->steps_total = 0;
+    ff_status st = clear_reset_state(s);
+    if (st != FF_OK) return st;
     return FF_OK;
 }
 
@@ -347,6 +373,87 @@ ff_status ff_set_launch(ff_system* s, int ppt, int block, int blocks_per_sm, int
     return FF_OK;
 }
 
+ff_status ff_set_reset(ff_system* s, const double* bound_lo, const double* bound_hi, double t_max,
+                       int check_every) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_set_reset: system is NULL");
+    if (check_every < 0) return fail(FF_ERR_INVALID_ARG, "ff_set_reset: check_every < 0");
+    if ((bound_lo == nullptr) != (bound_hi == nullptr))
+        return fail(FF_ERR_INVALID_ARG, "ff_set_reset: give both bounds or neither");
+    if (!std::isfinite(t_max)) return fail(FF_ERR_INVALID_ARG, "ff_set_reset: t_max not finite");
+    if (bound_lo) {
+        if (!all_finite(bound_lo, s->dim) || !all_finite(bound_hi, s->dim))
+            return fail(FF_ERR_INVALID_ARG, "ff_set_reset: non-finite bounds");
+        for (int k = 0; k < s->dim; ++k)
+            if (bound_lo[k] > bound_hi[k]) return fail(FF_ERR_INVALID_ARG, "ff_set_reset: bound_lo[%d] > bound_hi[%d]", k, k);
+    }
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_set_reset: set device");
+    if (check_every > 0 && !s->d_age) {
+        const size_t n = sizeof(uint32_t) * (size_t)s->pitch;
+        cudaError_t e = cudaMalloc(&s->d_age, n);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_resets, n);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_reset_table, sizeof(ff::ResetTable));
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->d_age, 0, n, s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->d_resets, 0, n, s->stream);
+        if (e != cudaSuccess) {
+            cudaFree(s->d_age);
+            cudaFree(s->d_resets);
+            cudaFree(s->d_reset_table);
+            s->d_age = s->d_resets = nullptr;
+            s->d_reset_table = nullptr;
+            return cuda_fail(e, "ff_set_reset: allocation");
+        }
+    }
+    s->check_every = check_every;
+    s->t_max = t_max;
+    s->has_bounds = bound_lo != nullptr;
+    for (int k = 0; k < s->dim; ++k) {
+        s->blo[k] = bound_lo ? (float)bound_lo[k] : 0.0f;
+        s->bhi[k] = bound_hi ? (float)bound_hi[k] : 0.0f;
+    }
+    s->reset_table_dirty = true;
+    return FF_OK;
+}
+
+ff_status ff_get_reset_state(ff_system* s, uint32_t* age, uint32_t* resets, int dst_is_device) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_get_reset_state: system is NULL");
+    if (!s->d_age) return fail(FF_ERR_STATE, "ff_get_reset_state: the reset was never enabled");
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_get_reset_state: set device");
+    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t n = sizeof(uint32_t) * (size_t)s->n_particles;
+    cudaError_t e = cudaSuccess;
+    if (age && n) e = cudaMemcpyAsync(age, s->d_age, n, kind, s->stream);
+    if (e == cudaSuccess && resets && n) e = cudaMemcpyAsync(resets, s->d_resets, n, kind, s->stream);
+    if (e == cudaSuccess && !dst_is_device) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_get_reset_state: copy");
+    return FF_OK;
+}
+
+static ff_status upload_reset_table(ff_system* s) {
+    ff::ResetTable& t = s->h_reset_table;
+    t = ff::ResetTable{};
+    for (int g = 0; g < s->n_groups; ++g) {
+        for (int k = 0; k < s->dim; ++k) {
+            t.lo[g][k] = s->groups[g].lo[k];
+            t.width[g][k] = s->groups[g].hi[k] - s->groups[g].lo[k];
+        }
+        t.count[g] = s->groups[g].count;
+        t.seed[g] = s->groups[g].seed;
+    }
+    for (int k = 0; k < s->dim; ++k) {
+        t.blo[k] = s->blo[k];
+        t.bhi[k] = s->bhi[k];
+    }
+    t.has_bounds = s->has_bounds ? 1 : 0;
+    // pageable source: the call returns once the table has been staged, so later edits are safe
+    cudaError_t e = cudaMemcpyAsync(s->d_reset_table, &t, sizeof(t), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_step: reset table upload");
+    s->reset_table_dirty = false;
+    return FF_OK;
+}
+
 ff_status ff_step(ff_system* s, int64_t n_steps, double dt) {
     if (!s) return fail(FF_ERR_INVALID_ARG, "ff_step: system is NULL");
     if (n_steps < 0) return fail(FF_ERR_INVALID_ARG, "ff_step: n_steps %lld < 0", (long long)n_steps);
@@ -377,14 +484,28 @@ ff_status ff_step(ff_system* s, int64_t n_steps, double dt) {
     ff::LaunchShape shape{ppt, s->block, s->blocks_per_sm, s->num_sms};
     const bool kahan = (s->flags & FF_FLAG_KAHAN) != 0;
     const bool pp = s->pparam_index >= 0;
+    if (s->check_every > 0) {
+        if (s->reset_table_dirty) {
+            ff_status st = upload_reset_table(s);
+            if (st != FF_OK) return st;
+        }
+        a.reset = s->d_reset_table;
+        a.age = s->d_age;
+        a.resets = s->d_resets;
+        a.check_every = s->check_every;
+        const double steps = (s->t_max > 0.0 && dt != 0.0) ? std::ceil(s->t_max / std::fabs(dt)) : 0.0;
+        a.max_age = steps <= 0.0 ? 0u : (steps >= 4294967295.0 ? 4294967295u : (uint32_t)steps);
+    }
     int64_t left = n_steps;
     while (left > 0) {
         int64_t chunk = (s->max_steps > 0 && left > s->max_steps) ? s->max_steps : left;
         if (chunk > ((int64_t)1 << 30)) chunk = (int64_t)1 << 30;  // kernels count steps in 32 bits
         a.n_steps = chunk;
+        a.step0 = s->steps_total;
         cudaError_t e = ff::launch_integrate(s->rhs_id, s->method, kahan, pp, a, shape, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "integrator launch");
         left -= chunk;
+        s->steps_total += chunk;
     }
     bool any_fwd = false, any_bwd = false;
     for (int g = 0; g < s->n_groups; ++g) (s->groups[g].direction > 0 ? any_fwd : any_bwd) = true;
@@ -498,7 +619,7 @@ ff_status ff_set_state(ff_system* s, const float* src, int src_is_device) {
         e = cudaMemsetAsync(s->d_comp, 0, sizeof(float) * (size_t)s->pitch * s->dim, s->stream);
     if (e == cudaSuccess && !src_is_device) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "ff_set_state: copy");
-    return FF_OK;
+    return clear_reset_state(s);
 }
 
 ff_status ff_stats(ff_system* s, int64_t* n_escaped, double* t_fwd, double* t_bwd) {

@@ -36,7 +36,32 @@ struct IntegrateArgs {
     float p[FF_MAX_PARAMS];         // system parameters (FP32)
     int64_t gend[FF_MAX_GROUPS];    // one past the last processed particle of each group
     int gblk[FF_MAX_GROUPS + 1];    // group-uniform kernels: first block of each group (prefix)
+    // particle reset (RESET variants only)
+    const struct ResetTable* reset;  // group boxes, sizes, seeds and state bounds (device)
+    uint32_t* age;                   // steps since each particle's last reset
+    uint32_t* resets;                // resets of each particle
+    int64_t step0;                   // global step number before this launch
+    int check_every;
+    uint32_t max_age;                // 0 = no age limit
 };
+
+// Reset data of a system, in device memory (read only when a particle resets).
+struct ResetTable {
+    double lo[FF_MAX_GROUPS][FF_MAX_DIM];
+    double width[FF_MAX_GROUPS][FF_MAX_DIM];  // hi - lo in double, as for the initial seeding
+    int64_t count[FF_MAX_GROUPS];
+    uint64_t seed[FF_MAX_GROUPS];
+    float blo[FF_MAX_DIM], bhi[FF_MAX_DIM];
+    int has_bounds;
+};
+
+// SplitMix64 output n of the stream seeded with s (Steele, Lea & Flood 2014).
+__device__ __forceinline__ uint64_t reset_splitmix64(uint64_t seed, uint64_t n) {
+    uint64_t z = seed + n * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
 
 // ---------------------------------------------------------------------------
 // Right-hand sides.  Each has DIM (registers per particle state), NP (params)
@@ -347,12 +372,47 @@ template <> struct Vec<4> {
     }
 };
 
+// Reset test and re-draw of one particle (paper Sec. 2.1, Appendix A).  The
+// state is tested in external coordinates; a reset particle gets the draws of
+// its next reset block, loses its compensation and restarts its age.
+template <int D, class Stepper>
+__device__ __forceinline__ void reset_check(const IntegrateArgs& a, const Stepper& st, float (&x)[D], float (&c)[D],
+                                         uint32_t& age, uint32_t& nres, int g, int64_t i) {
+    const ResetTable* t = a.reset;
+    float e[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) e[k] = x[k];
+    st.from_internal(e);
+    bool out = a.max_age > 0u && age >= a.max_age;
+    if (t->has_bounds)
+        for (int k = 0; k < a.dim; ++k) out |= !(e[k] >= t->blo[k] && e[k] <= t->bhi[k]);
+    if (!out) return;
+    const uint32_t r = nres + 1u;
+    const uint64_t j = (uint64_t)(i - a.gstart[g]);
+    const uint64_t base = ((uint64_t)r * (uint64_t)t->count[g] + j) * (uint64_t)a.dim;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if (k < a.dim) {
+            const uint64_t z = reset_splitmix64(t->seed[g], base + (uint64_t)k + 1u);
+            const double u = (double)(z >> 40) * (1.0 / 16777216.0);
+            e[k] = __double2float_rn(__dadd_rn(t->lo[g][k], __dmul_rn(t->width[g][k], u)));
+        } else {
+            e[k] = 0.0f;
+        }
+        c[k] = 0.0f;
+        x[k] = e[k];
+    }
+    st.to_internal(x);
+    age = 0u;
+    nres = r;
+}
+
 // ---------------------------------------------------------------------------
 // The persistent integrator.  Grid-stride over work items of PPT consecutive
 // particles; each work item loads its state once, runs n_steps steps with the
 // state in registers and stores it once.
 // ---------------------------------------------------------------------------
-template <class R, int METHOD, bool KAHAN, bool PP, int PPT>
+template <class R, int METHOD, bool KAHAN, bool PP, int PPT, bool RESET = false>
 __global__ void __launch_bounds__(R::MAX_BLOCK) integrate_kernel(const __grid_constant__ IntegrateArgs a) {
     constexpr int D = R::DIM;
     using Stepper = typename StepperFor<R, METHOD, KAHAN>::type;
@@ -379,13 +439,20 @@ __global__ void __launch_bounds__(R::MAX_BLOCK) integrate_kernel(const __grid_co
         }
         float prm[PPT][R::NP];
         Stepper st[PPT];
+        int grp[PPT];
+        uint32_t age[PPT], nres[PPT];
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int64_t i = i0 + j;
             float h = a.gh[0];
+            grp[j] = 0;
 #pragma unroll
             for (int g = 1; g < FF_MAX_GROUPS; ++g)
-                if (g < a.n_groups && i >= a.gstart[g]) h = a.gh[g];
+                if (g < a.n_groups && i >= a.gstart[g]) { h = a.gh[g]; grp[j] = g; }
+            if (RESET) {
+                age[j] = a.age[i];
+                nres[j] = a.resets[i];
+            }
             float pv = 0.f;
             if (PP) pv = a.pparam[i];
 #pragma unroll
@@ -394,6 +461,8 @@ __global__ void __launch_bounds__(R::MAX_BLOCK) integrate_kernel(const __grid_co
             st[j].to_internal(x[j]);
         }
         const int n_steps = (int)a.n_steps;  // the host splits launches at 2^30 steps
+        // steps until the next reset check (global step numbers that are multiples of check_every)
+        int countdown = RESET ? a.check_every - (int)(a.step0 % a.check_every) : 0;
 #pragma unroll 4
         for (int s = 0; s < n_steps; ++s) {
 #pragma unroll
@@ -411,10 +480,22 @@ __global__ void __launch_bounds__(R::MAX_BLOCK) integrate_kernel(const __grid_co
                         x[j][k] = fmaf(sc[k], acc[k], x[j][k]);
                     }
                 }
+                if (RESET) age[j] += 1u;
+            }
+            if (RESET && --countdown == 0) {
+                countdown = a.check_every;
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) reset_check<D>(a, st[j], x[j], c[j], age[j], nres[j], grp[j], i0 + j);
             }
         }
 #pragma unroll
-        for (int j = 0; j < PPT; ++j) st[j].from_internal(x[j]);
+        for (int j = 0; j < PPT; ++j) {
+            st[j].from_internal(x[j]);
+            if (RESET) {
+                a.age[i0 + j] = age[j];
+                a.resets[i0 + j] = nres[j];
+            }
+        }
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             if (k < a.dim) {
@@ -699,9 +780,30 @@ inline cudaError_t launch_ppt(const IntegrateArgs& a, const LaunchShape& s, cuda
     }
 }
 
+// Resetting particles: the scalar kernel, one particle per thread.
+template <class R>
+inline cudaError_t launch_reset_variants(int method, bool kahan, bool pp, const IntegrateArgs& a0,
+                                         const LaunchShape& s0, cudaStream_t st) {
+    IntegrateArgs a = a0;
+    LaunchShape s = s0;
+    a.n_vec = a0.n_vec * s0.ppt;
+    s.ppt = 1;
+    if (method == FF_RK4) {
+        if (kahan) return pp ? persistent_launch(integrate_kernel<R, FF_RK4, true, true, 1, true>, a, s, st)
+                             : persistent_launch(integrate_kernel<R, FF_RK4, true, false, 1, true>, a, s, st);
+        return pp ? persistent_launch(integrate_kernel<R, FF_RK4, false, true, 1, true>, a, s, st)
+                  : persistent_launch(integrate_kernel<R, FF_RK4, false, false, 1, true>, a, s, st);
+    }
+    if (kahan) return pp ? persistent_launch(integrate_kernel<R, FF_EULER, true, true, 1, true>, a, s, st)
+                         : persistent_launch(integrate_kernel<R, FF_EULER, true, false, 1, true>, a, s, st);
+    return pp ? persistent_launch(integrate_kernel<R, FF_EULER, false, true, 1, true>, a, s, st)
+              : persistent_launch(integrate_kernel<R, FF_EULER, false, false, 1, true>, a, s, st);
+}
+
 template <class R>
 inline cudaError_t launch_variants(int method, bool kahan, bool pp, const IntegrateArgs& a,
                                    const LaunchShape& s, cudaStream_t st) {
+    if (a.reset) return launch_reset_variants<R>(method, kahan, pp, a, s, st);
     if (method == FF_RK4) {
         if (kahan) return pp ? launch_ppt<R, FF_RK4, true, true>(a, s, st) : launch_ppt<R, FF_RK4, true, false>(a, s, st);
         return pp ? launch_ppt<R, FF_RK4, false, true>(a, s, st) : launch_ppt<R, FF_RK4, false, false>(a, s, st);

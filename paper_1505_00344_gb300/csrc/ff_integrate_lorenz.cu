@@ -40,8 +40,8 @@ static cudaError_t uniform_launch(Kernel kernel, const IntegrateArgs& a0, const 
 
 cudaError_t launch_integrate_lorenz(int method, bool kahan, bool pp, const IntegrateArgs& a,
                                     const LaunchShape& shape, cudaStream_t stream) {
-    // plain RK4 at 2 or 4 particles per thread runs as packed f32x2 pairs
-    if (method == FF_RK4 && !kahan && (shape.ppt == 2 || shape.ppt == 4)) {
+    // plain RK4 at 2 or 4 particles per thread runs as packed f32x2 pairs (without resets)
+    if (method == FF_RK4 && !kahan && !a.reset && (shape.ppt == 2 || shape.ppt == 4)) {
         bool aligned = true;
         for (int g = 0; g < a.n_groups; ++g) aligned = aligned && (a.gstart[g] % shape.ppt == 0);
         if (aligned && (!pp || a.pidx == 1)) {

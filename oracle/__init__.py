@@ -63,6 +63,11 @@ def _load():
         lib.ffo_integrate_reset.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, P, P, ctypes.c_int,
                                             ctypes.c_int, P, P, i64, i64, ctypes.c_int, P, P, ctypes.c_uint32,
                                             P, P, P, P, P, P, P]
+        lib.ffo_jacobians.restype = ctypes.c_int
+        lib.ffo_jacobians.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P]
+        lib.ffo_tangent.restype = ctypes.c_int
+        lib.ffo_tangent.argtypes = [ctypes.c_int, ctypes.c_int, i64, P, P, ctypes.c_int, ctypes.c_int, P, P, i64,
+                                    P, P, P]
         lib.ffo_count_escaped.restype = i64
         lib.ffo_count_escaped.argtypes = [ctypes.c_int, i64, i64, P, P]
         lib.ffo_splat2d.restype = None
@@ -214,6 +219,47 @@ def integrate_reset(rhs_id, state, params, groups, dt, n_steps, step0=0, check_e
     if rc != 0:
         raise ValueError("ffo_integrate_reset: bad arguments")
     return st, age, resets
+
+
+def jacobians(rhs_id, x, params):
+    """(J, Fp): d f / d x (dim x dim) and d f / d p (dim x n_params) at x."""
+    x = _c(x, np.float64)
+    p = _c(params, np.float64)
+    J = np.empty((x.size, x.size))
+    Fp = np.empty((x.size, p.size))
+    if _load().ffo_jacobians(rhs_id, x.size, _ptr(x), _ptr(p), p.size, _ptr(J), _ptr(Fp)) != 0:
+        raise ValueError("ffo_jacobians: system without derivatives or bad size")
+    return J, Fp
+
+
+def tangent(rhs_id, x0, params, h, n_steps, pparam_index=-1, pparam=None):
+    """Forward sensitivities of RK4: (x(T) [dim][P], S [P][dim][dim], Q [P][dim][n_params])."""
+    x0 = _c(x0, np.float64)
+    dim, P = x0.shape
+    p = _c(params, np.float64)
+    hh = np.broadcast_to(np.asarray(h, dtype=np.float64), (P,)).copy()
+    pp = None if pparam is None else _c(pparam, np.float64)
+    xT = np.empty_like(x0)
+    S = np.empty((P, dim, dim))
+    Q = np.empty((P, dim, p.size))
+    rc = _load().ffo_tangent(rhs_id, dim, P, _ptr(x0), _ptr(p), p.size, pparam_index, _ptr(pp), _ptr(hh),
+                             int(n_steps), _ptr(xT), _ptr(S), _ptr(Q))
+    if rc != 0:
+        raise ValueError("ffo_tangent: bad arguments or system without derivatives")
+    return xT, S, Q
+
+
+def mse_gradients(rhs_id, x0, params, h, n_steps, target, pparam_index=-1, pparam=None):
+    """Loss L = (1/P) sum_i |x_i(T) - t_i|^2 and its gradients from the forward sensitivities:
+    dL/dx0 [dim][P] and dL/dp [n_params] (with a per-particle parameter, its column is summed)."""
+    xT, S, Q = tangent(rhs_id, x0, params, h, n_steps, pparam_index, pparam)
+    P = xT.shape[1]
+    r = xT - target
+    L = float((r * r).sum() / P)
+    g = (2.0 / P) * r
+    dx0 = np.einsum("pij,ip->jp", S, g)
+    dp = np.einsum("piq,ip->q", Q, g)
+    return L, dx0, dp
 
 
 def count_escaped(state):

@@ -364,6 +364,149 @@ int ffo_integrate_reset(int rhs_id, int method, int dim, int64_t P, double *stat
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Derivatives for gradient checks (the paper has no gradients; these serve  */
+/* the adjoint of the integrator).                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Jacobian J[i*dim + k] = d f_i / d x_k and parameter Jacobian
+ * Fp[i*n_params + q] = d f_i / d p_q, differentiated by hand from the right-hand
+ * sides above.  Returns 0, or -1 for a system without derivatives here. */
+static int rhs_jacobians(int rhs_id, int dim, const double *x, const double *p, int n_params,
+                         double *J, double *Fp)
+{
+    for (int i = 0; i < dim * dim; ++i) J[i] = 0.0;
+    for (int i = 0; i < dim * n_params; ++i) Fp[i] = 0.0;
+    switch (rhs_id) {
+    case FFO_LINEAR:
+        for (int i = 0; i < dim; ++i) {
+            for (int k = 0; k < dim; ++k) J[i * dim + k] = p[i * dim + k];
+            for (int k = 0; k < dim; ++k) Fp[i * n_params + i * dim + k] = x[k];  /* d(Ax)_i / dA_ik */
+        }
+        return 0;
+    case FFO_HARMONIC: {
+        double w = p[0];
+        J[0 * 2 + 1] = 1.0;
+        J[1 * 2 + 0] = -(w * w);
+        Fp[1 * n_params + 0] = -2.0 * w * x[0];
+        return 0;
+    }
+    case FFO_LORENZ: {
+        double sigma = p[0], r = p[1], beta = p[2];
+        J[0] = -sigma; J[1] = sigma; J[2] = 0.0;
+        J[3] = r - x[2]; J[4] = -1.0; J[5] = -x[0];
+        J[6] = x[1]; J[7] = x[0]; J[8] = -beta;
+        Fp[0 * 3 + 0] = x[1] - x[0];
+        Fp[1 * 3 + 1] = x[0];
+        Fp[2 * 3 + 2] = -x[2];
+        return 0;
+    }
+    case FFO_WILSON_COWAN: {
+        double E = x[0], I = x[1];
+        double wEE = p[0], wEI = p[1], wIE = p[2], wII = p[3];
+        double P = p[4], Q = p[5], tauE = p[6], tauI = p[7], gain = p[8], th = p[9];
+        double aE = wEE * E - wEI * I + P, aI = wIE * E - wII * I + Q;
+        double SE = wc_sigmoid(aE, gain, th), SI = wc_sigmoid(aI, gain, th);
+        double dSE = gain * SE * (1.0 - SE), dSI = gain * SI * (1.0 - SI);  /* S'(a) */
+        double fE = (-E + SE) / tauE, fI = (-I + SI) / tauI;
+        J[0] = (-1.0 + dSE * wEE) / tauE;
+        J[1] = (-dSE * wEI) / tauE;
+        J[2] = (dSI * wIE) / tauI;
+        J[3] = (-1.0 - dSI * wII) / tauI;
+        /* dS/dgain = S (1 - S) (a - th), dS/dth = -gain S (1 - S) */
+        Fp[0 * 10 + 0] = dSE * E / tauE;
+        Fp[0 * 10 + 1] = -dSE * I / tauE;
+        Fp[0 * 10 + 4] = dSE / tauE;
+        Fp[0 * 10 + 6] = -fE / tauE;
+        Fp[0 * 10 + 8] = SE * (1.0 - SE) * (aE - th) / tauE;
+        Fp[0 * 10 + 9] = -dSE / tauE;
+        Fp[1 * 10 + 2] = dSI * E / tauI;
+        Fp[1 * 10 + 3] = -dSI * I / tauI;
+        Fp[1 * 10 + 5] = dSI / tauI;
+        Fp[1 * 10 + 7] = -fI / tauI;
+        Fp[1 * 10 + 8] = SI * (1.0 - SI) * (aI - th) / tauI;
+        Fp[1 * 10 + 9] = -dSI / tauI;
+        return 0;
+    }
+    default:
+        return -1;
+    }
+}
+
+/* Jacobians exposed for tests. */
+int ffo_jacobians(int rhs_id, int dim, const double *x, const double *p, int n_params, double *J, double *Fp)
+{
+    if (!rhs_dim_ok(rhs_id, dim, n_params)) return -1;
+    return rhs_jacobians(rhs_id, dim, x, p, n_params, J, Fp);
+}
+
+#define FFO_AUG_MAX (8 + 64 + 8 * 64)
+
+/* Right-hand side of the variational system y = (x, S, Q):
+ *   dx/dt = f(x, p),  dS/dt = J(x) S,  dQ/dt = J(x) Q + F_p(x). */
+static int aug_rhs(int rhs_id, int dim, int np, const double *y, const double *p, double *dy)
+{
+    double J[64], Fp[8 * 64];
+    const double *x = y, *S = y + dim, *Q = y + dim + dim * dim;
+    double *dx = dy, *dS = dy + dim, *dQ = dy + dim + dim * dim;
+    if (rhs_jacobians(rhs_id, dim, x, p, np, J, Fp) != 0) return -1;
+    rhs_eval(rhs_id, dim, x, p, dx);
+    for (int i = 0; i < dim; ++i) {
+        for (int c = 0; c < dim; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < dim; ++k) s += J[i * dim + k] * S[k * dim + c];
+            dS[i * dim + c] = s;
+        }
+        for (int q = 0; q < np; ++q) {
+            double s = Fp[i * np + q];
+            for (int k = 0; k < dim; ++k) s += J[i * dim + k] * Q[k * np + q];
+            dQ[i * np + q] = s;
+        }
+    }
+    return 0;
+}
+
+/* Forward sensitivities of the RK4 trajectories: classical RK4 applied to the
+ * variational system, which gives exactly the derivatives of the discrete RK4
+ * map (the stages of the augmented system are the chain rule of the stages of
+ * the original one).  Per particle i: xT[k*P+i], S[i][dim][dim] = d x(T) / d x0,
+ * Q[i][dim][n_params] = d x(T) / d p (with pparam_index >= 0 that column is the
+ * derivative with respect to the particle's own value).  Returns 0, or -1. */
+int ffo_tangent(int rhs_id, int dim, int64_t P, const double *x0, const double *params, int n_params,
+                int pparam_index, const double *pparam, const double *h, int64_t n_steps,
+                double *xT, double *S, double *Q)
+{
+    if (!rhs_dim_ok(rhs_id, dim, n_params) || dim > 8 || n_params > 64 || n_steps < 0) return -1;
+    if (pparam_index >= n_params || (pparam_index >= 0 && !pparam)) return -1;
+    const int n = dim + dim * dim + dim * n_params;
+    double y[FFO_AUG_MAX], k1[FFO_AUG_MAX], k2[FFO_AUG_MAX], k3[FFO_AUG_MAX], k4[FFO_AUG_MAX], ys[FFO_AUG_MAX];
+    double p[64];
+    for (int64_t i = 0; i < P; ++i) {
+        memcpy(p, params, sizeof(double) * (size_t)n_params);
+        if (pparam_index >= 0) p[pparam_index] = pparam[i];
+        for (int a = 0; a < n; ++a) y[a] = 0.0;
+        for (int k = 0; k < dim; ++k) {
+            y[k] = x0[(int64_t)k * P + i];
+            y[dim + k * dim + k] = 1.0;
+        }
+        double hh = h[i];
+        for (int64_t s = 0; s < n_steps; ++s) {
+            if (aug_rhs(rhs_id, dim, n_params, y, p, k1)) return -1;
+            for (int a = 0; a < n; ++a) ys[a] = y[a] + (hh / 2.0) * k1[a];
+            aug_rhs(rhs_id, dim, n_params, ys, p, k2);
+            for (int a = 0; a < n; ++a) ys[a] = y[a] + (hh / 2.0) * k2[a];
+            aug_rhs(rhs_id, dim, n_params, ys, p, k3);
+            for (int a = 0; a < n; ++a) ys[a] = y[a] + hh * k3[a];
+            aug_rhs(rhs_id, dim, n_params, ys, p, k4);
+            for (int a = 0; a < n; ++a) y[a] = y[a] + (hh / 6.0) * (k1[a] + 2.0 * k2[a] + 2.0 * k3[a] + k4[a]);
+        }
+        for (int k = 0; k < dim; ++k) xT[(int64_t)k * P + i] = y[k];
+        memcpy(S + i * dim * dim, y + dim, sizeof(double) * (size_t)(dim * dim));
+        memcpy(Q + i * dim * n_params, y + dim + dim * dim, sizeof(double) * (size_t)(dim * n_params));
+    }
+    return 0;
+}
+
 /* Escaped particle: some component is not finite or exceeds 1e30 in
  * magnitude.  flags[i] (optional) receives 1 for escaped particles. */
 int64_t ffo_count_escaped(int dim, int64_t P, int64_t pitch, const double *state, uint8_t *flags)

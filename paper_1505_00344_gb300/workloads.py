@@ -89,6 +89,8 @@ def _wc_4k():
                 dict(count=2048, direction=-1, seed=group_seed(0, 1), **box)],
         dt=0.01, steps_per_frame=1000, frames=1,
         view=dict(ndim_view=2, axes=(0, 1), lo=(0.0, 0.0), hi=(1.0, 1.0), width=256, height=256),
+        # the paper's reset region: the unit square of population activities (Sec. 2.1)
+        reset=dict(lo=[0.0, 0.0], hi=[1.0, 1.0], t_max=5.0, check_every=1),
     )
 
 
@@ -100,6 +102,8 @@ def _lorenz_4M():
                 dict(count=1048576, direction=-1, seed=group_seed(1, 1), **box)],
         dt=0.001, steps_per_frame=200, frames=100, splat_every_frame=True,
         view=dict(ndim_view=2, axes=(0, 2), lo=(-30.0, 0.0), hi=(30.0, 60.0), width=1920, height=1080),
+        # optional recycling of escaping backward particles (not part of the measured workload)
+        reset=dict(lo=[-60.0, -60.0, -20.0], hi=[60.0, 60.0, 100.0], t_max=0.0, check_every=10),
     )
 
 

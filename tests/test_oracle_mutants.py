@@ -55,6 +55,12 @@ MUTANTS = {
     "reset_schedule": ("if ((step0 + s + 1) % check_every != 0) continue;", "if ((step0 + s) % check_every != 0) continue;"),
     "reset_bound_strict": ("if (!(xf >= blo[k] && xf <= bhi[k])) out = 1;", "if (!(xf > blo[k] && xf < bhi[k])) out = 1;"),
     "reset_age_limit": ("if (max_age > 0 && age[i] >= max_age) out = 1;", "if (max_age > 0 && age[i] > max_age) out = 1;"),
+    "jac_lorenz_sign": ("J[3] = r - x[2]; J[4] = -1.0; J[5] = -x[0];", "J[3] = x[2] - r; J[4] = -1.0; J[5] = -x[0];"),
+    "jac_lorenz_param": ("Fp[2 * 3 + 2] = -x[2];", "Fp[2 * 3 + 2] = x[2];"),
+    "jac_wc_gain": ("Fp[0 * 10 + 8] = SE * (1.0 - SE) * (aE - th) / tauE;", "Fp[0 * 10 + 8] = SE * (1.0 - SE) * aE / tauE;"),
+    "jac_wc_cross": ("J[2] = (dSI * wIE) / tauI;", "J[2] = (dSI * wIE) / tauE;"),
+    "tangent_no_forcing": ("double s = Fp[i * np + q];", "double s = 0.0;"),
+    "tangent_stage": ("for (int a = 0; a < n; ++a) ys[a] = y[a] + hh * k3[a];", "for (int a = 0; a < n; ++a) ys[a] = y[a] + hh * k2[a];"),
     "escape_threshold": ("if (!(fabs(v) <= 1e30)) esc = 1;", "if (!(fabs(v) < 1e38)) esc = 1;"),
 }
 

@@ -1,0 +1,112 @@
+"""Pins of the oracle's derivatives, used to check the CUDA adjoint.
+
+* The hand-derived Jacobians d f/d x and d f/d p match central differences of the
+  (already pinned) right-hand sides.
+* For dx/dt = A x the sensitivity d x(T)/d x0 of n RK4 steps is exactly the matrix
+  power T(hA)^n, and d x(T)/d A matches central differences of that closed form.
+* The MSE gradients from the forward sensitivities match central differences of
+  the loss computed with the plain integrator (Lorenz, Wilson-Cowan), including a
+  per-particle parameter.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1505_00344_gb300.workloads import LORENZ_PARAMS, WC_PARAMS
+
+
+def fd_jac(rid, x, p, eps=1e-6):
+    x = np.asarray(x, float)
+    p = np.asarray(p, float)
+    J = np.empty((x.size, x.size))
+    Fp = np.empty((x.size, p.size))
+    for k in range(x.size):
+        e = np.zeros_like(x); e[k] = eps * max(1.0, abs(x[k]))
+        J[:, k] = (oracle.rhs(rid, x + e, p) - oracle.rhs(rid, x - e, p)) / (2 * e[k])
+    for q in range(p.size):
+        e = np.zeros_like(p); e[q] = eps * max(1.0, abs(p[q]))
+        Fp[:, q] = (oracle.rhs(rid, x, p + e) - oracle.rhs(rid, x, p - e)) / (2 * e[q])
+    return J, Fp
+
+
+@pytest.mark.parametrize("rid,x,p", [
+    (oracle.LORENZ, [3.0, -7.0, 25.0], LORENZ_PARAMS),
+    (oracle.LORENZ, [-12.0, 4.0, 1.0], [9.0, 150.0, 2.0]),
+    (oracle.WILSON_COWAN, [0.3, 0.6], WC_PARAMS),
+    (oracle.WILSON_COWAN, [0.9, 0.1], [3.0, 5.0, 2.0, 1.0, 0.5, -1.0, 1.5, 0.7, 2.0, 3.0]),
+    (oracle.HARMONIC, [0.4, -1.2], [2.5]),
+    (oracle.LINEAR, [1.0, -2.0, 0.5], list(np.arange(9) * 0.3 - 1.0)),
+])
+def test_jacobians_match_central_differences(rid, x, p):
+    J, Fp = oracle.jacobians(rid, x, p)
+    Jf, Ff = fd_jac(rid, x, p)
+    scale = max(1.0, np.abs(Jf).max(), np.abs(Ff).max())
+    assert np.abs(J - Jf).max() <= 1e-7 * scale
+    assert np.abs(Fp - Ff).max() <= 1e-7 * scale
+
+
+def taylor4(Z):
+    I = np.eye(Z.shape[0])
+    return I + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+
+
+def test_linear_sensitivity_is_matrix_power():
+    A = np.array([[-0.5, 1.0, 0.2], [-1.0, -0.3, 0.0], [0.1, 0.4, -0.8]])
+    x0 = np.array([[1.0, -0.5], [0.3, 2.0], [-1.2, 0.7]])
+    h, n = 0.05, 40
+    xT, S, Q = oracle.tangent(oracle.LINEAR, x0, A.reshape(-1), h, n)
+    M = np.linalg.matrix_power(taylor4(h * A), n)
+    for i in range(2):
+        np.testing.assert_allclose(S[i], M, rtol=1e-12, atol=1e-14)
+    # d x(T) / d A_ab by central differences of the closed form
+    eps = 1e-6
+    for a in range(3):
+        for b in range(3):
+            E = np.zeros_like(A); E[a, b] = eps
+            d = (np.linalg.matrix_power(taylor4(h * (A + E)), n) @ x0
+                 - np.linalg.matrix_power(taylor4(h * (A - E)), n) @ x0) / (2 * eps)
+            np.testing.assert_allclose(Q[:, :, a * 3 + b].T, d, rtol=1e-6, atol=1e-9)
+
+
+def loss(rid, x0, p, h, n, target, **kw):
+    xT = oracle.integrate(rid, x0, p, h, n, **kw)
+    return float(((xT - target) ** 2).sum() / x0.shape[1])
+
+
+@pytest.mark.parametrize("rid,params,box,h,n", [
+    (oracle.LORENZ, LORENZ_PARAMS, ([-20, -20, 0], [20, 20, 40]), 0.001, 300),
+    (oracle.WILSON_COWAN, WC_PARAMS, ([0, 0], [1, 1]), 0.01, 200),
+])
+def test_mse_gradients_match_finite_differences(rid, params, box, h, n):
+    dim = len(box[0])
+    x0 = oracle.seed_group(dim, box[0], box[1], 17, count=6).astype(np.float64)
+    target = oracle.seed_group(dim, box[0], box[1], 18, count=6).astype(np.float64)
+    hh = np.array([h, -h, h, h, -h, h])
+    L, dx0, dp = oracle.mse_gradients(rid, x0, params, hh, n, target)
+    assert abs(L - loss(rid, x0, params, hh, n, target)) <= 1e-12 * max(1.0, L)
+    eps = 1e-6
+    for k in range(dim):
+        for i in range(6):
+            e = np.zeros_like(x0); e[k, i] = eps
+            fd = (loss(rid, x0 + e, params, hh, n, target) - loss(rid, x0 - e, params, hh, n, target)) / (2 * eps)
+            assert abs(dx0[k, i] - fd) <= 1e-6 * max(1.0, abs(fd))
+    for q in range(len(params)):
+        e = np.zeros(len(params)); e[q] = eps * max(1.0, abs(params[q]))
+        fd = (loss(rid, x0, np.add(params, e), hh, n, target) - loss(rid, x0, np.subtract(params, e), hh, n, target)) \
+            / (2 * e[q])
+        assert abs(dp[q] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_per_particle_parameter_column():
+    x0 = oracle.seed_group(3, [-20, -20, 0], [20, 20, 40], 5, count=4).astype(np.float64)
+    target = np.zeros_like(x0)
+    r = np.array([5.0, 15.0, 28.0, 60.0])
+    _, S, Q = oracle.tangent(oracle.LORENZ, x0, LORENZ_PARAMS, 0.001, 200, pparam_index=1, pparam=r)
+    eps = 1e-6
+    for i in range(4):
+        rp, rm = r.copy(), r.copy()
+        rp[i] += eps
+        rm[i] -= eps
+        d = (oracle.integrate(oracle.LORENZ, x0, LORENZ_PARAMS, 0.001, 200, pparam_index=1, pparam=rp)
+             - oracle.integrate(oracle.LORENZ, x0, LORENZ_PARAMS, 0.001, 200, pparam_index=1, pparam=rm)) / (2 * eps)
+        np.testing.assert_allclose(Q[i, :, 1], d[:, i], rtol=1e-6, atol=1e-7)

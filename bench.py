@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--kahan", action="store_true")
     ap.add_argument("--reset", action="store_true", help="enable the workload's particle reset (not the default)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the taped forward and the adjoint (ff_backward) instead of the plain job")
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--checkpoint-every", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -420,11 +424,80 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_adjoint(args, rank, world, local):
+    """Gradients of L = (1/P) sum |x(T) - t|^2 w.r.t. initial states and parameters for the
+    workload's particles over --adjoint-steps RK4 steps (checkpoint every --checkpoint-every):
+    particle-steps/s of the plain forward, the taped forward and the adjoint sweep."""
+    import torch
+    import paper_1505_00344_gb300 as ff
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload_for(args, rank, world)
+    P, dim, n, dt = total_particles(w), w["dim"], args.adjoint_steps, w["dt"]
+    s = ff.System.from_workload(w, stream=torch.cuda.current_stream().cuda_stream)
+    x0 = torch.empty((dim, P), dtype=torch.float32, device=dev)
+    s.get_state(x0)
+    target = torch.empty_like(x0).uniform_(-20.0, 20.0)
+    dx0 = torch.empty_like(x0)
+    n_params = len(w["params"])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    def plain():
+        s.set_state(x0)
+        s.step(n, dt)
+
+    def taped():
+        s.set_state(x0)
+        s.tape_begin(args.checkpoint_every, n)
+        s.step(n, dt)
+
+    grad = torch.empty_like(x0)
+
+    def backward():
+        s.backward(grad, dx0, n_params)
+
+    for _ in range(args.warmup):
+        plain()
+    t_plain = [timed(plain) for _ in range(max(1, args.steps))]
+    t_fwd, t_bwd = [], []
+    for _ in range(max(1, args.steps)):
+        t_fwd.append(timed(taped))
+        xT = torch.empty_like(x0)
+        s.get_state(xT)
+        torch.mul(xT - target, 2.0 / P, out=grad)
+        t_bwd.append(timed(backward))
+    s.tape_end()
+    units = P * n
+    med = statistics.median
+    bwd = units / (med(t_bwd) / 1e3)
+    return {"metric": "adjoint particle-RK4-steps/sec (gradients w.r.t. initial states and parameters)",
+            "value": bwd, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": med(t_bwd), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (FP64 parameter sums)", "data": "synthetic",
+            "config": {"workload": w["name"], "particles": P, "rk4_steps": n, "checkpoint_every": args.checkpoint_every,
+                       "loss": "mean squared distance of final states to random targets"},
+            "plain_forward": units / (med(t_plain) / 1e3), "taped_forward": units / (med(t_fwd) / 1e3),
+            "backward_over_plain_time": med(t_bwd) / med(t_plain),
+            "ms": {"plain": med(t_plain), "taped_forward": med(t_fwd), "backward": med(t_bwd)}}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.adjoint:
+        out = run_adjoint(args, rank, world, local)
     else:
         out = run_ours(args, rank, world, local)
     if rank == 0 and out is not None:

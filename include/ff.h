@@ -239,10 +239,34 @@ ff_status ff_system_info(ff_system* sys, int64_t* n_particles, int64_t* pitch, i
 ff_status ff_set_launch(ff_system* sys, int particles_per_thread, int block, int blocks_per_sm,
                         int64_t max_steps_per_launch);
 
-/* Gradients through the integration (not part of the paper).  Not built yet:
- * returns FF_ERR_UNSUPPORTED. */
-ff_status ff_backward(ff_system* sys, const float* dL_dxT_dev, float* dL_dx0_dev,
-                      double* dL_dp_host);
+/* Gradients through the integration (not part of the paper): the discrete
+ * adjoint of the RK4 / Euler map, for losses of the final states.
+ *
+ * ff_tape_begin starts recording at the current state: every later ff_step
+ * stores a checkpoint of the state every checkpoint_every steps (1..256) and
+ * whenever the parameters or dt changed since the last checkpoint, up to
+ * max_steps steps in total; the checkpoints take
+ * (ceil(max_steps / checkpoint_every) + 16) * dim * pitch floats.  Supported
+ * systems: LINEAR, HARMONIC, WILSON_COWAN, LORENZ (FF_ERR_UNSUPPORTED for HH3
+ * and while particle reset is on).  ff_reset and ff_set_state end the tape.
+ * Errors: FF_ERR_INVALID_ARG for checkpoint_every outside 1..256 or
+ * max_steps < 1; FF_ERR_STATE without particles; FF_ERR_OOM. */
+ff_status ff_tape_begin(ff_system* sys, int64_t checkpoint_every, int64_t max_steps);
+
+/* Release the tape's memory (no-op without a tape). */
+ff_status ff_tape_end(ff_system* sys);
+
+/* Reverse sweep over the tape.  dL_dxT_dev: dL/dx at the current state, SoA
+ * [dim][P] (device, contiguous); dL_dx0_dev receives dL/dx at the tape's start
+ * (device, same layout; may be the same buffer); dL_dp_host receives n_params
+ * doubles: dL/dp summed over all taped steps (parameters changed mid-tape are
+ * treated as one vector), and with a per-particle parameter its entry is the
+ * sum over particles of the derivatives with respect to their own values.
+ * The recomputation runs plain FP32 steps from the checkpoints; the
+ * per-particle parameter sums are FP64 and reduced in a fixed order.
+ * Synchronises.  Errors: FF_ERR_STATE without a tape or after it ended,
+ * FF_ERR_INVALID_ARG for NULL buffers, FF_ERR_CUDA. */
+ff_status ff_backward(ff_system* sys, const float* dL_dxT_dev, float* dL_dx0_dev, double* dL_dp_host);
 
 /* Most groups ff_count_escaped_noalloc accepts (its fixed scratch holds one
  * 64-bit counter per group: 2 KB per GPU). */

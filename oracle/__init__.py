@@ -66,8 +66,8 @@ def _load():
         lib.ffo_jacobians.restype = ctypes.c_int
         lib.ffo_jacobians.argtypes = [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P]
         lib.ffo_tangent.restype = ctypes.c_int
-        lib.ffo_tangent.argtypes = [ctypes.c_int, ctypes.c_int, i64, P, P, ctypes.c_int, ctypes.c_int, P, P, i64,
-                                    P, P, P]
+        lib.ffo_tangent.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, P, P, ctypes.c_int, ctypes.c_int,
+                                    P, P, i64, P, P, P]
         lib.ffo_count_escaped.restype = i64
         lib.ffo_count_escaped.argtypes = [ctypes.c_int, i64, i64, P, P]
         lib.ffo_splat2d.restype = None
@@ -232,8 +232,8 @@ def jacobians(rhs_id, x, params):
     return J, Fp
 
 
-def tangent(rhs_id, x0, params, h, n_steps, pparam_index=-1, pparam=None):
-    """Forward sensitivities of RK4: (x(T) [dim][P], S [P][dim][dim], Q [P][dim][n_params])."""
+def tangent(rhs_id, x0, params, h, n_steps, pparam_index=-1, pparam=None, method=RK4):
+    """Forward sensitivities: (x(T) [dim][P], S [P][dim][dim], Q [P][dim][n_params])."""
     x0 = _c(x0, np.float64)
     dim, P = x0.shape
     p = _c(params, np.float64)
@@ -242,17 +242,17 @@ def tangent(rhs_id, x0, params, h, n_steps, pparam_index=-1, pparam=None):
     xT = np.empty_like(x0)
     S = np.empty((P, dim, dim))
     Q = np.empty((P, dim, p.size))
-    rc = _load().ffo_tangent(rhs_id, dim, P, _ptr(x0), _ptr(p), p.size, pparam_index, _ptr(pp), _ptr(hh),
+    rc = _load().ffo_tangent(rhs_id, method, dim, P, _ptr(x0), _ptr(p), p.size, pparam_index, _ptr(pp), _ptr(hh),
                              int(n_steps), _ptr(xT), _ptr(S), _ptr(Q))
     if rc != 0:
         raise ValueError("ffo_tangent: bad arguments or system without derivatives")
     return xT, S, Q
 
 
-def mse_gradients(rhs_id, x0, params, h, n_steps, target, pparam_index=-1, pparam=None):
+def mse_gradients(rhs_id, x0, params, h, n_steps, target, pparam_index=-1, pparam=None, method=RK4):
     """Loss L = (1/P) sum_i |x_i(T) - t_i|^2 and its gradients from the forward sensitivities:
     dL/dx0 [dim][P] and dL/dp [n_params] (with a per-particle parameter, its column is summed)."""
-    xT, S, Q = tangent(rhs_id, x0, params, h, n_steps, pparam_index, pparam)
+    xT, S, Q = tangent(rhs_id, x0, params, h, n_steps, pparam_index, pparam, method)
     P = xT.shape[1]
     r = xT - target
     L = float((r * r).sum() / P)

@@ -466,17 +466,18 @@ static int aug_rhs(int rhs_id, int dim, int np, const double *y, const double *p
     return 0;
 }
 
-/* Forward sensitivities of the RK4 trajectories: classical RK4 applied to the
- * variational system, which gives exactly the derivatives of the discrete RK4
- * map (the stages of the augmented system are the chain rule of the stages of
+/* Forward sensitivities of the trajectories: the stepper (RK4 or Euler)
+ * applied to the variational system, which gives exactly the derivatives of
+ * the discrete map (the stages of the augmented system are the chain rule of the stages of
  * the original one).  Per particle i: xT[k*P+i], S[i][dim][dim] = d x(T) / d x0,
  * Q[i][dim][n_params] = d x(T) / d p (with pparam_index >= 0 that column is the
  * derivative with respect to the particle's own value).  Returns 0, or -1. */
-int ffo_tangent(int rhs_id, int dim, int64_t P, const double *x0, const double *params, int n_params,
+int ffo_tangent(int rhs_id, int method, int dim, int64_t P, const double *x0, const double *params, int n_params,
                 int pparam_index, const double *pparam, const double *h, int64_t n_steps,
                 double *xT, double *S, double *Q)
 {
     if (!rhs_dim_ok(rhs_id, dim, n_params) || dim > 8 || n_params > 64 || n_steps < 0) return -1;
+    if (method != FFO_RK4 && method != FFO_EULER) return -1;
     if (pparam_index >= n_params || (pparam_index >= 0 && !pparam)) return -1;
     const int n = dim + dim * dim + dim * n_params;
     double y[FFO_AUG_MAX], k1[FFO_AUG_MAX], k2[FFO_AUG_MAX], k3[FFO_AUG_MAX], k4[FFO_AUG_MAX], ys[FFO_AUG_MAX];
@@ -492,6 +493,10 @@ int ffo_tangent(int rhs_id, int dim, int64_t P, const double *x0, const double *
         double hh = h[i];
         for (int64_t s = 0; s < n_steps; ++s) {
             if (aug_rhs(rhs_id, dim, n_params, y, p, k1)) return -1;
+            if (method == FFO_EULER) {  /* Euler on the variational system: the derivative of x + h f(x) */
+                for (int a = 0; a < n; ++a) y[a] = y[a] + hh * k1[a];
+                continue;
+            }
             for (int a = 0; a < n; ++a) ys[a] = y[a] + (hh / 2.0) * k1[a];
             aug_rhs(rhs_id, dim, n_params, ys, p, k2);
             for (int a = 0; a < n; ++a) ys[a] = y[a] + (hh / 2.0) * k2[a];

@@ -69,6 +69,8 @@ _SIGS = {
     "ff_backward": [_P, _P, _P, _P],
     "ff_count_escaped_noalloc": [_P, ctypes.c_int, _I64, _I64, _P, ctypes.c_int, _P, _P],
     "ff_set_reset": [_P, _P, _P, ctypes.c_double, ctypes.c_int],
+    "ff_tape_begin": [_P, _I64, _I64],
+    "ff_tape_end": [_P],
     "ff_get_reset_state": [_P, _P, _P, ctypes.c_int],
 }
 
@@ -255,11 +257,26 @@ def ff_set_launch(sys, particles_per_thread=1, block=256, blocks_per_sm=0, max_s
                                int(max_steps_per_launch)))
 
 
-def ff_backward(sys, dL_dxT, dL_dx0, dL_dp):
-    a, _, _ka = _buf(dL_dxT)
-    b, _, _kb = _buf(dL_dx0)
+def ff_tape_begin(sys, checkpoint_every=100, max_steps=1):
+    _check(lib().ff_tape_begin(sys, int(checkpoint_every), int(max_steps)))
+
+
+def ff_tape_end(sys):
+    _check(lib().ff_tape_end(sys))
+
+
+def ff_backward(sys, dL_dxT, dL_dx0, dL_dp=None):
+    """Reverse sweep: dL_dxT / dL_dx0 device buffers [dim][P]; returns dL/dp (host float64)."""
+    a, dev_a, _ka = _buf(dL_dxT)
+    b, dev_b, _kb = _buf(dL_dx0)
+    if not (dev_a and dev_b):
+        raise ValueError("dL_dxT and dL_dx0 must be device buffers")
+    n_params = ctypes.c_int(0)
+    if dL_dp is None:
+        dL_dp = np.zeros(FF_MAX_PARAMS, np.float64)
     c, _, _kc = _buf(dL_dp, np.float64)
     _check(lib().ff_backward(sys, a, b, c))
+    return dL_dp
 
 
 FF_NOALLOC_MAX_GROUPS = 256
@@ -329,6 +346,15 @@ class System:
 
     def step(self, n_steps, dt):
         ff_step(self.handle, n_steps, dt)
+
+    def tape_begin(self, checkpoint_every=100, max_steps=1):
+        ff_tape_begin(self.handle, checkpoint_every, max_steps)
+
+    def tape_end(self):
+        ff_tape_end(self.handle)
+
+    def backward(self, dL_dxT, dL_dx0, n_params):
+        return ff_backward(self.handle, dL_dxT, dL_dx0, np.zeros(max(n_params, 1), np.float64))[:n_params]
 
     def set_reset(self, bound_lo=None, bound_hi=None, t_max=0.0, check_every=1):
         ff_set_reset(self.handle, bound_lo, bound_hi, t_max, check_every)

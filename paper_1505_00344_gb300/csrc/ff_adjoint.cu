@@ -1,0 +1,343 @@
+// ff_adjoint.cu -- discrete adjoint of the RK4 / Euler integrator (not part of
+// the paper): gradients of a loss of the final states with respect to the
+// initial states and the parameters, by reverse sweeps over checkpointed chunks.
+//
+// One thread per particle walks the chunks in reverse with the adjoint state
+// lambda = dL/dx in registers.  A chunk of L <= M*M steps is recomputed from its
+// checkpoint twice: once to place sub-checkpoints every M steps (local memory),
+// then per sub-segment (in reverse) to put its <= M states in registers, which
+// the reverse RK4 steps consume from last to first.  Parameter gradients are
+// summed per particle in FP32 within a chunk, added to FP64 per chunk, and
+// reduced over particles through per-block FP64 partials in fixed order.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ff.h"
+#include "ff_adjoint.h"
+#include "ff_device.cuh"
+
+namespace ff {
+
+// ---------------------------------------------------------------------------
+// Vector-Jacobian products: jx = J(x)^T v and jp += F_p(x)^T v, differentiated
+// by hand from the right-hand sides in ff_device.cuh.
+// ---------------------------------------------------------------------------
+template <class R> struct Vjp;
+
+template <> struct Vjp<Lorenz> {
+    // f = (s (y - x), x (r - z) - y, x y - b z)
+    __device__ __forceinline__ static void apply(const float (&x)[3], const float* p, const float (&v)[3],
+                                                 float (&jx)[3], float* jp) {
+        const float s = p[0], r = p[1], b = p[2];
+        jx[0] = fmaf(-s, v[0], fmaf(r - x[2], v[1], x[1] * v[2]));
+        jx[1] = fmaf(s, v[0], fmaf(x[0], v[2], -v[1]));
+        jx[2] = fmaf(-x[0], v[1], -b * v[2]);
+        jp[0] = fmaf(x[1] - x[0], v[0], jp[0]);
+        jp[1] = fmaf(x[0], v[1], jp[1]);
+        jp[2] = fmaf(-x[2], v[2], jp[2]);
+    }
+};
+
+template <> struct Vjp<Harmonic> {
+    // f = (v, -w^2 x)
+    __device__ __forceinline__ static void apply(const float (&x)[2], const float* p, const float (&v)[2],
+                                                 float (&jx)[2], float* jp) {
+        const float w = p[0];
+        jx[0] = -(w * w) * v[1];
+        jx[1] = v[0];
+        jp[0] = fmaf(-2.0f * w * x[0], v[1], jp[0]);
+    }
+};
+
+template <> struct Vjp<WilsonCowan> {
+    // f_E = (-E + S(aE)) / tauE, f_I = (-I + S(aI)) / tauI, S' = gain S (1 - S)
+    __device__ __forceinline__ static void apply(const float (&x)[2], const float* p, const float (&v)[2],
+                                                 float (&jx)[2], float* jp) {
+        const float E = x[0], I = x[1];
+        const float wEE = p[0], wEI = p[1], wIE = p[2], wII = p[3], tE = p[6], tI = p[7], g = p[8], th = p[9];
+        const float aE = fmaf(wEE, E, fmaf(-wEI, I, p[4]));
+        const float aI = fmaf(wIE, E, fmaf(-wII, I, p[5]));
+        const float g2 = g * kLog2e;
+        const float SE = __fdividef(1.0f, 1.0f + exp2f(g2 * (th - aE)));
+        const float SI = __fdividef(1.0f, 1.0f + exp2f(g2 * (th - aI)));
+        const float sE = SE * (1.0f - SE), sI = SI * (1.0f - SI);  // S'/gain
+        const float uE = __fdividef(v[0], tE), uI = __fdividef(v[1], tI);  // v_k / tau_k
+        const float dE = g * sE * uE, dI = g * sI * uI;                   // S'(a) v / tau
+        jx[0] = fmaf(dE, wEE, -uE) + dI * wIE;
+        jx[1] = -dE * wEI - fmaf(dI, wII, uI);
+        jp[0] = fmaf(dE, E, jp[0]);
+        jp[1] = fmaf(-dE, I, jp[1]);
+        jp[2] = fmaf(dI, E, jp[2]);
+        jp[3] = fmaf(-dI, I, jp[3]);
+        jp[4] += dE;
+        jp[5] += dI;
+        jp[6] = fmaf(-(SE - E), __fdividef(uE, tE), jp[6]);   // d f_E / d tauE = -f_E / tauE
+        jp[7] = fmaf(-(SI - I), __fdividef(uI, tI), jp[7]);
+        jp[8] = fmaf(sE * (aE - th), uE, fmaf(sI * (aI - th), uI, jp[8]));
+        jp[9] = jp[9] - dE - dI;
+    }
+};
+
+template <> struct Vjp<Linear> {
+    // f = A x (A padded to 8x8 row-major)
+    __device__ __forceinline__ static void apply(const float (&x)[8], const float* p, const float (&v)[8],
+                                                 float (&jx)[8], float* jp) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float s = 0.f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s = fmaf(p[i * 8 + k], v[i], s);
+            jx[k] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) jp[i * 8 + k] = fmaf(v[i], x[k], jp[i * 8 + k]);
+    }
+};
+
+// One forward step (plain FP32, unshifted) used by the recomputation.
+template <class R, int METHOD>
+__device__ __forceinline__ void fwd_step(float (&x)[R::DIM], float h, const float* p) {
+    constexpr int D = R::DIM;
+    if (METHOD == FF_EULER) {
+        float k[D];
+        R::f(x, p, k);
+#pragma unroll
+        for (int i = 0; i < D; ++i) x[i] = fmaf(h, k[i], x[i]);
+        return;
+    }
+    const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
+    float k[D], xs[D], acc[D];
+    R::f(x, p, k);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { acc[i] = k[i]; xs[i] = fmaf(h2, k[i], x[i]); }
+    R::f(xs, p, k);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { acc[i] = fmaf(2.0f, k[i], acc[i]); xs[i] = fmaf(h2, k[i], x[i]); }
+    R::f(xs, p, k);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { acc[i] = fmaf(2.0f, k[i], acc[i]); xs[i] = fmaf(h, k[i], x[i]); }
+    R::f(xs, p, k);
+#pragma unroll
+    for (int i = 0; i < D; ++i) x[i] = fmaf(h6, acc[i] + k[i], x[i]);
+}
+
+// Reverse of one step at state x: lambda <- (d step / d x)^T lambda, and the
+// parameter contributions added to jp.  RK4 with stages x1 = x, x2 = x + h/2 k1,
+// x3 = x + h/2 k2, x4 = x + h k3 and x' = x + h/6 (k1 + 2 k2 + 2 k3 + k4):
+//   l4 = h/6 lam,           m4 = J(x4)^T l4
+//   l3 = h/3 lam + h m4,    m3 = J(x3)^T l3
+//   l2 = h/3 lam + h/2 m3,  m2 = J(x2)^T l2
+//   l1 = h/6 lam + h/2 m2,  m1 = J(x1)^T l1
+//   lam <- lam + m1 + m2 + m3 + m4,  jp += sum_s F_p(x_s)^T l_s.
+template <class R, int METHOD>
+__device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[R::DIM], float h, const float* p,
+                                         float* jp) {
+    constexpr int D = R::DIM;
+    if (METHOD == FF_EULER) {
+        float l[D], m[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) l[i] = h * lam[i];
+        Vjp<R>::apply(x, p, l, m, jp);
+#pragma unroll
+        for (int i = 0; i < D; ++i) lam[i] += m[i];
+        return;
+    }
+    const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
+    float k[D], x2[D], x3[D], x4[D];
+    R::f(x, p, k);
+#pragma unroll
+    for (int i = 0; i < D; ++i) x2[i] = fmaf(h2, k[i], x[i]);
+    R::f(x2, p, k);
+#pragma unroll
+    for (int i = 0; i < D; ++i) x3[i] = fmaf(h2, k[i], x[i]);
+    R::f(x3, p, k);
+#pragma unroll
+    for (int i = 0; i < D; ++i) x4[i] = fmaf(h, k[i], x[i]);
+    float l[D], m[D], sum[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) l[i] = h6 * lam[i];
+    Vjp<R>::apply(x4, p, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { sum[i] = m[i]; l[i] = fmaf(h3, lam[i], h * m[i]); }
+    Vjp<R>::apply(x3, p, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { sum[i] += m[i]; l[i] = fmaf(h3, lam[i], h2 * m[i]); }
+    Vjp<R>::apply(x2, p, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < D; ++i) { sum[i] += m[i]; l[i] = fmaf(h6, lam[i], h2 * m[i]); }
+    Vjp<R>::apply(x, p, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < D; ++i) lam[i] = lam[i] + (sum[i] + m[i]);
+}
+
+template <class R, int METHOD, bool PP, int M>
+__global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ AdjointArgs a) {
+    constexpr int D = R::DIM, NP = R::NP;
+    __shared__ double red[8][NP > 16 ? 1 : NP];  // per-warp partials (blocks of at most 256 threads)
+    double gacc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) gacc[q] = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        int g = 0;
+#pragma unroll
+        for (int q = 1; q < FF_MAX_GROUPS; ++q)
+            if (q < a.n_groups && i >= a.gstart[q]) g = q;
+        float lam[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) lam[k] = (k < a.dim) ? a.lam_in[k * a.n + i] : 0.0f;
+        const float pv = PP ? a.pparam[i] : 0.0f;
+        for (int c = a.n_chunks - 1; c >= 0; --c) {
+            const AdjChunk& ch = a.chunks[c];
+            float p[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) p[q] = (PP && q == a.pidx) ? pv : ch.p[q];
+            const float h = ch.gh[g];
+            const int L = ch.n_steps;
+            const float* ck = a.ckpt + (int64_t)ch.ckpt * a.dim * a.pitch;
+            float x[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) x[k] = (k < a.dim) ? ck[k * a.pitch + i] : 0.0f;
+            // sub-checkpoints every M steps
+            float cp[M][D];
+            int nsub = 0;
+            for (int base = 0; base < L; base += M, ++nsub) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) cp[nsub][k] = x[k];
+                const int nq = min(M, L - base);
+                for (int r = 0; r < nq; ++r) fwd_step<R, METHOD>(x, h, p);
+            }
+            float jp[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) jp[q] = 0.0f;
+            for (int sq = nsub - 1; sq >= 0; --sq) {
+                const int nq = min(M, L - sq * M);
+                float st[M][D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) x[k] = cp[sq][k];
+#pragma unroll
+                for (int r = 0; r < M; ++r) {
+                    if (r < nq) {
+#pragma unroll
+                        for (int k = 0; k < D; ++k) st[r][k] = x[k];
+                        if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
+                    }
+                }
+#pragma unroll
+                for (int r = M - 1; r >= 0; --r)
+                    if (r < nq) adj_step<R, METHOD>(st[r], lam, h, p, jp);
+            }
+#pragma unroll
+            for (int q = 0; q < NP; ++q) gacc[q] += (double)jp[q];
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+            if (k < a.dim) a.lam_out[k * a.n + i] = lam[k];
+    }
+    // per-block partial sums of the parameter gradient, in a fixed order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if constexpr (NP <= 16) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            double v = gacc[q];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) red[warp][q] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < NP) {
+            double v = 0.0;
+            for (int w = 0; w < nwarps; ++w) v += red[w][threadIdx.x];
+            a.partial[(int64_t)blockIdx.x * a.np_stride + threadIdx.x] = v;
+        }
+    } else {
+        // many parameters (the linear test system): one partial per thread, summed by the host-side pass
+        for (int q = 0; q < NP; ++q) {
+            double v = gacc[q];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) a.partial[((int64_t)blockIdx.x * nwarps + warp) * a.np_stride + q] = v;
+        }
+    }
+}
+
+// Sum of the per-block (or per-warp) partials, in a fixed order.
+__global__ void reduce_partials_kernel(const double* partial, int64_t rows, int np, int np_stride, double* out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= np) return;
+    double s = 0.0;
+    for (int64_t r = 0; r < rows; ++r) s += partial[r * np_stride + q];
+    out[q] = s;
+}
+
+template <class R, int METHOD, bool PP, int M>
+static cudaError_t launch_one(const AdjointArgs& a0, int block, int num_sms, cudaStream_t s, int64_t* rows) {
+    AdjointArgs a = a0;
+    auto kernel = adjoint_kernel<R, METHOD, PP, M>;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    int64_t need = (a.n + block - 1) / block;
+    int64_t cap = (int64_t)occ * num_sms;
+    if (cap > a.max_blocks) cap = a.max_blocks;  // rows of the partial-sum buffer
+    const int grid = (int)(need < cap ? need : cap);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    kernel<<<grid, block, 0, s>>>(a);
+    *rows = R::NP <= 16 ? grid : (int64_t)grid * (block / 32);
+    return cudaGetLastError();
+}
+
+template <class R, int M>
+static cudaError_t launch_m(int method, bool pp, const AdjointArgs& a, int block, int num_sms, cudaStream_t s,
+                            int64_t* rows) {
+    if (method == FF_RK4)
+        return pp ? launch_one<R, FF_RK4, true, M>(a, block, num_sms, s, rows)
+                  : launch_one<R, FF_RK4, false, M>(a, block, num_sms, s, rows);
+    return pp ? launch_one<R, FF_EULER, true, M>(a, block, num_sms, s, rows)
+              : launch_one<R, FF_EULER, false, M>(a, block, num_sms, s, rows);
+}
+
+template <class R>
+static cudaError_t launch_r(int method, bool pp, int m, const AdjointArgs& a, int block, int num_sms, cudaStream_t s,
+                            int64_t* rows) {
+    switch (m) {
+    case 4: return launch_m<R, 4>(method, pp, a, block, num_sms, s, rows);
+    case 8: return launch_m<R, 8>(method, pp, a, block, num_sms, s, rows);
+    case 16: return launch_m<R, 16>(method, pp, a, block, num_sms, s, rows);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+bool adjoint_supported(int rhs_id) {
+    return rhs_id == FF_RHS_LORENZ || rhs_id == FF_RHS_WILSON_COWAN || rhs_id == FF_RHS_HARMONIC ||
+           rhs_id == FF_RHS_LINEAR;
+}
+
+int adjoint_sub_steps(int64_t checkpoint_every) {
+    if (checkpoint_every <= 16) return 4;
+    if (checkpoint_every <= 64) return 8;
+    return 16;
+}
+
+int64_t adjoint_partial_rows(int num_sms) { return (int64_t)num_sms * 8 * 8; }
+
+cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const AdjointArgs& a, int num_sms,
+                           cudaStream_t s, double* dL_dp_dev, int n_params_kernel) {
+    const int block = 128;
+    int64_t rows = 0;
+    cudaError_t e;
+    switch (rhs_id) {
+    case FF_RHS_LORENZ: e = launch_r<Lorenz>(method, pp, m, a, block, num_sms, s, &rows); break;
+    case FF_RHS_WILSON_COWAN: e = launch_r<WilsonCowan>(method, pp, m, a, block, num_sms, s, &rows); break;
+    case FF_RHS_HARMONIC: e = launch_r<Harmonic>(method, pp, m, a, block, num_sms, s, &rows); break;
+    case FF_RHS_LINEAR: e = launch_r<Linear>(method, pp, m, a, block, num_sms, s, &rows); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    reduce_partials_kernel<<<(n_params_kernel + 63) / 64, 64, 0, s>>>(a.partial, rows, n_params_kernel, a.np_stride,
+                                                                       dL_dp_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace ff

@@ -1,0 +1,45 @@
+// ff_adjoint.h -- argument blocks and launcher of the discrete adjoint.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ff.h"
+
+namespace ff {
+
+// One checkpointed chunk of a taped run: n_steps steps from checkpoint `ckpt`
+// with parameters p (kernel layout) and the groups' signed steps gh.
+struct AdjChunk {
+    int n_steps;
+    int ckpt;
+    float p[FF_MAX_PARAMS];
+    float gh[FF_MAX_GROUPS];
+};
+
+struct AdjointArgs {
+    const float* ckpt;       // checkpoints, slot c at ckpt + c * dim * pitch (SoA planes)
+    const AdjChunk* chunks;  // device table, in time order
+    int n_chunks;
+    int dim;
+    const float* lam_in;     // dL/dx(T), SoA [dim][n], contiguous
+    float* lam_out;          // dL/dx(0), same layout (may alias lam_in)
+    const float* pparam;     // per-particle parameter values (PP only)
+    int pidx;
+    int np_stride;           // doubles per partial row
+    double* partial;         // per-block (or per-warp) FP64 partial sums of dL/dp
+    int64_t max_blocks;      // rows available in `partial` / warps per block
+    int64_t n;               // particles
+    int64_t pitch;           // floats between checkpoint planes
+    int n_groups;
+    int pad_;
+    int64_t gstart[FF_MAX_GROUPS];
+};
+
+bool adjoint_supported(int rhs_id);
+int adjoint_sub_steps(int64_t checkpoint_every);  // M with M * M >= checkpoint_every (at most 256)
+int64_t adjoint_partial_rows(int num_sms);
+cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const AdjointArgs& a, int num_sms,
+                           cudaStream_t s, double* dL_dp_dev, int n_params_kernel);
+
+}  // namespace ff

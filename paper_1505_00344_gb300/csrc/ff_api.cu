@@ -11,8 +11,11 @@
 #include <cuda_runtime.h>
 
 #include "ff.h"
+#include "ff_adjoint.h"
 #include "ff_aux.h"
 #include "ff_device.cuh"
+
+#include <vector>
 
 namespace {
 
@@ -112,6 +115,17 @@ struct ff_system {
     ff::ResetTable* d_reset_table = nullptr;
     ff::ResetTable h_reset_table = {};
     bool reset_table_dirty = true;
+    // adjoint tape
+    bool tape_on = false;
+    int64_t tape_every = 0, tape_slots = 0;
+    float* d_ckpt = nullptr;
+    ff::AdjChunk* d_chunks = nullptr;
+    double* d_partial = nullptr;
+    double* d_dp = nullptr;
+    int64_t partial_blocks = 0;
+    std::vector<ff::AdjChunk> chunks;
+    int64_t params_version = 0, chunk_version = -1;
+    double chunk_dt = 0.0;
 };
 
 namespace {
@@ -213,6 +227,10 @@ ff_status ff_destroy_system(ff_system* s) {
     cudaFree(s->d_age);
     cudaFree(s->d_resets);
     cudaFree(s->d_reset_table);
+    cudaFree(s->d_ckpt);
+    cudaFree(s->d_chunks);
+    cudaFree(s->d_partial);
+    cudaFree(s->d_dp);
     delete s;
     return FF_OK;
 }
@@ -277,6 +295,7 @@ ff_status ff_reset(ff_system* s) {
     s->t_fwd = s->t_bwd = s->c_fwd = s->c_bwd = 0.0;
     s->stepped = false;
     s->steps_total = 0;
+    s->tape_on = false;  // the state the tape started from is gone
     ff_status st = clear_reset_state(s);
     if (st != FF_OK) return st;
     return FF_OK;
@@ -294,6 +313,7 @@ ff_status ff_set_particle_param(ff_system* s, int param_index, double lo, double
     if (!s) return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param: system is NULL");
     if (param_index == -1) {
         s->pparam_index = -1;
+        s->params_version++;
         return FF_OK;
     }
     if (param_index < 0 || param_index >= s->n_params)
@@ -309,6 +329,7 @@ ff_status ff_set_particle_param(ff_system* s, int param_index, double lo, double
     if (e != cudaSuccess) return cuda_fail(e, "linspace kernel launch");
     s->pparam_index = param_index;
     s->pparam_linspace = true;
+    s->params_version++;
     return FF_OK;
 }
 
@@ -330,6 +351,7 @@ ff_status ff_set_particle_param_values(ff_system* s, int param_index, const floa
     if (e != cudaSuccess) return cuda_fail(e, "ff_set_particle_param_values: copy");
     s->pparam_index = param_index;
     s->pparam_linspace = false;
+    s->params_version++;
     return FF_OK;
 }
 
@@ -354,6 +376,7 @@ ff_status ff_set_params(ff_system* s, const double* params, int n_params) {
     // Parameters travel by value in each launch's argument block, so the new
     // values are seen exactly by the launches enqueued after this call.
     memcpy(s->params, params, sizeof(double) * n_params);
+    s->params_version++;
     return FF_OK;
 }
 
@@ -386,6 +409,8 @@ ff_status ff_set_reset(ff_system* s, const double* bound_lo, const double* bound
         for (int k = 0; k < s->dim; ++k)
             if (bound_lo[k] > bound_hi[k]) return fail(FF_ERR_INVALID_ARG, "ff_set_reset: bound_lo[%d] > bound_hi[%d]", k, k);
     }
+    if (check_every > 0 && s->tape_on)
+        return fail(FF_ERR_UNSUPPORTED, "ff_set_reset: particle reset cannot be taped for the adjoint");
     DeviceScope dev(s->device);
     if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_set_reset: set device");
     if (check_every > 0 && !s->d_age) {
@@ -454,15 +479,8 @@ static ff_status upload_reset_table(ff_system* s) {
     return FF_OK;
 }
 
-ff_status ff_step(ff_system* s, int64_t n_steps, double dt) {
-    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_step: system is NULL");
-    if (n_steps < 0) return fail(FF_ERR_INVALID_ARG, "ff_step: n_steps %lld < 0", (long long)n_steps);
-    if (!std::isfinite(dt)) return fail(FF_ERR_INVALID_ARG, "ff_step: dt not finite");
-    if (s->n_particles < 1) return fail(FF_ERR_STATE, "ff_step: no particles seeded");
-    if (n_steps == 0) return FF_OK;
-    DeviceScope dev(s->device);
-    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_step: set device");
-
+// Launch the integrator for n_steps steps of size dt (no argument checks).
+static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt) {
     ff::IntegrateArgs a{};
     a.x = s->d_state;
     a.comp = s->d_comp;
@@ -507,12 +525,155 @@ ff_status ff_step(ff_system* s, int64_t n_steps, double dt) {
         left -= chunk;
         s->steps_total += chunk;
     }
+    return FF_OK;
+}
+
+// Taped stepping: checkpoint the state at every chunk start; a chunk ends after
+// tape_every steps or when the parameters or dt change.
+static ff_status taped_steps(ff_system* s, int64_t n_steps, double dt) {
+    int64_t left = n_steps;
+    while (left > 0) {
+        const bool need_new = s->chunks.empty() || s->chunks.back().n_steps >= s->tape_every ||
+                              s->chunk_version != s->params_version || s->chunk_dt != dt;
+        if (need_new) {
+            if ((int64_t)s->chunks.size() >= s->tape_slots)
+                return fail(FF_ERR_STATE, "ff_step: the tape is full (raise max_steps in ff_tape_begin)");
+            ff::AdjChunk c{};
+            c.n_steps = 0;
+            c.ckpt = (int)s->chunks.size();
+            for (int q = 0; q < s->n_params; ++q) c.p[kernel_param_index(s, q)] = (float)s->params[q];
+            for (int g = 0; g < s->n_groups; ++g) c.gh[g] = (float)(s->groups[g].direction * dt);
+            const size_t bytes = sizeof(float) * (size_t)s->pitch * s->dim;
+            cudaError_t e = cudaMemcpyAsync(s->d_ckpt + (int64_t)c.ckpt * s->dim * s->pitch, s->d_state, bytes,
+                                            cudaMemcpyDeviceToDevice, s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "ff_step: checkpoint copy");
+            s->chunks.push_back(c);
+            s->chunk_version = s->params_version;
+            s->chunk_dt = dt;
+        }
+        int64_t take = s->tape_every - s->chunks.back().n_steps;
+        if (take > left) take = left;
+        ff_status st = integrate_steps(s, take, dt);
+        if (st != FF_OK) return st;
+        s->chunks.back().n_steps += (int)take;
+        left -= take;
+    }
+    return FF_OK;
+}
+
+ff_status ff_step(ff_system* s, int64_t n_steps, double dt) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_step: system is NULL");
+    if (n_steps < 0) return fail(FF_ERR_INVALID_ARG, "ff_step: n_steps %lld < 0", (long long)n_steps);
+    if (!std::isfinite(dt)) return fail(FF_ERR_INVALID_ARG, "ff_step: dt not finite");
+    if (s->n_particles < 1) return fail(FF_ERR_STATE, "ff_step: no particles seeded");
+    if (n_steps == 0) return FF_OK;
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_step: set device");
+    ff_status st = s->tape_on ? taped_steps(s, n_steps, dt) : integrate_steps(s, n_steps, dt);
+    if (st != FF_OK) return st;
     bool any_fwd = false, any_bwd = false;
     for (int g = 0; g < s->n_groups; ++g) (s->groups[g].direction > 0 ? any_fwd : any_bwd) = true;
     const double span = (double)n_steps * dt;
     if (any_fwd) kahan_add(s->t_fwd, s->c_fwd, span);
     if (any_bwd) kahan_add(s->t_bwd, s->c_bwd, -span);
     s->stepped = true;
+    return FF_OK;
+}
+
+static void free_tape(ff_system* s) {
+    cudaFree(s->d_ckpt);
+    cudaFree(s->d_chunks);
+    cudaFree(s->d_partial);
+    cudaFree(s->d_dp);
+    s->d_ckpt = nullptr;
+    s->d_chunks = nullptr;
+    s->d_partial = nullptr;
+    s->d_dp = nullptr;
+    s->chunks.clear();
+    s->tape_on = false;
+}
+
+ff_status ff_tape_begin(ff_system* s, int64_t checkpoint_every, int64_t max_steps) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_tape_begin: system is NULL");
+    if (checkpoint_every < 1 || checkpoint_every > 256)
+        return fail(FF_ERR_INVALID_ARG, "ff_tape_begin: checkpoint_every must be 1..256");
+    if (max_steps < 1) return fail(FF_ERR_INVALID_ARG, "ff_tape_begin: max_steps < 1");
+    if (!ff::adjoint_supported(s->rhs_id))
+        return fail(FF_ERR_UNSUPPORTED, "ff_tape_begin: no adjoint for this system yet");
+    if (s->check_every > 0) return fail(FF_ERR_UNSUPPORTED, "ff_tape_begin: particle reset is on");
+    if (s->n_particles < 1) return fail(FF_ERR_STATE, "ff_tape_begin: no particles seeded");
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_tape_begin: set device");
+    cudaError_t e = cudaStreamSynchronize(s->stream);  // earlier work may still read the old tape
+    if (e != cudaSuccess) return cuda_fail(e, "ff_tape_begin: synchronise");
+    free_tape(s);
+    const int64_t slots = (max_steps + checkpoint_every - 1) / checkpoint_every + 16;
+    s->partial_blocks = ff::adjoint_partial_rows(s->num_sms);
+    e = cudaMalloc(&s->d_ckpt, sizeof(float) * (size_t)slots * s->dim * s->pitch);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_chunks, sizeof(ff::AdjChunk) * (size_t)slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_partial, sizeof(double) * (size_t)s->partial_blocks * FF_MAX_PARAMS);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_dp, sizeof(double) * FF_MAX_PARAMS);
+    if (e != cudaSuccess) {
+        free_tape(s);
+        return cuda_fail(e, "ff_tape_begin: allocation");
+    }
+    s->tape_every = checkpoint_every;
+    s->tape_slots = slots;
+    s->chunk_version = -1;
+    s->tape_on = true;
+    return FF_OK;
+}
+
+ff_status ff_tape_end(ff_system* s) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_tape_end: system is NULL");
+    DeviceScope dev(s->device);
+    cudaStreamSynchronize(s->stream);
+    free_tape(s);
+    return FF_OK;
+}
+
+ff_status ff_backward(ff_system* s, const float* dL_dxT_dev, float* dL_dx0_dev, double* dL_dp_host) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_backward: system is NULL");
+    if (!dL_dxT_dev || !dL_dx0_dev || !dL_dp_host) return fail(FF_ERR_INVALID_ARG, "ff_backward: NULL buffer");
+    if (!s->tape_on) return fail(FF_ERR_STATE, "ff_backward: no tape (call ff_tape_begin before stepping)");
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_backward: set device");
+    double dp[FF_MAX_PARAMS] = {};
+    if (s->chunks.empty()) {  // nothing taped: the map is the identity
+        cudaError_t e = cudaMemcpyAsync(dL_dx0_dev, dL_dxT_dev, sizeof(float) * (size_t)s->dim * s->n_particles,
+                                        cudaMemcpyDeviceToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "ff_backward: copy");
+        for (int q = 0; q < s->n_params; ++q) dL_dp_host[q] = 0.0;
+        return FF_OK;
+    }
+    cudaError_t e = cudaMemcpyAsync(s->d_chunks, s->chunks.data(), sizeof(ff::AdjChunk) * s->chunks.size(),
+                                    cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_backward: chunk table upload");
+    ff::AdjointArgs a{};
+    a.ckpt = s->d_ckpt;
+    a.chunks = s->d_chunks;
+    a.n_chunks = (int)s->chunks.size();
+    a.dim = s->dim;
+    a.lam_in = dL_dxT_dev;
+    a.lam_out = dL_dx0_dev;
+    a.pparam = s->d_pparam;
+    a.pidx = s->pparam_index >= 0 ? kernel_param_index(s, s->pparam_index) : -1;
+    a.np_stride = FF_MAX_PARAMS;
+    a.partial = s->d_partial;
+    a.max_blocks = s->partial_blocks / 8;  // room for 8 rows (warps) per block
+    a.n = s->n_particles;
+    a.pitch = s->pitch;
+    a.n_groups = s->n_groups;
+    for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
+    const int np_kernel = s->rhs_id == FF_RHS_LINEAR ? 64 : s->n_params;
+    e = ff::launch_adjoint(s->rhs_id, s->method, s->pparam_index >= 0, ff::adjoint_sub_steps(s->tape_every), a,
+                           s->num_sms, s->stream, s->d_dp, np_kernel);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_backward: adjoint launch");
+    e = cudaMemcpyAsync(dp, s->d_dp, sizeof(double) * np_kernel, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_backward: gradient download");
+    for (int q = 0; q < s->n_params; ++q) dL_dp_host[q] = dp[kernel_param_index(s, q)];
     return FF_OK;
 }
 
@@ -619,6 +780,7 @@ ff_status ff_set_state(ff_system* s, const float* src, int src_is_device) {
         e = cudaMemsetAsync(s->d_comp, 0, sizeof(float) * (size_t)s->pitch * s->dim, s->stream);
     if (e == cudaSuccess && !src_is_device) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "ff_set_state: copy");
+    s->tape_on = false;
     return clear_reset_state(s);
 }
 
@@ -648,10 +810,6 @@ ff_status ff_system_info(ff_system* s, int64_t* n_particles, int64_t* pitch, int
     return FF_OK;
 }
 
-ff_status ff_backward(ff_system* s, const float* dL_dxT_dev, float* dL_dx0_dev, double* dL_dp_host) {
-    (void)s; (void)dL_dxT_dev; (void)dL_dx0_dev; (void)dL_dp_host;
-    return fail(FF_ERR_UNSUPPORTED, "ff_backward: the adjoint integrator is not built yet");
-}
 
 }  // extern "C"
 

@@ -92,7 +92,11 @@ def test_host_side_argument_errors(lib):
     assert lib.ff_set_particle_param(None, 0, 0.0, 1.0) == ff.FF_ERR_INVALID_ARG
     assert lib.ff_get_particle_param(None, None, 1, None) == ff.FF_ERR_INVALID_ARG
     assert lib.ff_destroy_system(None) == ff.FF_OK
-    assert lib.ff_backward(None, None, None, None) == ff.FF_ERR_UNSUPPORTED
+    assert lib.ff_backward(None, None, None, None) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_tape_begin(None, 100, 10) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_tape_end(None) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_set_reset(None, None, None, 0.0, 1) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_get_reset_state(None, None, None, 1) == ff.FF_ERR_INVALID_ARG
 
 
 def test_binding_raises_with_message(lib):

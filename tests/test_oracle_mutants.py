@@ -61,6 +61,7 @@ MUTANTS = {
     "jac_wc_cross": ("J[2] = (dSI * wIE) / tauI;", "J[2] = (dSI * wIE) / tauE;"),
     "tangent_no_forcing": ("double s = Fp[i * np + q];", "double s = 0.0;"),
     "tangent_stage": ("for (int a = 0; a < n; ++a) ys[a] = y[a] + hh * k3[a];", "for (int a = 0; a < n; ++a) ys[a] = y[a] + hh * k2[a];"),
+    "tangent_euler_step": ("for (int a = 0; a < n; ++a) y[a] = y[a] + hh * k1[a];", "for (int a = 0; a < n; ++a) y[a] = y[a] + (hh / 2.0) * k1[a];"),
     "escape_threshold": ("if (!(fabs(v) <= 1e30)) esc = 1;", "if (!(fabs(v) < 1e38)) esc = 1;"),
 }
 

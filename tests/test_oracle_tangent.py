@@ -50,6 +50,22 @@ def taylor4(Z):
     return I + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
 
 
+def test_euler_sensitivity_is_matrix_power():
+    A = np.array([[-0.5, 1.0], [-1.0, -0.3]])
+    x0 = np.array([[1.0], [0.3]])
+    h, n = 0.05, 30
+    _, S, _ = oracle.tangent(oracle.LINEAR, x0, A.reshape(-1), h, n, method=oracle.EULER)
+    np.testing.assert_allclose(S[0], np.linalg.matrix_power(np.eye(2) + h * A, n), rtol=1e-13, atol=1e-15)
+    # and the Euler loss gradient matches central differences
+    target = np.array([[0.2], [-0.1]])
+    L, dx0, dp = oracle.mse_gradients(oracle.LINEAR, x0, A.reshape(-1), h, n, target, method=oracle.EULER)
+    for k in range(2):
+        e = np.zeros_like(x0); e[k, 0] = 1e-6
+        lp = ((oracle.integrate(oracle.LINEAR, x0 + e, A.reshape(-1), h, n, method=oracle.EULER) - target) ** 2).sum()
+        lm = ((oracle.integrate(oracle.LINEAR, x0 - e, A.reshape(-1), h, n, method=oracle.EULER) - target) ** 2).sum()
+        assert abs(dx0[k, 0] - (lp - lm) / 2e-6) <= 1e-7
+
+
 def test_linear_sensitivity_is_matrix_power():
     A = np.array([[-0.5, 1.0, 0.2], [-1.0, -0.3, 0.0], [0.1, 0.4, -0.8]])
     x0 = np.array([[1.0, -0.5], [0.3, 2.0], [-1.2, 0.7]])

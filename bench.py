@@ -210,6 +210,9 @@ def run_ours(args, rank, world, local):
     every = w.get("splat_every_frame", False)
     schedule = {int(k): v for k, v in w.get("schedule", {}).items()}
     base_params = list(w["params"])
+    # the library fuses the splat into the integrator for the packed Lorenz kernel on 4-aligned groups
+    fused = (w["rhs"] == "lorenz" and (args.ppt or 4) in (2, 4) and not (args.kahan or args.reset)
+             and all(sum(g["count"] for g in w["groups"][:k]) % (args.ppt or 4) == 0 for k in range(len(w["groups"]))))
 
     def job(events=None):
         """One whole workload run; returns the number of our kernel launches enqueued."""
@@ -222,14 +225,18 @@ def run_ours(args, rank, world, local):
             if events is not None:
                 events.append(("int0", torch.cuda.Event(enable_timing=True)))
                 events[-1][1].record()
-            sysobj.step(w["steps_per_frame"], w["dt"])
-            launches += 1
+            splat = every or f == w["frames"] - 1
+            if splat:
+                # one frame: step + project + splat (fused into the integrator's last launch
+                # when the packed Lorenz kernel runs; launches counted as the fused kernel)
+                sysobj.step_splat(w["steps_per_frame"], w["dt"], view, image)
+                launches += 1 if fused else 2
+            else:
+                sysobj.step(w["steps_per_frame"], w["dt"])
+                launches += 1
             if events is not None:
                 events.append(("int1", torch.cuda.Event(enable_timing=True)))
                 events[-1][1].record()
-            if every or f == w["frames"] - 1:
-                sysobj.project_splat(view, image)
-                launches += 1
         return launches
 
     for _ in range(args.warmup):
@@ -279,13 +286,16 @@ def run_ours(args, rank, world, local):
     if flops_per_launch:
         achieved = flops_per_launch / (avg_int_ms / 1e3) / 1e12
         packed = (args.ppt or 4) in (2, 4) and not (args.kahan or args.reset)
-        kernel = "lorenz_rk4_x2u_kernel" if packed else "integrate_kernel<Lorenz,RK4>"
+        kernel = ("lorenz_rk4_x2u_kernel<splat>" if fused and every else
+                  "lorenz_rk4_x2u_kernel" if packed else "integrate_kernel<Lorenz,RK4>")
         # DRAM bytes come from the committed ncu summary of the packed kernel on the same sources
         traffic = traffic_from_profile(kernel_source_hash()) if packed and not args.particles else None
         roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / peak_tflops, 4), "traffic": traffic, "kernel": kernel,
                 "peak_basis": f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
                 "algorithmic_bytes_per_launch": 24 * n_work,
+                "launch_window": ("ff_step_splat: image clear + integrator with fused splat" if fused and every
+                                  else "ff_step: integrator"),
                 "avg_launch_ms": round(avg_int_ms, 4)}
         if clk:
             roof["frac_at_sampled_clock"] = round(achieved / (sms * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12), 4)

@@ -211,6 +211,17 @@ ff_status ff_set_params(ff_system* sys, const double* params, int n_params);
 ff_status ff_project_splat(ff_system* sys, const ff_view* view, uint32_t* image,
                            int image_is_device);
 
+/* One frame: exactly ff_step(n_steps, dt) followed by
+ * ff_project_splat(view, image, image_is_device), with the same results.  When
+ * the group-uniform packed Lorenz kernel runs (plain RK4, 2 or 4 particles per
+ * thread, 4-aligned groups, per-particle parameter absent or r, no reset, no
+ * tape, device image) the projection and splat are fused into the last
+ * integrator launch, which counts each particle from the registers that hold
+ * its final state; otherwise the two calls run one after the other.  Errors:
+ * those of ff_step and ff_project_splat. */
+ff_status ff_step_splat(ff_system* sys, int64_t n_steps, double dt, const ff_view* view, uint32_t* image,
+                        int image_is_device);
+
 /* Copy the state out, SoA [dim][P] with P the number of seeded particles
  * (dst holds dim*P floats; host or device).  A host copy synchronises. */
 ff_status ff_get_state(ff_system* sys, float* dst, int dst_is_device);

@@ -60,6 +60,7 @@ _SIGS = {
     "ff_step": [_P, _I64, ctypes.c_double],
     "ff_set_params": [_P, _P, ctypes.c_int],
     "ff_project_splat": [_P, ctypes.POINTER(ff_view), _P, ctypes.c_int],
+    "ff_step_splat": [_P, _I64, ctypes.c_double, ctypes.POINTER(ff_view), _P, ctypes.c_int],
     "ff_get_state": [_P, _P, ctypes.c_int],
     "ff_set_state": [_P, _P, ctypes.c_int],
     "ff_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -225,6 +226,13 @@ def ff_project_splat(sys, view, image):
     _check(lib().ff_project_splat(sys, ctypes.byref(view), ptr, dev))
 
 
+def ff_step_splat(sys, n_steps, dt, view, image):
+    if isinstance(view, dict):
+        view = make_view(**view)
+    ptr, dev, _keep = _buf(image)
+    _check(lib().ff_step_splat(sys, int(n_steps), float(dt), ctypes.byref(view), ptr, dev))
+
+
 def ff_get_state(sys, dst):
     ptr, dev, _keep = _buf(dst, np.float32)
     _check(lib().ff_get_state(sys, ptr, dev))
@@ -367,6 +375,9 @@ class System:
 
     def project_splat(self, view, image):
         ff_project_splat(self.handle, view, image)
+
+    def step_splat(self, n_steps, dt, view, image):
+        ff_step_splat(self.handle, n_steps, dt, view, image)
 
     def get_state(self, dst):
         ff_get_state(self.handle, dst)

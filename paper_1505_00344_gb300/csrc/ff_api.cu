@@ -479,8 +479,10 @@ static ff_status upload_reset_table(ff_system* s) {
     return FF_OK;
 }
 
-// Launch the integrator for n_steps steps of size dt (no argument checks).
-static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt) {
+// Launch the integrator for n_steps steps of size dt (no argument checks).  With
+// `fuse`, the last launch also projects and splats the final states (the caller
+// checked that the group-uniform packed kernel runs).
+static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const ff::ViewArgs* fuse = nullptr) {
     ff::IntegrateArgs a{};
     a.x = s->d_state;
     a.comp = s->d_comp;
@@ -514,13 +516,20 @@ static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt) {
         const double steps = (s->t_max > 0.0 && dt != 0.0) ? std::ceil(s->t_max / std::fabs(dt)) : 0.0;
         a.max_age = steps <= 0.0 ? 0u : (steps >= 4294967295.0 ? 4294967295u : (uint32_t)steps);
     }
+    a.n_real = s->n_particles;
     int64_t left = n_steps;
     while (left > 0) {
         int64_t chunk = (s->max_steps > 0 && left > s->max_steps) ? s->max_steps : left;
         if (chunk > ((int64_t)1 << 30)) chunk = (int64_t)1 << 30;  // kernels count steps in 32 bits
         a.n_steps = chunk;
         a.step0 = s->steps_total;
-        cudaError_t e = ff::launch_integrate(s->rhs_id, s->method, kahan, pp, a, shape, s->stream);
+        cudaError_t e;
+        if (fuse && chunk == left) {
+            a.view = *fuse;
+            e = ff::launch_integrate_lorenz_splat(pp, a, shape, s->stream);
+        } else {
+            e = ff::launch_integrate(s->rhs_id, s->method, kahan, pp, a, shape, s->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "integrator launch");
         left -= chunk;
         s->steps_total += chunk;
@@ -677,20 +686,20 @@ ff_status ff_backward(ff_system* s, const float* dL_dxT_dev, float* dL_dx0_dev, 
     return FF_OK;
 }
 
-ff_status ff_project_splat(ff_system* s, const ff_view* v, uint32_t* image, int image_is_device) {
-    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_project_splat: system is NULL");
-    if (!v || !image) return fail(FF_ERR_INVALID_ARG, "ff_project_splat: view or image is NULL");
+// Checked view -> kernel view arguments (axes, window or camera, image size, group mask).
+static ff_status view_args(const ff_system* s, const ff_view* v, ff::ViewArgs* out) {
+    ff::ViewArgs a{};
     if (v->ndim_view != 2 && v->ndim_view != 3)
         return fail(FF_ERR_INVALID_ARG, "ff_project_splat: ndim_view %d not 2 or 3", v->ndim_view);
     if (v->width < 1 || v->height < 1 || (int64_t)v->width * v->height >= ((int64_t)1 << 31))
         return fail(FF_ERR_INVALID_ARG, "ff_project_splat: image %d x %d out of range", v->width, v->height);
-    ff::SplatArgs a{};
     for (int q = 0; q < v->ndim_view; ++q) {
         const int ax = v->axes[q];
         if (ax < 0 || ax > s->dim || (ax == s->dim && s->pparam_index < 0))
             return fail(FF_ERR_INVALID_ARG, "ff_project_splat: axis %d out of range", ax);
-        a.ax[q] = (ax == s->dim) ? s->d_pparam : s->d_state + (int64_t)ax * s->pitch;
+        a.axes[q] = ax;
     }
+    a.ndim = v->ndim_view;
     a.W = v->width;
     a.H = v->height;
     a.Wf = (float)v->width;
@@ -712,12 +721,25 @@ ff_status ff_project_splat(ff_system* s, const ff_view* v, uint32_t* image, int 
         a.s0 = (float)((double)v->width / 2.0);
         a.s1 = (float)((double)v->height / 2.0);
     }
+    const uint32_t all = (s->n_groups >= 32) ? 0xffffffffu : ((1u << s->n_groups) - 1u);
+    a.mask = v->group_mask & all;
+    *out = a;
+    return FF_OK;
+}
+
+ff_status ff_project_splat(ff_system* s, const ff_view* v, uint32_t* image, int image_is_device) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_project_splat: system is NULL");
+    if (!v || !image) return fail(FF_ERR_INVALID_ARG, "ff_project_splat: view or image is NULL");
+    ff::SplatArgs a{};
+    ff_status vst = view_args(s, v, &a.v);
+    if (vst != FF_OK) return vst;
+    for (int q = 0; q < v->ndim_view; ++q)
+        a.ax[q] = (a.v.axes[q] == s->dim) ? s->d_pparam : s->d_state + (int64_t)a.v.axes[q] * s->pitch;
     a.n = s->n_particles;
     a.n_groups = s->n_groups;
     uint32_t all = (s->n_groups >= 32) ? 0xffffffffu : ((1u << s->n_groups) - 1u);
-    a.mask = v->group_mask & all;
     for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
-    const bool masked = a.mask != all;
+    const bool masked = a.v.mask != all;
 
     DeviceScope dev(s->device);
     if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_project_splat: set device");
@@ -738,10 +760,10 @@ ff_status ff_project_splat(ff_system* s, const ff_view* v, uint32_t* image, int 
     }
     if (e == cudaSuccess && !v->accumulate) e = cudaMemsetAsync(target, 0, bytes, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "ff_project_splat: image clear/upload");
-    a.image = target;
+    a.v.image = target;
     bool strip = false;  // a linspace parameter on an axis: consecutive particles share a column or row
     for (int q = 0; q < v->ndim_view; ++q) strip = strip || (v->axes[q] == s->dim && s->pparam_linspace);
-    if (s->n_particles > 0 && a.mask != 0) {
+    if (s->n_particles > 0 && a.v.mask != 0) {
         e = ff::launch_splat(a, v->ndim_view, masked, strip, s->num_sms, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "splat kernel launch");
     }
@@ -750,6 +772,46 @@ ff_status ff_project_splat(ff_system* s, const ff_view* v, uint32_t* image, int 
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "ff_project_splat: image download");
     }
+    return FF_OK;
+}
+
+ff_status ff_step_splat(ff_system* s, int64_t n_steps, double dt, const ff_view* v, uint32_t* image,
+                        int image_is_device) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_step_splat: system is NULL");
+    if (!v || !image) return fail(FF_ERR_INVALID_ARG, "ff_step_splat: view or image is NULL");
+    ff::ViewArgs va{};
+    ff_status st = view_args(s, v, &va);
+    if (st != FF_OK) return st;
+    // the fused path: group-uniform packed Lorenz kernel, device image, plain stepping
+    ff::IntegrateArgs probe{};
+    probe.n_groups = s->n_groups;
+    for (int g = 0; g < s->n_groups; ++g) probe.gstart[g] = s->groups[g].start;
+    probe.pidx = s->pparam_index >= 0 ? kernel_param_index(s, s->pparam_index) : -1;
+    ff::LaunchShape shape{s->ppt, s->block, s->blocks_per_sm, s->num_sms};
+    const bool fusable = image_is_device && s->rhs_id == FF_RHS_LORENZ && !s->tape_on && s->check_every == 0 &&
+                         n_steps > 0 && s->n_particles > 0 && std::isfinite(dt) &&
+                         ff::lorenz_uniform_packed(s->method, (s->flags & FF_FLAG_KAHAN) != 0,
+                                                   s->pparam_index >= 0, probe, shape);
+    if (!fusable) {
+        st = ff_step(s, n_steps, dt);
+        if (st != FF_OK) return st;
+        return ff_project_splat(s, v, image, image_is_device);
+    }
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_step_splat: set device");
+    if (!v->accumulate) {
+        cudaError_t e = cudaMemsetAsync(image, 0, sizeof(uint32_t) * (size_t)v->width * v->height, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "ff_step_splat: image clear");
+    }
+    va.image = image;
+    st = integrate_steps(s, n_steps, dt, &va);
+    if (st != FF_OK) return st;
+    bool any_fwd = false, any_bwd = false;
+    for (int g = 0; g < s->n_groups; ++g) (s->groups[g].direction > 0 ? any_fwd : any_bwd) = true;
+    const double span = (double)n_steps * dt;
+    if (any_fwd) kahan_add(s->t_fwd, s->c_fwd, span);
+    if (any_bwd) kahan_add(s->t_bwd, s->c_bwd, -span);
+    s->stepped = true;
     return FF_OK;
 }
 

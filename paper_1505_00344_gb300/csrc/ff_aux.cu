@@ -51,40 +51,12 @@ __global__ void linspace_kernel(float* out, int64_t P, double lo, double width) 
 // operation is rounded on its own (explicit _rn intrinsics, no contraction)
 // so the pixel decision is reproducible bit for bit.
 // ---------------------------------------------------------------------------
-// Pixel (column fc, row fr as floats) of one projected particle; false if it
-// is not drawn.
-template <int NDV>
-__device__ __forceinline__ bool pixel_of(const SplatArgs& a, float u, float v, float w, int& col, int& row) {
-    float fc, fr;
-    if (NDV == 2) {
-        fc = floorf(__fmul_rn(__fsub_rn(u, a.lo0), a.s0));
-        fr = floorf(__fmul_rn(__fsub_rn(v, a.lo1), a.s1));
-    } else {
-        float cl[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float t = __fadd_rn(__fmul_rn(a.m[j], u), __fmul_rn(a.m[4 + j], v));
-            t = __fadd_rn(t, __fmul_rn(a.m[8 + j], w));
-            cl[j] = __fadd_rn(t, a.m[12 + j]);
-        }
-        if (!(cl[3] > 0.0f)) return false;
-        const float nx = __fdiv_rn(cl[0], cl[3]);
-        const float ny = __fdiv_rn(cl[1], cl[3]);
-        fc = floorf(__fmul_rn(__fsub_rn(nx, -1.0f), a.s0));
-        fr = floorf(__fmul_rn(__fsub_rn(ny, -1.0f), a.s1));
-    }
-    if (!(fc >= 0.0f && fc < a.Wf && fr >= 0.0f && fr < a.Hf)) return false;
-    col = (int)fc;
-    row = (int)fr;
-    return true;
-}
-
 __device__ __forceinline__ bool group_selected(const SplatArgs& a, int64_t i) {
     int g = 0;
 #pragma unroll
     for (int q = 1; q < FF_MAX_GROUPS; ++q)
         if (q < a.n_groups && i >= a.gstart[q]) g = q;
-    return (a.mask >> g) & 1u;
+    return (a.v.mask >> g) & 1u;
 }
 
 // Global mode: each thread projects 4 consecutive particles (one 16-byte load
@@ -106,8 +78,8 @@ __global__ void __launch_bounds__(kSplatBlock) splat_global_kernel(const __grid_
         for (int j = 0; j < 4; ++j) {
             const int64_t i = i0 + j;
             int col, row;
-            if (i < a.n && (!MASKED || group_selected(a, i)) && pixel_of<NDV>(a, u[j], v[j], w[j], col, row))
-                atomicAdd(&a.image[(int64_t)row * a.W + col], 1u);
+            if (i < a.n && (!MASKED || group_selected(a, i)) && pixel_of<NDV>(a.v, u[j], v[j], w[j], col, row))
+                atomicAdd(&a.v.image[(int64_t)row * a.v.W + col], 1u);
         }
     }
 }
@@ -135,7 +107,7 @@ __global__ void __launch_bounds__(kSplatBlock) splat_shared_kernel(const __grid_
             int col = -1, row = -1;
             if (i < a.n && (!MASKED || group_selected(a, i))) {
                 const float w = NDV == 3 ? a.ax[2][i] : 0.0f;
-                if (!pixel_of<NDV>(a, a.ax[0][i], a.ax[1][i], w, col, row)) col = -1;
+                if (!pixel_of<NDV>(a.v, a.ax[0][i], a.ax[1][i], w, col, row)) col = -1;
             }
             cols[q] = col;
             rows[q] = row;
@@ -168,13 +140,13 @@ __global__ void __launch_bounds__(kSplatBlock) splat_shared_kernel(const __grid_
                     const uint32_t v = bins[b];
                     if (v) {
                         const int r = b / bw;
-                        atomicAdd(&a.image[(int64_t)(br0 + r) * a.W + bc0 + (b - r * bw)], v);
+                        atomicAdd(&a.v.image[(int64_t)(br0 + r) * a.v.W + bc0 + (b - r * bw)], v);
                     }
                 }
             } else {
 #pragma unroll
                 for (int q = 0; q < kSplatPerThread; ++q)
-                    if (cols[q] >= 0) atomicAdd(&a.image[(int64_t)rows[q] * a.W + cols[q]], 1u);
+                    if (cols[q] >= 0) atomicAdd(&a.v.image[(int64_t)rows[q] * a.v.W + cols[q]], 1u);
             }
         }
         __syncthreads();

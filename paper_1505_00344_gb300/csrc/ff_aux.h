@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "ff.h"
+#include "ff_project.cuh"
 
 namespace ff {
 
@@ -26,15 +27,10 @@ constexpr int kSplatChunk = kSplatBlock * kSplatPerThread;
 constexpr int kSplatBins = 8192;  // 32 KB shared-memory histogram
 
 struct SplatArgs {
+    ViewArgs v;
     const float* ax[3];  // planes of the view axes (16-byte aligned; readable up to n rounded to 4)
     int64_t n;           // particles
-    uint32_t* image;
-    int W, H;
-    float Wf, Hf;
-    float lo0, s0, lo1, s1;  // 2D window (3D: lo = -1, s = W/2, H/2)
-    float m[16];             // 3D Model-View-Projection, column-major
     int n_groups;
-    uint32_t mask;
     int64_t gstart[FF_MAX_GROUPS];
 };
 

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "ff.h"
+#include "ff_project.cuh"
 
 namespace ff {
 
@@ -43,6 +44,9 @@ struct IntegrateArgs {
     int64_t step0;                   // global step number before this launch
     int check_every;
     uint32_t max_age;                // 0 = no age limit
+    // fused projection + splat after the last step (group-uniform packed Lorenz kernel only)
+    int64_t n_real;                  // seeded particles (the rest are padding)
+    ViewArgs view;
 };
 
 // Reset data of a system, in device memory (read only when a particle resets).
@@ -651,7 +655,7 @@ __global__ void __launch_bounds__(512) lorenz_rk4_x2_kernel(const __grid_constan
 // argument block instead of living in per-thread registers, which leaves room
 // for more resident warps.  Used when every group starts on a multiple of the
 // particles per thread and a per-particle parameter, if any, is r.
-template <bool PP_R, int NPAIR>
+template <bool PP_R, int NPAIR, bool SPLAT = false>
 __global__ void __launch_bounds__(512) lorenz_rk4_x2u_kernel(const __grid_constant__ IntegrateArgs a) {
     constexpr int PPT = 2 * NPAIR;
     int g = 0;
@@ -715,6 +719,20 @@ __global__ void __launch_bounds__(512) lorenz_rk4_x2u_kernel(const __grid_consta
         Vec<PPT>::store(a.x + i0, xs);
         Vec<PPT>::store(a.x + a.pitch + i0, ys);
         Vec<PPT>::store(a.x + 2 * a.pitch + i0, zs);
+        if (SPLAT && ((a.view.mask >> g) & 1u)) {
+            // the render step on the final states held in registers: one count per drawn particle
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                if (i0 + j >= a.n_real) continue;
+                const float rj = PP_R ? r[j] : a.p[1];
+                auto coord = [&](int ax) { return ax == 0 ? xs[j] : ax == 1 ? ys[j] : ax == 2 ? zs[j] : rj; };
+                const float u = coord(a.view.axes[0]), v = coord(a.view.axes[1]), w = coord(a.view.axes[2]);
+                int col, row;
+                const bool drawn = a.view.ndim == 2 ? pixel_of<2>(a.view, u, v, w, col, row)
+                                                    : pixel_of<3>(a.view, u, v, w, col, row);
+                if (drawn) atomicAdd(&a.view.image[(int64_t)row * a.view.W + col], 1u);
+            }
+        }
     }
 }
 
@@ -731,6 +749,9 @@ cudaError_t launch_integrate(int rhs_id, int method, bool kahan, bool pp, const 
                              const LaunchShape& shape, cudaStream_t stream);
 cudaError_t launch_integrate_lorenz(int method, bool kahan, bool pp, const IntegrateArgs& a,
                                     const LaunchShape& shape, cudaStream_t stream);
+bool lorenz_uniform_packed(int method, bool kahan, bool pp, const IntegrateArgs& a, const LaunchShape& shape);
+cudaError_t launch_integrate_lorenz_splat(bool pp, const IntegrateArgs& a, const LaunchShape& shape,
+                                          cudaStream_t stream);
 cudaError_t launch_integrate_wc(int method, bool kahan, bool pp, const IntegrateArgs& a,
                                 const LaunchShape& shape, cudaStream_t stream);
 cudaError_t launch_integrate_hh3(int method, bool kahan, bool pp, const IntegrateArgs& a,

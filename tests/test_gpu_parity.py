@@ -433,3 +433,63 @@ def test_state_errors():
     with pytest.raises(ff.FFError) as e:
         groups_ok.seed(1, LZ_BOX[0], LZ_BOX[1], 1, 99)
     assert e.value.status == ff.FF_ERR_STATE
+
+
+# ---------------------------------------------------------------------------
+# ff_step_splat: identical to ff_step + ff_project_splat (fused or not)
+# ---------------------------------------------------------------------------
+FUSE_VIEWS = {
+    "xz": dict(ndim_view=2, axes=(0, 2), lo=(-30.0, 0.0), hi=(30.0, 60.0), width=640, height=360),
+    "xz_group1": dict(ndim_view=2, axes=(0, 2), lo=(-30.0, 0.0), hi=(30.0, 60.0), width=640, height=360,
+                      group_mask=0b10),
+    "cam3d": dict(ndim_view=3, axes=(0, 1, 2), width=300, height=200,
+                  mvp=look_at_perspective((60.0, 60.0, 80.0), (0.0, 0.0, 25.0), (0.0, 0.0, 1.0), 50.0, 1.5, 1.0,
+                                          500.0)),
+    "r_axis": dict(ndim_view=2, axes=(3, 2), lo=(0.0, 0.0), hi=(60.0, 120.0), width=512, height=256),
+}
+
+
+@pytest.mark.parametrize("view_name,counts,ppt,kahan,pp,accumulate", [
+    ("xz", (3000, 1000), 4, False, False, False),        # fused
+    ("xz_group1", (3000, 1000), 2, False, False, True),  # fused, masked, accumulating
+    ("cam3d", (1001,), 4, False, False, False),           # fused, ragged count (padding not drawn)
+    ("r_axis", (2048, 1024), 4, False, True, False),      # fused with per-particle r
+    ("xz", (3000, 1001), 4, False, False, False),        # misaligned group: separate calls
+    ("xz", (3000, 1000), 4, True, False, False),         # Kahan: separate calls
+    ("xz", (3000, 1000), 1, False, False, False),        # scalar kernel: separate calls
+])
+def test_step_splat_equals_step_then_splat(view_name, counts, ppt, kahan, pp, accumulate):
+    view = dict(FUSE_VIEWS[view_name], accumulate=int(accumulate))
+    groups = [G(c, *LZ_BOX, 1 if t == 0 else -1, 300 + t) for t, c in enumerate(counts)]
+    a = make_system("lorenz", LORENZ_PARAMS, groups, 3, ppt=ppt, kahan=kahan)
+    b = make_system("lorenz", LORENZ_PARAMS, groups, 3, ppt=ppt, kahan=kahan)
+    if pp:
+        a.set_particle_param(1, 0.0, 60.0)
+        b.set_particle_param(1, 0.0, 60.0)
+    H, W = view["height"], view["width"]
+    ia = torch.zeros((H, W), dtype=torch.int32, device="cuda") + (7 if accumulate else 0)
+    ib = ia.clone()
+    for _ in range(3):
+        a.step_splat(150, 0.001, view, ia)
+        b.step(150, 0.001)
+        b.project_splat(view, ib)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(get_state(a), get_state(b))
+    assert torch.equal(ia, ib)
+    assert int(ia.sum()) > 0
+
+
+def test_step_splat_fallbacks_wc_and_host_image():
+    groups = [G(999, [0, 0], [1, 1], 1, 3), G(1000, [0, 0], [1, 1], -1, 4)]
+    a = make_system("wilson_cowan", WC_PARAMS, groups, 2)
+    b = make_system("wilson_cowan", WC_PARAMS, groups, 2)
+    view = dict(ndim_view=2, axes=(0, 1), lo=(0.0, 0.0), hi=(1.0, 1.0), width=64, height=64)
+    ha = np.zeros((64, 64), np.uint32)
+    a.step_splat(50, 0.01, view, ha)  # host image: separate calls inside
+    b.step(50, 0.01)
+    hb = np.zeros((64, 64), np.uint32)
+    b.project_splat(view, hb)
+    np.testing.assert_array_equal(get_state(a), get_state(b))
+    np.testing.assert_array_equal(ha, hb)
+    with pytest.raises(ff.FFError):
+        a.step_splat(1, 0.01, dict(view, ndim_view=5), ha)

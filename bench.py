@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="time the taped forward and the adjoint (ff_backward) instead of the plain job")
     ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--batch", default="", help="time a batched workload (hh3_batch64, mixed_batch256)")
+    ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--checkpoint-every", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -501,6 +503,53 @@ def run_adjoint(args, rank, world, local):
             "ms": {"plain": med(t_plain), "taped_forward": med(t_fwd), "backward": med(t_bwd)}}
 
 
+def run_batch(args, rank, world, local):
+    """A batched workload: ff_batch_step (one graph launch, autotuned launch shapes) against
+    stepping the same systems one after the other with ff_step."""
+    import torch
+    import paper_1505_00344_gb300 as ff
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream().cuda_stream
+    ws = W.batch_workload(args.batch)
+    systems = [ff.System.from_workload(w, stream=stream) for w in ws]
+    dts = [w["dt"] for w in ws]
+    n = args.batch_steps
+    units = sum(total_particles(w) for w in ws) * n
+    b = ff.Batch(systems, stream=stream)
+    b.autotune(dts, trial_steps=max(8, min(64, n // 10)))
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(e)
+
+    def batched():
+        b.step(n, dts)
+
+    def one_by_one():
+        for s_, dt in zip(systems, dts):
+            s_.step(n, dt)
+
+    for _ in range(args.warmup):
+        batched()
+    tb = [timed(batched) for _ in range(max(1, args.steps))]
+    to = [timed(one_by_one) for _ in range(max(1, args.steps))]
+    med = statistics.median
+    return {"metric": "particle-RK4-steps/sec (batched systems)", "value": units / (med(tb) / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": med(tb),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.batch, "systems": len(ws), "particles": units // n, "rk4_steps": n,
+                       "launch": b.describe().strip().split("\n")},
+            "one_by_one": units / (med(to) / 1e3), "speedup_vs_one_by_one": med(to) / med(tb),
+            "gpu_launches": len({(w["rhs"], w["method"]) for w in ws})}  # one kernel per family in the graph
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -508,6 +557,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.adjoint:
         out = run_adjoint(args, rank, world, local)
+    elif args.batch:
+        out = run_batch(args, rank, world, local)
     else:
         out = run_ours(args, rank, world, local)
     if rank == 0 and out is not None:

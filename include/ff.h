@@ -279,6 +279,39 @@ ff_status ff_tape_end(ff_system* sys);
  * FF_ERR_INVALID_ARG for NULL buffers, FF_ERR_CUDA. */
 ff_status ff_backward(ff_system* sys, const float* dL_dxT_dev, float* dL_dx0_dev, double* dL_dp_host);
 
+/* Batched stepping (not part of the paper): several systems -- each with its
+ * own right-hand side, method, parameters, groups and particle count -- advance
+ * together.  Members of one family (same right-hand side, method and presence
+ * of a per-particle parameter) run in one persistent launch over a table of work tiles, each block taking tiles
+ * round-robin; the families are parallel branches of one CUDA graph, captured
+ * once per step count and replayed by every ff_batch_step with that count.
+ * The systems keep owning their state; the batch borrows them until
+ * ff_batch_destroy, and they must not be destroyed, re-seeded, taped or given
+ * a particle reset, and must keep or lack their per-particle parameter
+ * meanwhile (ff_batch_step then returns FF_ERR_STATE).
+ * Members run the scalar integrator (no packed Lorenz kernel, no fused splat).
+ *
+ * ff_batch_create: systems on one device, each with particles, no Kahan flag,
+ *   no reset, no tape; cuda_stream orders the batch's work (NULL = legacy
+ *   default stream).  Errors: FF_ERR_INVALID_ARG (NULL/duplicate systems,
+ *   different devices), FF_ERR_UNSUPPORTED (Kahan, reset, tape), FF_ERR_STATE
+ *   (no particles), FF_ERR_CUDA / FF_ERR_OOM.
+ * ff_batch_step: n_steps (0..2^30) steps; dt[i] is the step of system i
+ *   (host array of n_systems doubles).  Parameters set with ff_set_params
+ *   take effect at the next call.  Asynchronous.
+ * ff_batch_autotune: times every launch shape (particles per thread 1/2/4 for
+ *   dimension <= 4, blocks of 64..512 threads) of each family on the members'
+ *   own data for trial_steps steps (twice), keeps the fastest, and restores the
+ *   members' states exactly.  Synchronises.
+ * ff_batch_describe: one line per family: members, launch shape, tiles, tuned
+ *   rate (NUL-terminated, truncated to text_len). */
+typedef struct ff_batch ff_batch;
+ff_status ff_batch_create(ff_system* const* systems, int n_systems, void* cuda_stream, ff_batch** out);
+ff_status ff_batch_step(ff_batch* batch, int64_t n_steps, const double* dt);
+ff_status ff_batch_autotune(ff_batch* batch, const double* dt, int64_t trial_steps);
+ff_status ff_batch_describe(ff_batch* batch, char* text, int text_len);
+ff_status ff_batch_destroy(ff_batch* batch);
+
 /* Most groups ff_count_escaped_noalloc accepts (its fixed scratch holds one
  * 64-bit counter per group: 2 KB per GPU). */
 #define FF_NOALLOC_MAX_GROUPS 256

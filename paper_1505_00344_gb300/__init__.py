@@ -71,6 +71,11 @@ _SIGS = {
     "ff_count_escaped_noalloc": [_P, ctypes.c_int, _I64, _I64, _P, ctypes.c_int, _P, _P],
     "ff_set_reset": [_P, _P, _P, ctypes.c_double, ctypes.c_int],
     "ff_tape_begin": [_P, _I64, _I64],
+    "ff_batch_create": [_P, ctypes.c_int, _P, ctypes.POINTER(_P)],
+    "ff_batch_step": [_P, _I64, _P],
+    "ff_batch_autotune": [_P, _P, _I64],
+    "ff_batch_describe": [_P, ctypes.c_char_p, ctypes.c_int],
+    "ff_batch_destroy": [_P],
     "ff_tape_end": [_P],
     "ff_get_reset_state": [_P, _P, _P, ctypes.c_int],
 }
@@ -305,6 +310,63 @@ def ff_count_escaped_noalloc(state, dim, n_particles, pitch, group_starts, strea
     _check(lib().ff_count_escaped_noalloc(ptr, int(dim), int(n_particles), int(pitch), starts.ctypes.data,
                                           starts.size, _stream_ptr(stream), counts.ctypes.data))
     return counts
+
+
+def ff_batch_create(systems, stream=None):
+    """systems: ff_system handles (or System objects)."""
+    handles = [getattr(x, "handle", x) for x in systems]
+    arr = (_P * len(handles))(*handles)
+    out = _P()
+    _check(lib().ff_batch_create(arr, len(handles), _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def ff_batch_step(batch, n_steps, dt):
+    d, dp = _dbl(dt)
+    _check(lib().ff_batch_step(batch, int(n_steps), dp))
+
+
+def ff_batch_autotune(batch, dt, trial_steps=64):
+    d, dp = _dbl(dt)
+    _check(lib().ff_batch_autotune(batch, dp, int(trial_steps)))
+
+
+def ff_batch_describe(batch):
+    buf = ctypes.create_string_buffer(4096)
+    _check(lib().ff_batch_describe(batch, buf, len(buf)))
+    return buf.value.decode()
+
+
+def ff_batch_destroy(batch):
+    _check(lib().ff_batch_destroy(batch))
+
+
+class Batch:
+    """Owning handle over one ff_batch (the systems stay owned by their System objects)."""
+
+    def __init__(self, systems, stream=None):
+        self.systems = list(systems)  # keep the systems alive as long as the batch
+        self.handle = ff_batch_create(self.systems, stream)
+
+    def step(self, n_steps, dt):
+        ff_batch_step(self.handle, n_steps, dt)
+
+    def autotune(self, dt, trial_steps=64):
+        ff_batch_autotune(self.handle, dt, trial_steps)
+
+    def describe(self):
+        return ff_batch_describe(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ff_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ff_last_error():

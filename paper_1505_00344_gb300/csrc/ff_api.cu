@@ -14,13 +14,24 @@
 #include "ff_adjoint.h"
 #include "ff_aux.h"
 #include "ff_device.cuh"
-
-#include <vector>
+#include "ff_internal.h"
 
 namespace {
-
 thread_local std::string g_last_error;
 
+int rhs_dim_ok(int rhs_id, int dim, int n_params) {
+    switch (rhs_id) {
+    case FF_RHS_LINEAR: return dim >= 1 && dim <= 8 && n_params == dim * dim;
+    case FF_RHS_HARMONIC: return dim == 2 && n_params == 1;
+    case FF_RHS_WILSON_COWAN: return dim == 2 && n_params == 10;
+    case FF_RHS_LORENZ: return dim == 3 && n_params == 3;
+    case FF_RHS_HH3: return dim == 15 && n_params == 16;
+    default: return 0;
+    }
+}
+}  // namespace
+
+namespace ff {
 ff_status fail(ff_status code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -37,104 +48,21 @@ ff_status cuda_fail(cudaError_t e, const char* what) {
     return fail(FF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-struct Group {
-    int64_t start, count;
-    int direction;
-    uint64_t seed;
-    double lo[FF_MAX_DIM], hi[FF_MAX_DIM];
-};
-
-// Makes the system's device current for the lifetime of the object.
-struct DeviceScope {
-    int prev = -1;
-    bool changed = false;
-    cudaError_t err = cudaSuccess;
-    explicit DeviceScope(int dev) {
-        err = cudaGetDevice(&prev);
-        if (err == cudaSuccess && prev != dev) {
-            err = cudaSetDevice(dev);
-            changed = (err == cudaSuccess);
-        }
-    }
-    ~DeviceScope() {
-        if (changed) cudaSetDevice(prev);
-    }
-};
-
-bool all_finite(const double* v, int n) {
-    for (int i = 0; i < n; ++i)
-        if (!std::isfinite(v[i])) return false;
-    return true;
-}
-
-int rhs_dim_ok(int rhs_id, int dim, int n_params) {
-    switch (rhs_id) {
-    case FF_RHS_LINEAR: return dim >= 1 && dim <= 8 && n_params == dim * dim;
-    case FF_RHS_HARMONIC: return dim == 2 && n_params == 1;
-    case FF_RHS_WILSON_COWAN: return dim == 2 && n_params == 10;
-    case FF_RHS_LORENZ: return dim == 3 && n_params == 3;
-    case FF_RHS_HH3: return dim == 15 && n_params == 16;
-    default: return 0;
-    }
-}
-
-}  // namespace
-
-struct ff_system {
-    int device = 0;
-    int num_sms = 1;
-    cudaStream_t stream = nullptr;
-    int rhs_id = 0, dim = 0, method = 0;
-    unsigned flags = 0;
-    int n_params = 0;
-    double params[FF_MAX_PARAMS] = {};
-    int64_t capacity = 0, pitch = 0, n_particles = 0;
-    float* d_state = nullptr;
-    float* d_comp = nullptr;
-    float* d_pparam = nullptr;
-    int pparam_index = -1;
-    bool pparam_linspace = false;  // values monotone in the particle index
-    int n_groups = 0;
-    Group groups[FF_MAX_GROUPS] = {};
-    bool stepped = false;
-    double t_fwd = 0, t_bwd = 0, c_fwd = 0, c_bwd = 0;  // Kahan-summed simulated time
-    unsigned long long* d_counter = nullptr;
-    uint32_t* d_stage = nullptr;  // device copy of a host image
-    size_t stage_bytes = 0;
-    // launch shape
-    int ppt = 1, block = 256, blocks_per_sm = 0;
-    int64_t max_steps = 0;
-    // particle reset
-    int64_t steps_total = 0;  // steps since the last ff_reset (global step numbers)
-    int check_every = 0;      // 0 = reset off
-    double t_max = 0.0;
-    bool has_bounds = false;
-    float blo[FF_MAX_DIM] = {}, bhi[FF_MAX_DIM] = {};
-    uint32_t* d_age = nullptr;
-    uint32_t* d_resets = nullptr;
-    ff::ResetTable* d_reset_table = nullptr;
-    ff::ResetTable h_reset_table = {};
-    bool reset_table_dirty = true;
-    // adjoint tape
-    bool tape_on = false;
-    int64_t tape_every = 0, tape_slots = 0;
-    float* d_ckpt = nullptr;
-    ff::AdjChunk* d_chunks = nullptr;
-    double* d_partial = nullptr;
-    double* d_dp = nullptr;
-    int64_t partial_blocks = 0;
-    std::vector<ff::AdjChunk> chunks;
-    int64_t params_version = 0, chunk_version = -1;
-    double chunk_dt = 0.0;
-};
-
-namespace {
-
-// Kernel index of parameter q of the user's vector (LINEAR is padded to 8x8).
 int kernel_param_index(const ff_system* s, int q) {
     if (s->rhs_id == FF_RHS_LINEAR) return (q / s->dim) * 8 + (q % s->dim);
     return q;
 }
+}  // namespace ff
+
+using ff::all_finite;
+using ff::cuda_fail;
+using ff::DeviceScope;
+using ff::fail;
+using ff::Group;
+using ff::kernel_param_index;
+
+
+namespace {
 
 void kahan_add(double& sum, double& comp, double v) {
     double y = v - comp;
@@ -482,8 +410,11 @@ static ff_status upload_reset_table(ff_system* s) {
 // Launch the integrator for n_steps steps of size dt (no argument checks).  With
 // `fuse`, the last launch also projects and splats the final states (the caller
 // checked that the group-uniform packed kernel runs).
-static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const ff::ViewArgs* fuse = nullptr) {
-    ff::IntegrateArgs a{};
+}  // extern "C"
+
+namespace ff {
+void fill_integrate_args(const ff_system* s, double dt, IntegrateArgs* out) {
+    IntegrateArgs a{};
     a.x = s->d_state;
     a.comp = s->d_comp;
     a.pparam = s->d_pparam;
@@ -499,8 +430,27 @@ static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const
         a.gh[g] = (float)(s->groups[g].direction * dt);
     }
     for (int q = 0; q < s->n_params; ++q) a.p[kernel_param_index(s, q)] = (float)s->params[q];
+    a.n_vec = n_work / s->ppt;
+    a.n_real = s->n_particles;
+    *out = a;
+}
+
+void account_steps(ff_system* s, int64_t n_steps, double dt) {
+    bool any_fwd = false, any_bwd = false;
+    for (int g = 0; g < s->n_groups; ++g) (s->groups[g].direction > 0 ? any_fwd : any_bwd) = true;
+    const double span = (double)n_steps * dt;
+    if (any_fwd) kahan_add(s->t_fwd, s->c_fwd, span);
+    if (any_bwd) kahan_add(s->t_bwd, s->c_bwd, -span);
+    s->stepped = true;
+}
+}  // namespace ff
+
+extern "C" {
+
+static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const ff::ViewArgs* fuse = nullptr) {
+    ff::IntegrateArgs a{};
+    ff::fill_integrate_args(s, dt, &a);
     const int ppt = s->ppt;
-    a.n_vec = n_work / ppt;
     ff::LaunchShape shape{ppt, s->block, s->blocks_per_sm, s->num_sms};
     const bool kahan = (s->flags & FF_FLAG_KAHAN) != 0;
     const bool pp = s->pparam_index >= 0;
@@ -516,7 +466,6 @@ static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const
         const double steps = (s->t_max > 0.0 && dt != 0.0) ? std::ceil(s->t_max / std::fabs(dt)) : 0.0;
         a.max_age = steps <= 0.0 ? 0u : (steps >= 4294967295.0 ? 4294967295u : (uint32_t)steps);
     }
-    a.n_real = s->n_particles;
     int64_t left = n_steps;
     while (left > 0) {
         int64_t chunk = (s->max_steps > 0 && left > s->max_steps) ? s->max_steps : left;
@@ -580,12 +529,7 @@ ff_status ff_step(ff_system* s, int64_t n_steps, double dt) {
     if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_step: set device");
     ff_status st = s->tape_on ? taped_steps(s, n_steps, dt) : integrate_steps(s, n_steps, dt);
     if (st != FF_OK) return st;
-    bool any_fwd = false, any_bwd = false;
-    for (int g = 0; g < s->n_groups; ++g) (s->groups[g].direction > 0 ? any_fwd : any_bwd) = true;
-    const double span = (double)n_steps * dt;
-    if (any_fwd) kahan_add(s->t_fwd, s->c_fwd, span);
-    if (any_bwd) kahan_add(s->t_bwd, s->c_bwd, -span);
-    s->stepped = true;
+    ff::account_steps(s, n_steps, dt);
     return FF_OK;
 }
 
@@ -806,12 +750,7 @@ ff_status ff_step_splat(ff_system* s, int64_t n_steps, double dt, const ff_view*
     va.image = image;
     st = integrate_steps(s, n_steps, dt, &va);
     if (st != FF_OK) return st;
-    bool any_fwd = false, any_bwd = false;
-    for (int g = 0; g < s->n_groups; ++g) (s->groups[g].direction > 0 ? any_fwd : any_bwd) = true;
-    const double span = (double)n_steps * dt;
-    if (any_fwd) kahan_add(s->t_fwd, s->c_fwd, span);
-    if (any_bwd) kahan_add(s->t_bwd, s->c_bwd, -span);
-    s->stepped = true;
+    ff::account_steps(s, n_steps, dt);
     return FF_OK;
 }
 

@@ -138,6 +138,42 @@ def _hh3_1M():
     )
 
 
+def batch_workload(name: str) -> list:
+    """Batched workloads: a list of single-system workloads stepped together.
+
+    * ``hh3_batch64``: 64 three-neuron Hodgkin-Huxley systems of 16,384 particles, coupling
+      strengths gsyn = linspace(0, 1, 64), each with its own seeded drive currents.
+    * ``mixed_batch256``: 256 systems cycling Wilson-Cowan, Lorenz and HH3 (system s has type
+      s mod 3) with particle counts drawn log-uniform between 1,024 and 1,048,576 (seeded).
+    """
+    hh = _hh3_1M()
+    if name == "hh3_batch64":
+        out = []
+        for k, g in enumerate(np.linspace(0.0, 1.0, 64)):
+            w = dict(hh, name=f"hh3_batch64_{k}")
+            p = hh3_params(BASE_SEED + 3 + 1000 * k)
+            p[7] = float(g)
+            w["params"] = p
+            w["groups"] = [dict(hh["groups"][0], count=16384, seed=group_seed(3, 0) + 7919 * k)]
+            out.append(w)
+        return out
+    if name == "mixed_batch256":
+        rng = np.random.default_rng(BASE_SEED + 4)
+        sizes = np.rint(np.exp(rng.uniform(np.log(1024), np.log(1048576), 256))).astype(int)
+        bases = (_wc_4k(), _lorenz_4M(), hh)
+        out = []
+        for k, n in enumerate(sizes):
+            b = bases[k % 3]
+            w = dict(b, name=f"mixed_batch256_{k}")
+            if b["rhs"] == "hh3":
+                w["params"] = hh3_params(BASE_SEED + 3 + 1000 * k)
+            g0 = b["groups"][0]
+            w["groups"] = [dict(g0, count=int(n), direction=1, seed=group_seed(4, 0) + 7919 * k)]
+            out.append(w)
+        return out
+    raise KeyError(name)
+
+
 WORKLOADS = {w["name"]: w for w in (_wc_4k(), _lorenz_4M(), _lorenz_bif_8M(), _hh3_1M())}
 
 

@@ -97,6 +97,11 @@ def test_host_side_argument_errors(lib):
     assert lib.ff_tape_end(None) == ff.FF_ERR_INVALID_ARG
     assert lib.ff_set_reset(None, None, None, 0.0, 1) == ff.FF_ERR_INVALID_ARG
     assert lib.ff_get_reset_state(None, None, None, 1) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_batch_create(None, 1, None, ctypes.byref(out)) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_batch_step(None, 1, None) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_batch_autotune(None, None, 8) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_batch_describe(None, None, 0) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_batch_destroy(None) == ff.FF_OK
 
 
 def test_binding_raises_with_message(lib):

@@ -164,6 +164,21 @@ static double hh_vtrap(double v)
     return v / (-expm1(-v / 10.0));
 }
 
+/* d/dv of v / (1 - e^(-v/10)).  With x = v/10 it is g'(x) for g(x) = x / (1 - e^-x),
+ * g'(x) = (1 - e^-x (1 + x)) / (1 - e^-x)^2.  Near x = 0 the numerator cancels, so
+ * there the Taylor series of g' (from g = 1 + x/2 + x^2/12 - x^4/720 + x^6/30240 - ...,
+ * the Bernoulli-number expansion) is used: 1/2 + x/6 - x^3/180 + x^5/5040 - x^7/151200. */
+static double hh_vtrap_deriv(double v)
+{
+    double x = v / 10.0;
+    if (fabs(x) < 1e-2) {
+        double x2 = x * x;
+        return 0.5 + x * (1.0 / 6.0 + x2 * (-1.0 / 180.0 + x2 * (1.0 / 5040.0 - x2 / 151200.0)));
+    }
+    double e = exp(-x), d = -expm1(-x);
+    return (1.0 - e * (1.0 + x)) / (d * d);
+}
+
 /* Hodgkin-Huxley rate functions of the squid axon (Hodgkin & Huxley 1952,
  * cited for Eq. 6-9) in the convention with rest near -65 mV. */
 static double hh_alpha_m(double V) { return 0.1 * hh_vtrap(V + 40.0); }
@@ -428,6 +443,64 @@ static int rhs_jacobians(int rhs_id, int dim, const double *x, const double *p, 
         Fp[1 * 10 + 9] = -dSI / tauI;
         return 0;
     }
+    case FFO_HH3: {
+        /* Eq. 6-11 differentiated term by term.  Gate rates depend on V only;
+         * the rate constants are fixed numbers, not parameters. */
+        double C = p[0], gNa = p[1], gK = p[2], gL = p[3];
+        double ENa = p[4], EK = p[5], EL = p[6], gsyn = p[7], Esyn = p[8];
+        double tau_r = p[12], tau_d = p[13], sig = p[14], theta = p[15];
+        const int np = n_params;
+        for (int i = 0; i < 3; ++i) {
+            const double *xi = x + 5 * i;
+            double V = xi[0], m = xi[1], h = xi[2], n = xi[3], s = xi[4];
+            double s_others = 0.0;
+            for (int j = 0; j < 3; ++j)
+                if (j != i) s_others += x[5 * j + 4];
+            double m3h = m * m * m * h, n4 = n * n * n * n;
+            double Itot = gL * (EL - V) + gNa * m3h * (ENa - V) + gK * n4 * (EK - V) +
+                          gsyn * (Esyn - V) * s_others + p[9 + i];
+            int rV = 5 * i, rm = rV + 1, rh = rV + 2, rn = rV + 3, rs = rV + 4;
+            /* voltage row */
+            J[rV * dim + rV] = (-gL - gNa * m3h - gK * n4 - gsyn * s_others) / C;
+            J[rV * dim + rm] = 3.0 * gNa * m * m * h * (ENa - V) / C;
+            J[rV * dim + rh] = gNa * m * m * m * (ENa - V) / C;
+            J[rV * dim + rn] = 4.0 * gK * n * n * n * (EK - V) / C;
+            for (int j = 0; j < 3; ++j)
+                if (j != i) J[rV * dim + 5 * j + 4] = gsyn * (Esyn - V) / C;
+            Fp[rV * np + 0] = -Itot / (C * C);
+            Fp[rV * np + 1] = m3h * (ENa - V) / C;
+            Fp[rV * np + 2] = n4 * (EK - V) / C;
+            Fp[rV * np + 3] = (EL - V) / C;
+            Fp[rV * np + 4] = gNa * m3h / C;
+            Fp[rV * np + 5] = gK * n4 / C;
+            Fp[rV * np + 6] = gL / C;
+            Fp[rV * np + 7] = (Esyn - V) * s_others / C;
+            Fp[rV * np + 8] = gsyn * s_others / C;
+            Fp[rV * np + 9 + i] = 1.0 / C;
+            /* gates: d/dV of a(V)(1 - y) - b(V) y, and -(a + b) on the diagonal */
+            double am = hh_alpha_m(V), bm = hh_beta_m(V), ah = hh_alpha_h(V), bh = hh_beta_h(V);
+            double an = hh_alpha_n(V), bn = hh_beta_n(V);
+            double dam = 0.1 * hh_vtrap_deriv(V + 40.0), dbm = -bm / 18.0;
+            double dah = -ah / 20.0, dbh = bh * (1.0 - bh) / 10.0;
+            double dan = 0.01 * hh_vtrap_deriv(V + 55.0), dbn = -bn / 80.0;
+            J[rm * dim + rV] = dam * (1.0 - m) - dbm * m;
+            J[rm * dim + rm] = -(am + bm);
+            J[rh * dim + rV] = dah * (1.0 - h) - dbh * h;
+            J[rh * dim + rh] = -(ah + bh);
+            J[rn * dim + rV] = dan * (1.0 - n) - dbn * n;
+            J[rn * dim + rn] = -(an + bn);
+            /* synapse: act = 1 / (1 + exp(-sig (V - theta))), act' = sig act (1 - act) */
+            double act = 1.0 / (1.0 + exp(-sig * (V - theta)));
+            double a1 = act * (1.0 - act);
+            J[rs * dim + rV] = sig * a1 * (1.0 - s) / tau_r;
+            J[rs * dim + rs] = -act / tau_r - 1.0 / tau_d;
+            Fp[rs * np + 12] = -act * (1.0 - s) / (tau_r * tau_r);
+            Fp[rs * np + 13] = s / (tau_d * tau_d);
+            Fp[rs * np + 14] = a1 * (V - theta) * (1.0 - s) / tau_r;
+            Fp[rs * np + 15] = -sig * a1 * (1.0 - s) / tau_r;
+        }
+        return 0;
+    }
     default:
         return -1;
     }
@@ -440,13 +513,13 @@ int ffo_jacobians(int rhs_id, int dim, const double *x, const double *p, int n_p
     return rhs_jacobians(rhs_id, dim, x, p, n_params, J, Fp);
 }
 
-#define FFO_AUG_MAX (8 + 64 + 8 * 64)
+#define FFO_AUG_MAX (16 + 16 * 16 + 16 * 64)
 
 /* Right-hand side of the variational system y = (x, S, Q):
  *   dx/dt = f(x, p),  dS/dt = J(x) S,  dQ/dt = J(x) Q + F_p(x). */
 static int aug_rhs(int rhs_id, int dim, int np, const double *y, const double *p, double *dy)
 {
-    double J[64], Fp[8 * 64];
+    double J[16 * 16], Fp[16 * 64];
     const double *x = y, *S = y + dim, *Q = y + dim + dim * dim;
     double *dx = dy, *dS = dy + dim, *dQ = dy + dim + dim * dim;
     if (rhs_jacobians(rhs_id, dim, x, p, np, J, Fp) != 0) return -1;
@@ -476,7 +549,7 @@ int ffo_tangent(int rhs_id, int method, int dim, int64_t P, const double *x0, co
                 int pparam_index, const double *pparam, const double *h, int64_t n_steps,
                 double *xT, double *S, double *Q)
 {
-    if (!rhs_dim_ok(rhs_id, dim, n_params) || dim > 8 || n_params > 64 || n_steps < 0) return -1;
+    if (!rhs_dim_ok(rhs_id, dim, n_params) || dim > 16 || n_params > 64 || n_steps < 0) return -1;
     if (method != FFO_RK4 && method != FFO_EULER) return -1;
     if (pparam_index >= n_params || (pparam_index >= 0 && !pparam)) return -1;
     const int n = dim + dim * dim + dim * n_params;

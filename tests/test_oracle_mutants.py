@@ -59,6 +59,19 @@ MUTANTS = {
     "jac_lorenz_param": ("Fp[2 * 3 + 2] = -x[2];", "Fp[2 * 3 + 2] = x[2];"),
     "jac_wc_gain": ("Fp[0 * 10 + 8] = SE * (1.0 - SE) * (aE - th) / tauE;", "Fp[0 * 10 + 8] = SE * (1.0 - SE) * aE / tauE;"),
     "jac_wc_cross": ("J[2] = (dSI * wIE) / tauI;", "J[2] = (dSI * wIE) / tauE;"),
+    "jac_hh_leak_dropped": ("J[rV * dim + rV] = (-gL - gNa * m3h - gK * n4 - gsyn * s_others) / C;",
+                            "J[rV * dim + rV] = (-gNa * m3h - gK * n4 - gsyn * s_others) / C;"),
+    "jac_hh_m_power": ("J[rV * dim + rm] = 3.0 * gNa * m * m * h * (ENa - V) / C;",
+                       "J[rV * dim + rm] = 3.0 * gNa * m * m * m * (ENa - V) / C;"),
+    "jac_hh_syn_self": ("if (j != i) J[rV * dim + 5 * j + 4]", "if (j != (i + 1) % 3) J[rV * dim + 5 * j + 4]"),
+    "jac_hh_C_sign": ("Fp[rV * np + 0] = -Itot / (C * C);", "Fp[rV * np + 0] = Itot / (C * C);"),
+    "jac_hh_drive_index": ("Fp[rV * np + 9 + i] = 1.0 / C;", "Fp[rV * np + 9] = 1.0 / C;"),
+    "jac_hh_beta_h_deriv": ("dbh = bh * (1.0 - bh) / 10.0;", "dbh = -bh * (1.0 - bh) / 10.0;"),
+    "jac_hh_gate_diag": ("J[rn * dim + rn] = -(an + bn);", "J[rn * dim + rn] = -(an - bn);"),
+    "jac_hh_theta_sign": ("Fp[rs * np + 15] = -sig * a1 * (1.0 - s) / tau_r;",
+                          "Fp[rs * np + 15] = sig * a1 * (1.0 - s) / tau_r;"),
+    "jac_hh_vtrap_series": ("return 0.5 + x * (1.0 / 6.0 + x2", "return 0.5 + x * (1.0 / 3.0 + x2"),
+    "jac_hh_vtrap_closed": ("return (1.0 - e * (1.0 + x)) / (d * d);", "return (1.0 - e * (1.0 - x)) / (d * d);"),
     "tangent_no_forcing": ("double s = Fp[i * np + q];", "double s = 0.0;"),
     "tangent_stage": ("for (int a = 0; a < n; ++a) ys[a] = y[a] + hh * k3[a];", "for (int a = 0; a < n; ++a) ys[a] = y[a] + hh * k2[a];"),
     "tangent_euler_step": ("for (int a = 0; a < n; ++a) y[a] = y[a] + hh * k1[a];", "for (int a = 0; a < n; ++a) y[a] = y[a] + (hh / 2.0) * k1[a];"),

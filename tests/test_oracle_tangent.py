@@ -12,7 +12,13 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1505_00344_gb300.workloads import LORENZ_PARAMS, WC_PARAMS
+from paper_1505_00344_gb300.workloads import HH3_BASE, LORENZ_PARAMS, WC_PARAMS
+
+
+def hh_state(V1, V2, V3):
+    # neuron i: (V_i, m, h, n, s) with distinct gate values per neuron
+    g = [(0.05, 0.6, 0.32, 0.1), (0.3, 0.2, 0.55, 0.7), (0.9, 0.05, 0.8, 0.45)]
+    return [v for V, gi in zip((V1, V2, V3), g) for v in (V, *gi)]
 
 
 def fd_jac(rid, x, p, eps=1e-6):
@@ -36,13 +42,19 @@ def fd_jac(rid, x, p, eps=1e-6):
     (oracle.WILSON_COWAN, [0.9, 0.1], [3.0, 5.0, 2.0, 1.0, 0.5, -1.0, 1.5, 0.7, 2.0, 3.0]),
     (oracle.HARMONIC, [0.4, -1.2], [2.5]),
     (oracle.LINEAR, [1.0, -2.0, 0.5], list(np.arange(9) * 0.3 - 1.0)),
+    (oracle.HH3, hh_state(-63.0, -20.0, 12.5), HH3_BASE),
+    # V at the removable points of alpha_m (-40) and alpha_n (-55), and just beside them
+    (oracle.HH3, hh_state(-40.0, -55.0, -40.03), HH3_BASE),
+    (oracle.HH3, hh_state(-54.96, -39.5, -85.0), [1.3, 100.0, 30.0, 0.5, 55.0, -70.0, -50.0, 0.9, -75.0,
+                                                   7.0, 11.0, 13.0, 0.3, 6.0, 0.8, -15.0]),
 ])
 def test_jacobians_match_central_differences(rid, x, p):
     J, Fp = oracle.jacobians(rid, x, p)
     Jf, Ff = fd_jac(rid, x, p)
-    scale = max(1.0, np.abs(Jf).max(), np.abs(Ff).max())
-    assert np.abs(J - Jf).max() <= 1e-7 * scale
-    assert np.abs(Fp - Ff).max() <= 1e-7 * scale
+    # per row of f: central differences are good to ~1e-9 of the row's largest entry
+    scale = np.maximum(1.0, np.maximum(np.abs(Jf).max(axis=1), np.abs(Ff).max(axis=1)))[:, None]
+    assert (np.abs(J - Jf) / scale).max() <= 1e-7
+    assert (np.abs(Fp - Ff) / scale).max() <= 1e-7
 
 
 def taylor4(Z):
@@ -92,25 +104,30 @@ def loss(rid, x0, p, h, n, target, **kw):
 @pytest.mark.parametrize("rid,params,box,h,n", [
     (oracle.LORENZ, LORENZ_PARAMS, ([-20, -20, 0], [20, 20, 40]), 0.001, 300),
     (oracle.WILSON_COWAN, WC_PARAMS, ([0, 0], [1, 1]), 0.01, 200),
+    (oracle.HH3, HH3_BASE, ([-80, 0, 0, 0, 0] * 3, [40, 1, 1, 1, 1] * 3), 0.01, 150),
 ])
 def test_mse_gradients_match_finite_differences(rid, params, box, h, n):
     dim = len(box[0])
     x0 = oracle.seed_group(dim, box[0], box[1], 17, count=6).astype(np.float64)
     target = oracle.seed_group(dim, box[0], box[1], 18, count=6).astype(np.float64)
-    hh = np.array([h, -h, h, h, -h, h])
+    # HH3 run backward in time is unstable (the gates leave [0, 1]): forward steps only
+    hh = np.array([h, h, h, h, h, h]) if rid == oracle.HH3 else np.array([h, -h, h, h, -h, h])
     L, dx0, dp = oracle.mse_gradients(rid, x0, params, hh, n, target)
     assert abs(L - loss(rid, x0, params, hh, n, target)) <= 1e-12 * max(1.0, L)
+    # central differences with a step relative to the coordinate; the bar adds their
+    # rounding floor, ~ 50 ulp of the loss divided by the step
     eps = 1e-6
+    floor = 50 * np.finfo(float).eps * max(1.0, L)
     for k in range(dim):
         for i in range(6):
-            e = np.zeros_like(x0); e[k, i] = eps
-            fd = (loss(rid, x0 + e, params, hh, n, target) - loss(rid, x0 - e, params, hh, n, target)) / (2 * eps)
-            assert abs(dx0[k, i] - fd) <= 1e-6 * max(1.0, abs(fd))
+            e = np.zeros_like(x0); e[k, i] = eps * max(1.0, abs(x0[k, i]))
+            fd = (loss(rid, x0 + e, params, hh, n, target) - loss(rid, x0 - e, params, hh, n, target)) / (2 * e[k, i])
+            assert abs(dx0[k, i] - fd) <= 1e-6 * max(1.0, abs(fd)) + floor / e[k, i]
     for q in range(len(params)):
         e = np.zeros(len(params)); e[q] = eps * max(1.0, abs(params[q]))
         fd = (loss(rid, x0, np.add(params, e), hh, n, target) - loss(rid, x0, np.subtract(params, e), hh, n, target)) \
             / (2 * e[q])
-        assert abs(dp[q] - fd) <= 1e-6 * max(1.0, abs(fd))
+        assert abs(dp[q] - fd) <= 1e-6 * max(1.0, abs(fd)) + floor / e[q]
 
 
 def test_per_particle_parameter_column():

@@ -257,9 +257,9 @@ ff_status ff_set_launch(ff_system* sys, int particles_per_thread, int block, int
  * stores a checkpoint of the state every checkpoint_every steps (1..256) and
  * whenever the parameters or dt changed since the last checkpoint, up to
  * max_steps steps in total; the checkpoints take
- * (ceil(max_steps / checkpoint_every) + 16) * dim * pitch floats.  Supported
- * systems: LINEAR, HARMONIC, WILSON_COWAN, LORENZ (FF_ERR_UNSUPPORTED for HH3
- * and while particle reset is on).  ff_reset and ff_set_state end the tape.
+ * (ceil(max_steps / checkpoint_every) + 16) * dim * pitch floats.  Every
+ * system has an adjoint; FF_ERR_UNSUPPORTED while particle reset is on (a
+ * re-draw is not differentiable).  ff_reset and ff_set_state end the tape.
  * Errors: FF_ERR_INVALID_ARG for checkpoint_every outside 1..256 or
  * max_steps < 1; FF_ERR_STATE without particles; FF_ERR_OOM. */
 ff_status ff_tape_begin(ff_system* sys, int64_t checkpoint_every, int64_t max_steps);

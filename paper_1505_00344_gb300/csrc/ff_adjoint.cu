@@ -5,8 +5,9 @@
 // One thread per particle walks the chunks in reverse with the adjoint state
 // lambda = dL/dx in registers.  A chunk of L <= M*M steps is recomputed from its
 // checkpoint twice: once to place sub-checkpoints every M steps (local memory),
-// then per sub-segment (in reverse) to put its <= M states in registers, which
-// the reverse RK4 steps consume from last to first.  Parameter gradients are
+// then per sub-segment (in reverse) to put its <= M states in registers (local
+// memory for the 15-dimensional system), which the reverse RK4 steps consume
+// from last to first.  Parameter gradients are
 // summed per particle in FP32 within a chunk, added to FP64 per chunk, and
 // reduced over particles through per-block FP64 partials in fixed order.
 #include <cstdint>
@@ -75,6 +76,109 @@ template <> struct Vjp<WilsonCowan> {
         jp[7] = fmaf(-(SI - I), __fdividef(uI, tI), jp[7]);
         jp[8] = fmaf(sE * (aE - th), uE, fmaf(sI * (aI - th), uI, jp[8]));
         jp[9] = jp[9] - dE - dI;
+    }
+};
+
+// g(y) = y / (1 - e^-y) and g'(y) = (1 - e^-y (1 + y)) / (1 - e^-y)^2, given e = e^-y.
+// For |y| < 0.5, where the differences cancel in FP32, the Bernoulli series
+// g' = 1/2 + y/6 - y^3/180 + y^5/5040 - y^7/151200 (next term below 1e-9).
+__device__ __forceinline__ void x_over_expm1(float y, float e, float& g, float& dg) {
+    if (fabsf(y) < 0.5f) {
+        const float y2 = y * y;
+        g = bernoulli_series(y);
+        dg = fmaf(y, fmaf(y2, fmaf(y2, fmaf(y2, -1.0f / 151200.0f, 1.0f / 5040.0f), -1.0f / 180.0f), 1.0f / 6.0f),
+                  0.5f);
+    } else {
+        const float r = __fdividef(1.0f, 1.0f - e);
+        g = y * r;
+        dg = fmaf(-e, 1.0f + y, 1.0f) * r * r;
+    }
+}
+
+template <> struct Vjp<HH3> {
+    // Eq. 6-11 differentiated term by term; the gate rates depend on V only.
+    // Per neuron i with u_i = v_V,i / C:
+    //   d/dV_i: -u_i (gL + gNa m^3 h + gK n^4 + gsyn S_i) + sum over gates of
+    //           v_y (a'(1 - y) - b' y) + v_s sig act (1 - act)(1 - s) / tau_r
+    //   d/dm, d/dh, d/dn: the current terms' derivatives times u_i minus v_y (a + b)
+    //   d/ds_i: -v_s (act / tau_r + 1 / tau_d) + sum_{j != i} gsyn (Esyn - V_j) u_j
+    // where S_i is the sum of the other neurons' s.
+    __device__ __forceinline__ static void apply(const float (&x)[15], const float* p, const float (&v)[15],
+                                                 float (&jx)[15], float* jp) {
+        const float C = p[0], gNa = p[1], gK = p[2], gL = p[3];
+        const float ENa = p[4], EK = p[5], EL = p[6], gsyn = p[7], Esyn = p[8];
+        const float inv_tr = __fdividef(1.0f, p[12]), inv_td = __fdividef(1.0f, p[13]);
+        const float sig = p[14], theta = p[15];
+        const float invC = __fdividef(1.0f, C);
+        const float s_sum = x[4] + x[9] + x[14];
+        constexpr float kE25 = 12.182493960703473f;  // e^2.5
+        constexpr float kE1 = 2.718281828459045f;    // e^1
+        constexpr float kE3 = 20.085536923187668f;   // e^3
+        float syn[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float V = x[5 * i], m = x[5 * i + 1], h = x[5 * i + 2], n = x[5 * i + 3], s = x[5 * i + 4];
+            const float uV = v[5 * i] * invC, vm = v[5 * i + 1], vh = v[5 * i + 2], vn = v[5 * i + 3];
+            const float vs = v[5 * i + 4];
+            // rates (same formulation as the forward right-hand side)
+            const float u = V + 65.0f;
+            const float q = exp2f(u * (-kLog2e / 80.0f));
+            const float q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
+            const float bm = 4.0f * exp2f(u * (-kLog2e / 18.0f));
+            const float ah = 0.07f * q4;
+            const float bn = 0.125f * q;
+            const float bh = __fdividef(1.0f, fmaf(kE3, q8, 1.0f));
+            const float act = __fdividef(1.0f, 1.0f + exp2f(sig * kLog2e * (theta - V)));
+            float gm, dgm, gn, dgn;
+            x_over_expm1((V + 40.0f) * 0.1f, kE25 * q8, gm, dgm);
+            x_over_expm1((V + 55.0f) * 0.1f, kE1 * q8, gn, dgn);
+            const float am = gm, dam = 0.1f * dgm;   // alpha_m = 0.1 (V+40) / (1 - e^{-(V+40)/10})
+            const float an = 0.1f * gn, dan = 0.01f * dgn;
+            const float dbm = bm * (-1.0f / 18.0f), dah = ah * (-1.0f / 20.0f), dbn = bn * (-1.0f / 80.0f);
+            const float dbh = 0.1f * bh * (1.0f - bh);
+            const float a1 = act * (1.0f - act);
+            // currents
+            const float m2 = m * m, m3 = m2 * m, m3h = m3 * h;
+            const float n2 = n * n, n3 = n2 * n, n4 = n2 * n2;
+            const float others = s_sum - s;
+            const float dNa = ENa - V, dK = EK - V, dL = EL - V, dS = Esyn - V;
+            float I = gL * dL;
+            I = fmaf(gNa * m3h, dNa, I);
+            I = fmaf(gK * n4, dK, I);
+            I = fmaf(gsyn * others, dS, I);
+            I = I + p[9 + i];
+            const float gtot = fmaf(gsyn, others, fmaf(gK, n4, fmaf(gNa, m3h, gL)));
+            float jv = -uV * gtot;
+            jv = fmaf(vm, fmaf(dam, 1.0f - m, -dbm * m), jv);
+            jv = fmaf(vh, fmaf(dah, 1.0f - h, -dbh * h), jv);
+            jv = fmaf(vn, fmaf(dan, 1.0f - n, -dbn * n), jv);
+            const float sv = vs * inv_tr * (1.0f - s);  // v_s (1 - s) / tau_r
+            jv = fmaf(sig * a1, sv, jv);
+            jx[5 * i] = jv;
+            jx[5 * i + 1] = fmaf(uV * 3.0f * gNa * m2 * h, dNa, -vm * (am + bm));
+            jx[5 * i + 2] = fmaf(uV * gNa * m3, dNa, -vh * (ah + bh));
+            jx[5 * i + 3] = fmaf(uV * 4.0f * gK * n3, dK, -vn * (an + bn));
+            jx[5 * i + 4] = -vs * fmaf(act, inv_tr, inv_td);
+            syn[i] = gsyn * dS * uV;
+            // parameters
+            jp[0] = fmaf(-I * invC, uV, jp[0]);
+            jp[1] = fmaf(m3h * dNa, uV, jp[1]);
+            jp[2] = fmaf(n4 * dK, uV, jp[2]);
+            jp[3] = fmaf(dL, uV, jp[3]);
+            jp[4] = fmaf(gNa * m3h, uV, jp[4]);
+            jp[5] = fmaf(gK * n4, uV, jp[5]);
+            jp[6] = fmaf(gL, uV, jp[6]);
+            jp[7] = fmaf(dS * others, uV, jp[7]);
+            jp[8] = fmaf(gsyn * others, uV, jp[8]);
+            jp[9 + i] += uV;
+            jp[12] = fmaf(-act * inv_tr, sv, jp[12]);
+            jp[13] = fmaf(s * inv_td * inv_td, vs, jp[13]);
+            jp[14] = fmaf(a1 * (V - theta), sv, jp[14]);
+            jp[15] = fmaf(-sig * a1, sv, jp[15]);
+        }
+        const float syn_sum = syn[0] + syn[1] + syn[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) jx[5 * i + 4] += syn_sum - syn[i];
     }
 };
 
@@ -217,17 +321,27 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
                 float st[M][D];
 #pragma unroll
                 for (int k = 0; k < D; ++k) x[k] = cp[sq][k];
-#pragma unroll
-                for (int r = 0; r < M; ++r) {
-                    if (r < nq) {
+                if constexpr (D > 8) {
+                    // large states: the sub-segment stays in local memory (indexed at run time)
+                    for (int r = 0; r < nq; ++r) {
 #pragma unroll
                         for (int k = 0; k < D; ++k) st[r][k] = x[k];
                         if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
                     }
-                }
+                    for (int r = nq - 1; r >= 0; --r) adj_step<R, METHOD>(st[r], lam, h, p, jp);
+                } else {
 #pragma unroll
-                for (int r = M - 1; r >= 0; --r)
-                    if (r < nq) adj_step<R, METHOD>(st[r], lam, h, p, jp);
+                    for (int r = 0; r < M; ++r) {
+                        if (r < nq) {
+#pragma unroll
+                            for (int k = 0; k < D; ++k) st[r][k] = x[k];
+                            if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
+                        }
+                    }
+#pragma unroll
+                    for (int r = M - 1; r >= 0; --r)
+                        if (r < nq) adj_step<R, METHOD>(st[r], lam, h, p, jp);
+                }
             }
 #pragma unroll
             for (int q = 0; q < NP; ++q) gacc[q] += (double)jp[q];
@@ -311,7 +425,7 @@ static cudaError_t launch_r(int method, bool pp, int m, const AdjointArgs& a, in
 
 bool adjoint_supported(int rhs_id) {
     return rhs_id == FF_RHS_LORENZ || rhs_id == FF_RHS_WILSON_COWAN || rhs_id == FF_RHS_HARMONIC ||
-           rhs_id == FF_RHS_LINEAR;
+           rhs_id == FF_RHS_LINEAR || rhs_id == FF_RHS_HH3;
 }
 
 int adjoint_sub_steps(int64_t checkpoint_every) {
@@ -332,6 +446,7 @@ cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const Adjoint
     case FF_RHS_WILSON_COWAN: e = launch_r<WilsonCowan>(method, pp, m, a, block, num_sms, s, &rows); break;
     case FF_RHS_HARMONIC: e = launch_r<Harmonic>(method, pp, m, a, block, num_sms, s, &rows); break;
     case FF_RHS_LINEAR: e = launch_r<Linear>(method, pp, m, a, block, num_sms, s, &rows); break;
+    case FF_RHS_HH3: e = launch_r<HH3>(method, pp, m, a, block, num_sms, s, &rows); break;
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

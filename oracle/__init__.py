@@ -75,6 +75,11 @@ def _load():
                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, P]
         lib.ffo_splat3d.restype = None
         lib.ffo_splat3d.argtypes = [i64, P, P, P, P, P, ctypes.c_int, ctypes.c_int, P]
+        d, f, c_int = ctypes.c_double, ctypes.c_float, ctypes.c_int
+        lib.ffo_sprites2d.restype = None
+        lib.ffo_sprites2d.argtypes = [i64, P, P, P, P, d, d, d, d, c_int, c_int, f, d, P, P, P, P]
+        lib.ffo_sprites3d.restype = None
+        lib.ffo_sprites3d.argtypes = [i64, P, P, P, P, P, P, c_int, c_int, f, d, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -292,3 +297,38 @@ def splat3d(x, y, z, mvp, W, H, include=None, image=None):
     img = np.zeros((H, W), dtype=np.uint32) if image is None else image
     _load().ffo_splat3d(x.size, _ptr(x), _ptr(y), _ptr(z), _ptr(inc), _ptr(m), W, H, _ptr(img))
     return img
+
+
+def _sprite_buffers(W, H, group, colour, P):
+    g = np.zeros(P, np.int32) if group is None else _c(group, np.int32)
+    col = _c(colour, np.float64).reshape(-1, 4)
+    if g.size and (g.min() < 0 or g.max() >= col.shape[0]):
+        raise ValueError("group index without a colour")
+    return g, col, np.zeros((H, W, 4)), np.zeros((H, W, 4)), np.zeros((H, W), np.uint32)
+
+
+def sprites2d(u, v, lo, hi, W, H, radius, gain, colour, group=None, include=None):
+    """Soft sprites of a 2D view: returns (image [H][W][4], sum of |contributions|
+    per channel [H][W][4], fragments per pixel [H][W]), all from FP64 sums."""
+    u = _c(u, np.float32)
+    v = _c(v, np.float32)
+    g, col, img, aimg, frags = _sprite_buffers(W, H, group, colour, u.size)
+    inc = None if include is None else _c(include, np.uint8)
+    _load().ffo_sprites2d(u.size, _ptr(u), _ptr(v), _ptr(g), _ptr(inc), float(lo[0]), float(hi[0]), float(lo[1]),
+                          float(hi[1]), W, H, float(radius), float(gain), _ptr(col), _ptr(img), _ptr(aimg),
+                          _ptr(frags))
+    return img, aimg, frags
+
+
+def sprites3d(x, y, z, mvp, W, H, radius, gain, colour, group=None, include=None):
+    """Soft sprites of a 3D perspective view (constant on-screen size)."""
+    x = _c(x, np.float32)
+    y = _c(y, np.float32)
+    z = _c(z, np.float32)
+    m = _c(mvp, np.float32).reshape(16)
+    g, col, img, aimg, frags = _sprite_buffers(W, H, group, colour, x.size)
+    inc = None if include is None else _c(include, np.uint8)
+    _load().ffo_sprites3d(x.size, _ptr(x), _ptr(y), _ptr(z), _ptr(g), _ptr(inc), _ptr(m), W, H, float(radius),
+                          float(gain), _ptr(col), _ptr(img), _ptr(aimg), _ptr(frags))
+    return img, aimg, frags
+

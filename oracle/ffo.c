@@ -638,6 +638,112 @@ void ffo_splat2d(int64_t P, const float *u, const float *v, const uint8_t *inclu
     }
 }
 
+/* Soft-sprite render technique (Appendix A: the geometry shader emits a square
+ * facing the camera and centred on the projected particle; the fragment shader
+ * gives each pixel of that square an intensity that falls off smoothly with the
+ * pixel's distance from the centre, giving a round particle; the blend
+ * glBlendFunc(GL_SRC_ALPHA, GL_ONE) adds intensity times the particle's colour
+ * to what the pixel already holds).  The paper gives neither the square's size
+ * nor the falloff; the readings taken here:
+ *  - the particle's centre, in continuous pixel units, is (a - lo) * scale on
+ *    each axis: the count splat's coordinate before its floor;
+ *  - pixel (col, row) is sampled at its centre (col + 1/2, row + 1/2); with the
+ *    square's half-side R and q = (dx^2 + dy^2) / R^2 the pixel is covered iff
+ *    q < 1 and gets intensity a = (1 - q)^2, which meets zero with zero slope at
+ *    the rim (the square's corners, q >= 1, get nothing);
+ *  - channel k (0..3) of the pixel gains gain * a * colour[g][k], g the
+ *    particle's group; the image is [H][W][4] with the channels interleaved.
+ * Coverage (q < 1) is decided in FP32 with every operation rounded on its own,
+ * like the pixel rule; the intensities and sums are formed in double.
+ * abs_image (optional) receives the sums of |contribution| per channel and
+ * frags (optional) the number of fragments per pixel: the scale of the rounding
+ * error of any FP32 summation of the same contributions. */
+static void sprite_add(double *image, double *abs_image, uint32_t *frags, int W, int H,
+                       float pc, float pr, float R, float inv_r2, double gain, const double *colour)
+{
+    /* the comparisons also reject non-finite centres */
+    if (!(pc > -R - 1.0f && pc < (float)W + R + 1.0f && pr > -R - 1.0f && pr < (float)H + R + 1.0f))
+        return;
+    int c0 = (int)floorf(pc - R), c1 = (int)ceilf(pc + R);
+    int r0 = (int)floorf(pr - R), r1 = (int)ceilf(pr + R);
+    if (c0 < 0) c0 = 0;
+    if (r0 < 0) r0 = 0;
+    if (c1 > W - 1) c1 = W - 1;
+    if (r1 > H - 1) r1 = H - 1;
+    for (int row = r0; row <= r1; ++row) {
+        for (int col = c0; col <= c1; ++col) {
+            float dx = ((float)col + 0.5f) - pc;
+            float dy = ((float)row + 0.5f) - pr;
+            float dx2 = dx * dx;
+            float dy2 = dy * dy;
+            float d2 = dx2 + dy2;
+            float q = d2 * inv_r2;
+            if (!(q < 1.0f)) continue;
+            double a = (1.0 - (double)q) * (1.0 - (double)q);
+            int64_t at = ((int64_t)row * W + col) * 4;
+            for (int k = 0; k < 4; ++k) {
+                double c = gain * a * colour[k];
+                image[at + k] += c;
+                if (abs_image) abs_image[at + k] += fabs(c);
+            }
+            if (frags) frags[(int64_t)row * W + col] += 1u;
+        }
+    }
+}
+
+/* 2D soft sprites: the window map of ffo_splat2d, then sprite_add.  group[i] is
+ * particle i's group; colour holds 4 channel weights per group; radius R > 0
+ * pixels (1/R^2 is formed in double and rounded to float). */
+void ffo_sprites2d(int64_t P, const float *u, const float *v, const int32_t *group, const uint8_t *include,
+                   double lo_u, double hi_u, double lo_v, double hi_v, int W, int H,
+                   float R, double gain, const double *colour,
+                   double *image, double *abs_image, uint32_t *frags)
+{
+    float lo_uf = (float)lo_u, lo_vf = (float)lo_v;
+    float su = (float)((double)W / (hi_u - lo_u));
+    float sv = (float)((double)H / (hi_v - lo_v));
+    float inv_r2 = (float)(1.0 / ((double)R * (double)R));
+    for (int64_t i = 0; i < P; ++i) {
+        if (include && !include[i]) continue;
+        float du = u[i] - lo_uf;
+        float pc = du * su;
+        float dv = v[i] - lo_vf;
+        float pr = dv * sv;
+        sprite_add(image, abs_image, frags, W, H, pc, pr, R, inv_r2, gain, colour + 4 * group[i]);
+    }
+}
+
+/* 3D soft sprites: the perspective map of ffo_splat3d (particles with clip
+ * w <= 0 dropped), then sprite_add with a square of constant size on screen
+ * (the geometry shader builds it after the projection). */
+void ffo_sprites3d(int64_t P, const float *x, const float *y, const float *z, const int32_t *group,
+                   const uint8_t *include, const float *m, int W, int H,
+                   float R, double gain, const double *colour,
+                   double *image, double *abs_image, uint32_t *frags)
+{
+    float su = (float)((double)W / 2.0), sv = (float)((double)H / 2.0);
+    float inv_r2 = (float)(1.0 / ((double)R * (double)R));
+    for (int64_t i = 0; i < P; ++i) {
+        if (include && !include[i]) continue;
+        float cl[4];
+        for (int j = 0; j < 4; ++j) {
+            float a = m[0 + j] * x[i];
+            float b = m[4 + j] * y[i];
+            float c = m[8 + j] * z[i];
+            float s = a + b;
+            s = s + c;
+            s = s + m[12 + j];
+            cl[j] = s;
+        }
+        if (!(cl[3] > 0.0f)) continue;
+        float nx = cl[0] / cl[3];
+        float ny = cl[1] / cl[3];
+        float pc = (nx - -1.0f) * su;
+        float pr = (ny - -1.0f) * sv;
+        sprite_add(image, abs_image, frags, W, H, pc, pr, R, inv_r2, gain, colour + 4 * group[i]);
+    }
+}
+
 /* 3D render technique (Appendix A, vertex + geometry shaders): clip = M [x,1]
  * with M the column-major 4x4 Model-View-Projection matrix (element (row j,
  * column c) at m[4c + j]), each row summed left to right; particles with

@@ -28,7 +28,8 @@ MUTANTS = {
                         "return 1.0 / (1.0 + exp(-(a - thresh)));"),
     "wc_tau_swapped": ("dx[1] = (-I + wc_sigmoid(aI, gain, th)) / tauI;",
                        "dx[1] = (-I + wc_sigmoid(aI, gain, th)) / tauE;"),
-    "hh_ring_not_all_to_all": ("if (j != i) s_others", "if (j == (i + 2) % 3) s_others"),
+    "hh_ring_not_all_to_all": ("if (j != i) s_others += x[5 * j + 4];\n        double I_L",
+                               "if (j == (i + 2) % 3) s_others += x[5 * j + 4];\n        double I_L"),
     "hh_beta_m_scale": ("return 4.0 * exp(-(V + 65.0) / 18.0);", "return 4.0 * exp(-(V + 65.0) / 20.0);"),
     "hh_n_power": ("double I_K = gK * (n * n * n * n) * (EK - V);", "double I_K = gK * (n * n * n) * (EK - V);"),
     "hh_tau_swap": ("di[4] = act * (1.0 - s) / tau_r - s / tau_d;", "di[4] = act * (1.0 - s) / tau_d - s / tau_r;"),
@@ -45,10 +46,14 @@ MUTANTS = {
                   "double u = (double)(r >> 41) * (1.0 / 8388608.0);"),
     "linspace_denominator": ("(double)i / (double)(P - 1)", "(double)i / (double)(P)"),
     "pixel_round_half": ("float q = d * scale_f;", "float q = d * scale_f + 0.5f;"),
-    "behind_camera_kept": ("if (!(cl[3] > 0.0f)) continue;", "if (!(cl[3] != 0.0f)) continue;"),
-    "mvp_row_major": ("float a = m[0 + j] * x[i];", "float a = m[4 * j] * x[i];"),
-    "rows_top_down": ("image[(int64_t)r * W + (int64_t)c] += 1u;\n    }\n}\n\n/* 3D",
-                      "image[(int64_t)(H - 1 - (int)r) * W + (int64_t)c] += 1u;\n    }\n}\n\n/* 3D"),
+    "behind_camera_kept": ("if (!(cl[3] > 0.0f)) continue;\n        float nx = cl[0] / cl[3];\n        float ny = cl[1] / cl[3];\n        float c =",
+                           "if (!(cl[3] != 0.0f)) continue;\n        float nx = cl[0] / cl[3];\n        float ny = cl[1] / cl[3];\n        float c ="),
+    "mvp_row_major": ("Hf = (float)H;\n    for (int64_t i = 0; i < P; ++i) {\n        if (include && !include[i]) continue;\n        float cl[4];\n        for (int j = 0; j < 4; ++j) {\n            float a = m[0 + j] * x[i];",
+                      "Hf = (float)H;\n    for (int64_t i = 0; i < P; ++i) {\n        if (include && !include[i]) continue;\n        float cl[4];\n        for (int j = 0; j < 4; ++j) {\n            float a = m[4 * j] * x[i];"),
+    "sprite_mvp_row_major": ("inv_r2 = (float)(1.0 / ((double)R * (double)R));\n    for (int64_t i = 0; i < P; ++i) {\n        if (include && !include[i]) continue;\n        float cl[4];\n        for (int j = 0; j < 4; ++j) {\n            float a = m[0 + j] * x[i];",
+                             "inv_r2 = (float)(1.0 / ((double)R * (double)R));\n    for (int64_t i = 0; i < P; ++i) {\n        if (include && !include[i]) continue;\n        float cl[4];\n        for (int j = 0; j < 4; ++j) {\n            float a = m[4 * j] * x[i];"),
+    "rows_top_down": ("image[(int64_t)r * W + (int64_t)c] += 1u;\n    }\n}\n\n/* Soft-sprite",
+                      "image[(int64_t)(H - 1 - (int)r) * W + (int64_t)c] += 1u;\n    }\n}\n\n/* Soft-sprite"),
     "reset_counter_block": ("uint64_t n = ((uint64_t)r * (uint64_t)count[i] + (uint64_t)j[i])",
                             "uint64_t n = ((uint64_t)(r - 1u) * (uint64_t)count[i] + (uint64_t)j[i])"),
     "reset_age_kept": ("            age[i] = 0u;\n            resets[i] = r;", "            resets[i] = r;"),
@@ -72,6 +77,17 @@ MUTANTS = {
                           "Fp[rs * np + 15] = sig * a1 * (1.0 - s) / tau_r;"),
     "jac_hh_vtrap_series": ("return 0.5 + x * (1.0 / 6.0 + x2", "return 0.5 + x * (1.0 / 3.0 + x2"),
     "jac_hh_vtrap_closed": ("return (1.0 - e * (1.0 + x)) / (d * d);", "return (1.0 - e * (1.0 - x)) / (d * d);"),
+    "sprite_falloff_linear": ("double a = (1.0 - (double)q) * (1.0 - (double)q);", "double a = (1.0 - (double)q);"),
+    "sprite_pixel_corner": ("float dx = ((float)col + 0.5f) - pc;", "float dx = (float)col - pc;"),
+    "sprite_radius_not_squared": ("(hi_v - lo_v));\n    float inv_r2 = (float)(1.0 / ((double)R * (double)R));",
+                                  "(hi_v - lo_v));\n    float inv_r2 = (float)(1.0 / (double)R);"),
+    "sprite_rim_inclusive": ("if (!(q < 1.0f)) continue;\n            double a", "if (!(q <= 1.0f)) continue;\n            double a"),
+    "sprite_rows_top_down": ("int64_t at = ((int64_t)row * W + col) * 4;", "int64_t at = ((int64_t)(H - 1 - row) * W + col) * 4;"),
+    "sprite_one_colour": ("colour + 4 * group[i]);\n    }\n}\n\n/* 3D soft", "colour);\n    }\n}\n\n/* 3D soft"),
+    "sprite_channel": ("double c = gain * a * colour[k];", "double c = gain * a * colour[0];"),
+    "sprite_3d_offset": ("float pc = (nx - -1.0f) * su;", "float pc = nx * su;"),
+    "sprite_3d_behind": ("if (!(cl[3] > 0.0f)) continue;\n        float nx = cl[0] / cl[3];\n        float ny = cl[1] / cl[3];\n        float pc",
+                         "if (!(cl[3] != 0.0f)) continue;\n        float nx = cl[0] / cl[3];\n        float ny = cl[1] / cl[3];\n        float pc"),
     "tangent_no_forcing": ("double s = Fp[i * np + q];", "double s = 0.0;"),
     "tangent_stage": ("for (int a = 0; a < n; ++a) ys[a] = y[a] + hh * k3[a];", "for (int a = 0; a < n; ++a) ys[a] = y[a] + hh * k2[a];"),
     "tangent_euler_step": ("for (int a = 0; a < n; ++a) y[a] = y[a] + hh * k1[a];", "for (int a = 0; a < n; ++a) y[a] = y[a] + (hh / 2.0) * k1[a];"),
@@ -83,7 +99,7 @@ MUTANTS = {
 def test_pins_catch_planted_mistake(name, tmp_path):
     old, new = MUTANTS[name]
     src = open(SRC).read()
-    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    assert src.count(old) == 1, f"mutation site for {name} not found or not unique"
     mutated = src.replace(old, new, 1)
     csrc = tmp_path / "ffo_mut.c"
     csrc.write_text(mutated)

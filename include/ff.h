@@ -222,6 +222,36 @@ ff_status ff_project_splat(ff_system* sys, const ff_view* view, uint32_t* image,
 ff_status ff_step_splat(ff_system* sys, int64_t n_steps, double dt, const ff_view* view, uint32_t* image,
                         int image_is_device);
 
+/* Soft sprites (paper Appendix A: the geometry shader emits a screen-facing
+ * square around each projected particle, the fragment shader gives each of its
+ * pixels an intensity falling off smoothly with the distance from the centre,
+ * and glBlendFunc(GL_SRC_ALPHA, GL_ONE) adds intensity x colour to the pixel).
+ * The particle's centre is the view's pixel coordinate before the floor (the
+ * 2D window map, or the 3D map after the perspective divide), so sprites keep
+ * a constant size on the screen.  Pixel (col, row) is sampled at its centre
+ * (col + 1/2, row + 1/2); with q = d^2 / radius^2, computed in float with every
+ * operation rounded on its own, a pixel with q < 1 gains
+ *     gain * (1 - q)^2 * colour[g][k]     in channel k = 0..3
+ * for a particle of group g; q >= 1 (the square's corners) gains nothing.
+ * Colours may have any sign.  Sums are FP32 in an unspecified order. */
+#define FF_SPRITE_MAX_RADIUS 32.0f
+typedef struct ff_sprite {
+    float radius;                    /* half-side of the square, pixels: 0 < radius <= 32 */
+    float gain;                      /* factor on every contribution */
+    float colour[FF_MAX_GROUPS][4];  /* channel weights of each group */
+} ff_sprite;
+
+/* Draw every selected particle of `view` as a soft sprite into the float image
+ * [height][width][4] (channels interleaved).  view->accumulate = 0 clears the
+ * image first; group_mask selects groups as in ff_project_splat.  image is a
+ * device pointer aligned to 16 bytes (image_is_device = 1) or host memory (0;
+ * the call then stages the image on the device and synchronises).
+ * Errors: those of ff_project_splat; FF_ERR_INVALID_ARG for a NULL sprite, a
+ * radius outside (0, 32], non-finite gain or colours, or a device image not
+ * aligned to 16 bytes. */
+ff_status ff_project_sprites(ff_system* sys, const ff_view* view, const ff_sprite* sprite, float* image,
+                             int image_is_device);
+
 /* Copy the state out, SoA [dim][P] with P the number of seeded particles
  * (dst holds dim*P floats; host or device).  A host copy synchronises. */
 ff_status ff_get_state(ff_system* sys, float* dst, int dst_is_device);

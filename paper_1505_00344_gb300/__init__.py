@@ -45,6 +45,26 @@ class ff_view(ctypes.Structure):
                 ("height", ctypes.c_int), ("group_mask", ctypes.c_uint32), ("accumulate", ctypes.c_int)]
 
 
+class ff_sprite(ctypes.Structure):
+    _fields_ = [("radius", ctypes.c_float), ("gain", ctypes.c_float),
+                ("colour", (ctypes.c_float * 4) * FF_MAX_GROUPS)]
+
+
+def make_sprite(radius=1.5, gain=1.0, colours=((1.0, 1.0, 1.0, 1.0),)):
+    """A soft-sprite description: radius in pixels, gain, and up to FF_MAX_GROUPS
+    rows of 4 channel weights (groups beyond the rows given get zeros)."""
+    sp = ff_sprite()
+    sp.radius = float(radius)
+    sp.gain = float(gain)
+    rows = np.asarray(colours, dtype=np.float64).reshape(-1, 4)
+    if rows.shape[0] > FF_MAX_GROUPS:
+        raise ValueError(f"at most {FF_MAX_GROUPS} colour rows")
+    for g, row in enumerate(rows):
+        for k in range(4):
+            sp.colour[g][k] = float(row[k])
+    return sp
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -61,6 +81,7 @@ _SIGS = {
     "ff_set_params": [_P, _P, ctypes.c_int],
     "ff_project_splat": [_P, ctypes.POINTER(ff_view), _P, ctypes.c_int],
     "ff_step_splat": [_P, _I64, ctypes.c_double, ctypes.POINTER(ff_view), _P, ctypes.c_int],
+    "ff_project_sprites": [_P, ctypes.POINTER(ff_view), ctypes.POINTER(ff_sprite), _P, ctypes.c_int],
     "ff_get_state": [_P, _P, ctypes.c_int],
     "ff_set_state": [_P, _P, ctypes.c_int],
     "ff_stats": [_P, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -236,6 +257,16 @@ def ff_step_splat(sys, n_steps, dt, view, image):
         view = make_view(**view)
     ptr, dev, _keep = _buf(image)
     _check(lib().ff_step_splat(sys, int(n_steps), float(dt), ctypes.byref(view), ptr, dev))
+
+
+def ff_project_sprites(sys, view, sprite, image):
+    """Soft sprites into a float32 image [height][width][4] (host array or CUDA tensor)."""
+    if isinstance(view, dict):
+        view = make_view(**view)
+    if isinstance(sprite, dict):
+        sprite = make_sprite(**sprite)
+    ptr, dev, _keep = _buf(image, np.float32)
+    _check(lib().ff_project_sprites(sys, ctypes.byref(view), ctypes.byref(sprite), ptr, dev))
 
 
 def ff_get_state(sys, dst):
@@ -440,6 +471,9 @@ class System:
 
     def step_splat(self, n_steps, dt, view, image):
         ff_step_splat(self.handle, n_steps, dt, view, image)
+
+    def project_sprites(self, view, sprite, image):
+        ff_project_sprites(self.handle, view, sprite, image)
 
     def get_state(self, dst):
         ff_get_state(self.handle, dst)

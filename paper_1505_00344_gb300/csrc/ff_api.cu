@@ -719,6 +719,69 @@ ff_status ff_project_splat(ff_system* s, const ff_view* v, uint32_t* image, int 
     return FF_OK;
 }
 
+ff_status ff_project_sprites(ff_system* s, const ff_view* v, const ff_sprite* sp, float* image,
+                             int image_is_device) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_project_sprites: system is NULL");
+    if (!v || !image || !sp) return fail(FF_ERR_INVALID_ARG, "ff_project_sprites: view, sprite or image is NULL");
+    if (!(sp->radius > 0.0f && sp->radius <= FF_SPRITE_MAX_RADIUS))
+        return fail(FF_ERR_INVALID_ARG, "ff_project_sprites: radius %g outside (0, 32]", (double)sp->radius);
+    if (!std::isfinite(sp->gain)) return fail(FF_ERR_INVALID_ARG, "ff_project_sprites: non-finite gain");
+    if (image_is_device && (reinterpret_cast<uintptr_t>(image) & 15u) != 0)
+        return fail(FF_ERR_INVALID_ARG, "ff_project_sprites: device image not aligned to 16 bytes");
+    ff::SpriteArgs a{};
+    ff_status vst = view_args(s, v, &a.v);
+    if (vst != FF_OK) return vst;
+    for (int g = 0; g < FF_MAX_GROUPS; ++g) {
+        float c[4];
+        for (int k = 0; k < 4; ++k) {
+            if (!std::isfinite(sp->colour[g][k]))
+                return fail(FF_ERR_INVALID_ARG, "ff_project_sprites: non-finite colour of group %d", g);
+            c[k] = sp->gain * sp->colour[g][k];
+        }
+        a.colour[g] = make_float4(c[0], c[1], c[2], c[3]);
+    }
+    for (int q = 0; q < v->ndim_view; ++q)
+        a.ax[q] = (a.v.axes[q] == s->dim) ? s->d_pparam : s->d_state + (int64_t)a.v.axes[q] * s->pitch;
+    a.n = s->n_particles;
+    a.n_groups = s->n_groups;
+    for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
+    a.R = sp->radius;
+    a.inv_r2 = (float)(1.0 / ((double)sp->radius * (double)sp->radius));
+    const uint32_t all = (s->n_groups >= 32) ? 0xffffffffu : ((1u << s->n_groups) - 1u);
+    const bool masked = a.v.mask != all;
+
+    DeviceScope dev(s->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_project_sprites: set device");
+    const size_t bytes = sizeof(float) * 4 * (size_t)v->width * v->height;
+    float* target = image;
+    cudaError_t e = cudaSuccess;
+    if (!image_is_device) {
+        if (s->stage_bytes < bytes) {
+            cudaFree(s->d_stage);
+            s->d_stage = nullptr;
+            s->stage_bytes = 0;
+            e = cudaMalloc(&s->d_stage, bytes);
+            if (e != cudaSuccess) return cuda_fail(e, "ff_project_sprites: staging image");
+            s->stage_bytes = bytes;
+        }
+        target = reinterpret_cast<float*>(s->d_stage);
+        if (v->accumulate) e = cudaMemcpyAsync(target, image, bytes, cudaMemcpyHostToDevice, s->stream);
+    }
+    if (e == cudaSuccess && !v->accumulate) e = cudaMemsetAsync(target, 0, bytes, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_project_sprites: image clear/upload");
+    a.image = reinterpret_cast<float4*>(target);
+    if (s->n_particles > 0 && a.v.mask != 0) {
+        e = ff::launch_sprites(a, v->ndim_view, masked, s->num_sms, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "sprite kernel launch");
+    }
+    if (!image_is_device) {
+        e = cudaMemcpyAsync(image, target, bytes, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "ff_project_sprites: image download");
+    }
+    return FF_OK;
+}
+
 ff_status ff_step_splat(ff_system* s, int64_t n_steps, double dt, const ff_view* v, uint32_t* image,
                         int image_is_device) {
     if (!s) return fail(FF_ERR_INVALID_ARG, "ff_step_splat: system is NULL");

@@ -222,6 +222,78 @@ cudaError_t launch_splat(const SplatArgs& a, int ndim_view, bool masked, bool st
     return cudaGetLastError();
 }
 
+// Soft sprites (paper Appendix A, geometry + fragment shaders with additive
+// blending).  Each thread projects 4 consecutive particles (16-byte plane
+// loads) and walks each sprite's bounding box; every pixel centre inside the
+// disc q = d^2 / R^2 < 1 receives (1 - q)^2 times the group's colour with one
+// fire-and-forget 16-byte vector reduction, so the four channels of a pixel
+// travel together.  Coverage arithmetic rounds every operation on its own, so
+// the set of touched pixels is reproducible bit for bit.
+__device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+template <int NDV, bool MASKED>
+__global__ void __launch_bounds__(kSplatBlock) sprite_kernel(const __grid_constant__ SpriteArgs a) {
+    const int64_t n4 = (a.n + 3) / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const float R = a.R, lo_c = -R - 1.0f, hi_c = a.v.Wf + R + 1.0f, hi_r = a.v.Hf + R + 1.0f;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += stride) {
+        const int64_t i0 = 4 * t;
+        const float4 u4 = __ldcs(reinterpret_cast<const float4*>(a.ax[0] + i0));
+        const float4 v4 = __ldcs(reinterpret_cast<const float4*>(a.ax[1] + i0));
+        float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (NDV == 3) w4 = __ldcs(reinterpret_cast<const float4*>(a.ax[2] + i0));
+        const float u[4] = {u4.x, u4.y, u4.z, u4.w}, v[4] = {v4.x, v4.y, v4.z, v4.w},
+                    w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t i = i0 + j;
+            if (i >= a.n) continue;
+            int g = 0;
+#pragma unroll
+            for (int q = 1; q < FF_MAX_GROUPS; ++q)
+                if (q < a.n_groups && i >= a.gstart[q]) g = q;
+            if (MASKED && !((a.v.mask >> g) & 1u)) continue;
+            float pc, pr;
+            if (!sprite_centre<NDV>(a.v, u[j], v[j], w[j], pc, pr)) continue;
+            // off-window (and non-finite) centres are rejected before any integer conversion
+            if (!(pc > lo_c && pc < hi_c && pr > lo_c && pr < hi_r)) continue;
+            const int c0 = max(0, (int)floorf(pc - R)), c1 = min(a.v.W - 1, (int)ceilf(pc + R));
+            const int r0 = max(0, (int)floorf(pr - R)), r1 = min(a.v.H - 1, (int)ceilf(pr + R));
+            const float4 col = a.colour[g];
+            for (int row = r0; row <= r1; ++row) {
+                const float dy = __fsub_rn(__fadd_rn((float)row, 0.5f), pr);
+                const float dy2 = __fmul_rn(dy, dy);
+                float4* line = a.image + (int64_t)row * a.v.W;
+                for (int c = c0; c <= c1; ++c) {
+                    const float dx = __fsub_rn(__fadd_rn((float)c, 0.5f), pc);
+                    const float q = __fmul_rn(__fadd_rn(__fmul_rn(dx, dx), dy2), a.inv_r2);
+                    if (q < 1.0f) {
+                        const float om = 1.0f - q;
+                        const float wgt = om * om;
+                        red_add_v4(line + c, wgt * col.x, wgt * col.y, wgt * col.z, wgt * col.w);
+                    }
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_sprites(const SpriteArgs& a, int ndim_view, bool masked, int num_sms, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const int grid = grid_for((a.n + 3) / 4, kSplatBlock, num_sms, 8);
+    if (ndim_view == 2) {
+        if (masked) sprite_kernel<2, true><<<grid, kSplatBlock, 0, s>>>(a);
+        else sprite_kernel<2, false><<<grid, kSplatBlock, 0, s>>>(a);
+    } else {
+        if (masked) sprite_kernel<3, true><<<grid, kSplatBlock, 0, s>>>(a);
+        else sprite_kernel<3, false><<<grid, kSplatBlock, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_escape_count(const float* x, int64_t pitch, int dim, int64_t n,
                                 unsigned long long* counter, int num_sms, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);

@@ -34,7 +34,21 @@ struct SplatArgs {
     int64_t gstart[FF_MAX_GROUPS];
 };
 
+// Soft sprites: a square of half-side R pixels around each projected particle;
+// pixel centres with q = d^2 / R^2 < 1 gain (1 - q)^2 times the group's colour.
+struct SpriteArgs {
+    ViewArgs v;            // projection (v.image unused)
+    float4* image;         // [H][W] float4, channels interleaved, 16-byte aligned
+    const float* ax[3];    // planes of the view axes (16-byte aligned; readable up to n rounded to 4)
+    int64_t n;
+    int n_groups;
+    float R, inv_r2;       // radius and 1 / R^2 (formed in double, rounded)
+    int64_t gstart[FF_MAX_GROUPS];
+    float4 colour[FF_MAX_GROUPS];  // gain * colour per group
+};
+
 cudaError_t launch_seed(const SeedArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_sprites(const SpriteArgs& a, int ndim_view, bool masked, int num_sms, cudaStream_t s);
 cudaError_t launch_linspace(float* out, int64_t P, double lo, double hi, int num_sms,
                             cudaStream_t s);
 // strip: consecutive particles map to a narrow strip of the image (a linspace

@@ -51,4 +51,27 @@ __device__ __forceinline__ bool pixel_of(const ViewArgs& a, float u, float v, fl
     return true;
 }
 
+// Continuous pixel coordinates of a projected particle (the pixel rule before
+// its floor): the centre of its soft sprite.  False if it is behind the camera.
+template <int NDV>
+__device__ __forceinline__ bool sprite_centre(const ViewArgs& a, float u, float v, float w, float& pc, float& pr) {
+    if constexpr (NDV == 2) {
+        pc = __fmul_rn(__fsub_rn(u, a.lo0), a.s0);
+        pr = __fmul_rn(__fsub_rn(v, a.lo1), a.s1);
+        return true;
+    } else {
+        float cl[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float t = __fadd_rn(__fmul_rn(a.m[j], u), __fmul_rn(a.m[4 + j], v));
+            t = __fadd_rn(t, __fmul_rn(a.m[8 + j], w));
+            cl[j] = __fadd_rn(t, a.m[12 + j]);
+        }
+        if (!(cl[3] > 0.0f)) return false;
+        pc = __fmul_rn(__fsub_rn(__fdiv_rn(cl[0], cl[3]), -1.0f), a.s0);
+        pr = __fmul_rn(__fsub_rn(__fdiv_rn(cl[1], cl[3]), -1.0f), a.s1);
+        return true;
+    }
+}
+
 }  // namespace ff

@@ -59,6 +59,18 @@ def test_view_struct_layout_matches_c(tmp_path):
     assert c_vals == py_vals
 
 
+def test_sprite_struct_layout_matches_c(tmp_path):
+    src = tmp_path / "sprite.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "ff.h"\nint main(void){\n'
+                   'printf("%zu %zu %zu %zu\\n", sizeof(ff_sprite), offsetof(ff_sprite, radius),'
+                   ' offsetof(ff_sprite, gain), offsetof(ff_sprite, colour));return 0;}\n')
+    exe = tmp_path / "sprite"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    c_vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    S = ff.ff_sprite
+    assert c_vals == [ctypes.sizeof(S), S.radius.offset, S.gain.offset, S.colour.offset]
+
+
 def _status(fn, *args):
     return fn(*args)
 
@@ -102,6 +114,8 @@ def test_host_side_argument_errors(lib):
     assert lib.ff_batch_autotune(None, None, 8) == ff.FF_ERR_INVALID_ARG
     assert lib.ff_batch_describe(None, None, 0) == ff.FF_ERR_INVALID_ARG
     assert lib.ff_batch_destroy(None) == ff.FF_OK
+    sp = ff.make_sprite(2.0)
+    assert lib.ff_project_sprites(None, None, ctypes.byref(sp), None, 1) == ff.FF_ERR_INVALID_ARG
 
 
 def test_binding_raises_with_message(lib):

@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--batch", default="", help="time a batched workload (hh3_batch64, mixed_batch256)")
     ap.add_argument("--batch-steps", type=int, default=1000)
     ap.add_argument("--checkpoint-every", type=int, default=100)
+    ap.add_argument("--sprites", type=float, default=0.0,
+                    help="render soft sprites of this radius (pixels) instead of counts, and time them")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -550,6 +552,80 @@ def run_batch(args, rank, world, local):
             "gpu_launches": len({(w["rhs"], w["method"]) for w in ws})}  # one kernel per family in the graph
 
 
+def run_sprites(args, rank, world, local):
+    """The workload's frame loop with soft sprites (radius --sprites) instead of the count
+    splat: frames/s of ff_step + ff_project_sprites, and the sprite kernel's own rate."""
+    import math
+
+    import torch
+    import paper_1505_00344_gb300 as ff
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload_for(args, rank, world)
+    stream = torch.cuda.current_stream().cuda_stream
+    s = ff.System.from_workload(w, stream=stream)
+    v = w["view"]
+    Wd, Hd = v["width"], v["height"]
+    view = ff.make_view(**v)
+    groups = len(w["groups"])
+    palette = [[1.0, 0.55, 0.15, 1.0], [0.2, 0.45, 1.0, 1.0], [0.3, 1.0, 0.4, 1.0], [1.0, 0.3, 0.8, 1.0]]
+    sprite = ff.make_sprite(args.sprites, 0.05, [palette[g % 4] for g in range(groups)])
+    img = torch.zeros((Hd, Wd, 4), dtype=torch.float32, device=dev)
+    counts = torch.zeros((Hd, Wd), dtype=torch.int32, device=dev)
+    frames = args.frames or w["frames"]
+    n, dt = w["steps_per_frame"], w["dt"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    events = []
+
+    def job(record):
+        s.reset()
+        for _ in range(frames):
+            s.step(n, dt)
+            if record:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                s.project_sprites(view, sprite, img)
+                b.record()
+                events.append((a, b))
+            else:
+                s.project_sprites(view, sprite, img)
+
+    for _ in range(args.warmup):
+        job(False)
+    ts = []
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        job(True)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    sprite_ms = statistics.median([x.elapsed_time(y) for x, y in events])
+    # fragments of the last frame: drawn particles (the count splat) x the lattice points of a disc
+    s.project_splat(view, counts)
+    drawn = int(counts.sum().item())
+    frags = drawn * math.pi * args.sprites ** 2
+    med = statistics.median(ts)
+    P = total_particles(w)
+    return {"metric": "frames/sec (RK4 frames with soft-sprite rendering)", "value": frames / (med / 1e3),
+            "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": med,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "particles": P, "frames": frames, "steps_per_frame": n,
+                       "sprite_radius": args.sprites, "image": [Hd, Wd, 4], "l2": "256 MB flush between steps"},
+            "particle_steps_per_s": P * n * frames / (med / 1e3),
+            "sprite_kernel": {"ms_per_frame": sprite_ms, "drawn_particles": drawn,
+                              "fragments_per_frame_est": frags,
+                              "fragments_per_s": frags / (sprite_ms / 1e3),
+                              "reduction_GBps": 16.0 * frags / (sprite_ms / 1e3) / 1e9,
+                              "share_of_frame": sprite_ms * frames / med},
+            "gpu_launches": 2 * frames}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -559,6 +635,8 @@ def main():
         out = run_adjoint(args, rank, world, local)
     elif args.batch:
         out = run_batch(args, rank, world, local)
+    elif args.sprites > 0:
+        out = run_sprites(args, rank, world, local)
     else:
         out = run_ours(args, rank, world, local)
     if rank == 0 and out is not None:

@@ -316,9 +316,10 @@ ff_status ff_backward(ff_system* sys, const float* dL_dxT_dev, float* dL_dx0_dev
  * round-robin; the families are parallel branches of one CUDA graph, captured
  * once per step count and replayed by every ff_batch_step with that count.
  * The systems keep owning their state; the batch borrows them until
- * ff_batch_destroy, and they must not be destroyed, re-seeded, taped or given
- * a particle reset, and must keep or lack their per-particle parameter
- * meanwhile (ff_batch_step then returns FF_ERR_STATE).
+ * ff_batch_destroy, and they must not be destroyed, re-seeded, taped (other
+ * than by ff_batch_tape_begin) or given a particle reset, and must keep or
+ * lack their per-particle parameter meanwhile (ff_batch_step then returns
+ * FF_ERR_STATE).
  * Members run the scalar integrator (no packed Lorenz kernel, no fused splat).
  *
  * ff_batch_create: systems on one device, each with particles, no Kahan flag,
@@ -334,12 +335,33 @@ ff_status ff_backward(ff_system* sys, const float* dL_dxT_dev, float* dL_dx0_dev
  *   own data for trial_steps steps (twice), keeps the fastest, and restores the
  *   members' states exactly.  Synchronises.
  * ff_batch_describe: one line per family: members, launch shape, tiles, tuned
- *   rate (NUL-terminated, truncated to text_len). */
+ *   rate (NUL-terminated, truncated to text_len).
+ *
+ * Batched gradients.  ff_batch_tape_begin starts every member's tape
+ * (ff_tape_begin with the same arguments; on failure none is left started).
+ * While taped, ff_batch_step runs in segments that end wherever a member's
+ * chunk ends (every checkpoint_every steps, or where its parameters or dt
+ * changed); the first launch of a chunk stores the member's checkpoint from the
+ * state it loads.  ff_batch_backward then runs one reverse-sweep launch per
+ * family over tiles of 128 particles of one member, with the arithmetic of
+ * ff_backward (dL/dx0 bit-identical to it), and reduces each member's
+ * parameter gradient over its tiles in a fixed order:
+ *   dL_dxT_dev[i], dL_dx0_dev[i]: device SoA [dim_i][P_i] buffers of member i
+ *     (host arrays of n_systems pointers; a member's two may alias);
+ *   dL_dp_host: n_systems * FF_MAX_PARAMS doubles, member i's gradient at
+ *     [i * FF_MAX_PARAMS + q] for q < its n_params (zeros after).
+ *   Synchronises.  Errors: FF_ERR_STATE without a batch tape, FF_ERR_INVALID_ARG
+ *   for NULL arrays or buffers.
+ * ff_batch_tape_end ends every member's tape. */
 typedef struct ff_batch ff_batch;
 ff_status ff_batch_create(ff_system* const* systems, int n_systems, void* cuda_stream, ff_batch** out);
 ff_status ff_batch_step(ff_batch* batch, int64_t n_steps, const double* dt);
 ff_status ff_batch_autotune(ff_batch* batch, const double* dt, int64_t trial_steps);
 ff_status ff_batch_describe(ff_batch* batch, char* text, int text_len);
+ff_status ff_batch_tape_begin(ff_batch* batch, int64_t checkpoint_every, int64_t max_steps);
+ff_status ff_batch_tape_end(ff_batch* batch);
+ff_status ff_batch_backward(ff_batch* batch, const float* const* dL_dxT_dev, float* const* dL_dx0_dev,
+                            double* dL_dp_host);
 ff_status ff_batch_destroy(ff_batch* batch);
 
 /* Most groups ff_count_escaped_noalloc accepts (its fixed scratch holds one

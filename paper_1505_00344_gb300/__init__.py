@@ -97,6 +97,9 @@ _SIGS = {
     "ff_batch_autotune": [_P, _P, _I64],
     "ff_batch_describe": [_P, ctypes.c_char_p, ctypes.c_int],
     "ff_batch_destroy": [_P],
+    "ff_batch_tape_begin": [_P, _I64, _I64],
+    "ff_batch_tape_end": [_P],
+    "ff_batch_backward": [_P, _P, _P, _P],
     "ff_tape_end": [_P],
     "ff_get_reset_state": [_P, _P, _P, ctypes.c_int],
 }
@@ -372,6 +375,30 @@ def ff_batch_destroy(batch):
     _check(lib().ff_batch_destroy(batch))
 
 
+def ff_batch_tape_begin(batch, checkpoint_every, max_steps):
+    _check(lib().ff_batch_tape_begin(batch, int(checkpoint_every), int(max_steps)))
+
+
+def ff_batch_tape_end(batch):
+    _check(lib().ff_batch_tape_end(batch))
+
+
+def ff_batch_backward(batch, dL_dxT, dL_dx0):
+    """dL_dxT, dL_dx0: one CUDA tensor (or device pointer) per member, SoA [dim][P].
+    Returns the parameter gradients, an array [n_systems][FF_MAX_PARAMS] (float64)."""
+    if len(dL_dxT) != len(dL_dx0):
+        raise ValueError("one input and one output buffer per member")
+    n = len(dL_dxT)
+    ins = (ctypes.c_void_p * n)(*[_buf(t)[0] for t in dL_dxT])
+    outs = (ctypes.c_void_p * n)(*[_buf(t)[0] for t in dL_dx0])
+    for t in list(dL_dxT) + list(dL_dx0):
+        if _buf(t)[1] != 1:
+            raise ValueError("gradient buffers must be device memory")
+    dp = np.zeros((n, FF_MAX_PARAMS), np.float64)
+    _check(lib().ff_batch_backward(batch, ins, outs, dp.ctypes.data))
+    return dp
+
+
 class Batch:
     """Owning handle over one ff_batch (the systems stay owned by their System objects)."""
 
@@ -387,6 +414,15 @@ class Batch:
 
     def describe(self):
         return ff_batch_describe(self.handle)
+
+    def tape_begin(self, checkpoint_every, max_steps):
+        ff_batch_tape_begin(self.handle, checkpoint_every, max_steps)
+
+    def tape_end(self):
+        ff_batch_tape_end(self.handle)
+
+    def backward(self, dL_dxT, dL_dx0):
+        return ff_batch_backward(self.handle, dL_dxT, dL_dx0)
 
     def close(self):
         if getattr(self, "handle", None):

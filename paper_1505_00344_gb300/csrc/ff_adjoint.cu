@@ -21,7 +21,9 @@ namespace ff {
 
 // ---------------------------------------------------------------------------
 // Vector-Jacobian products: jx = J(x)^T v and jp += F_p(x)^T v, differentiated
-// by hand from the right-hand sides in ff_device.cuh.
+// by hand from the right-hand sides in ff_device.cuh.  No product is left for the
+// compiler to fuse into a following addition (fmaf or _rn forms throughout), so
+// every kernel that inlines them rounds the same way.
 // ---------------------------------------------------------------------------
 template <class R> struct Vjp;
 
@@ -64,18 +66,18 @@ template <> struct Vjp<WilsonCowan> {
         const float sE = SE * (1.0f - SE), sI = SI * (1.0f - SI);  // S'/gain
         const float uE = __fdividef(v[0], tE), uI = __fdividef(v[1], tI);  // v_k / tau_k
         const float dE = g * sE * uE, dI = g * sI * uI;                   // S'(a) v / tau
-        jx[0] = fmaf(dE, wEE, -uE) + dI * wIE;
-        jx[1] = -dE * wEI - fmaf(dI, wII, uI);
+        jx[0] = fmaf(dI, wIE, fmaf(dE, wEE, -uE));
+        jx[1] = fmaf(-dE, wEI, -fmaf(dI, wII, uI));
         jp[0] = fmaf(dE, E, jp[0]);
         jp[1] = fmaf(-dE, I, jp[1]);
         jp[2] = fmaf(dI, E, jp[2]);
         jp[3] = fmaf(-dI, I, jp[3]);
-        jp[4] += dE;
-        jp[5] += dI;
+        jp[4] = __fadd_rn(jp[4], dE);
+        jp[5] = __fadd_rn(jp[5], dI);
         jp[6] = fmaf(-(SE - E), __fdividef(uE, tE), jp[6]);   // d f_E / d tauE = -f_E / tauE
         jp[7] = fmaf(-(SI - I), __fdividef(uI, tI), jp[7]);
         jp[8] = fmaf(sE * (aE - th), uE, fmaf(sI * (aI - th), uI, jp[8]));
-        jp[9] = jp[9] - dE - dI;
+        jp[9] = __fsub_rn(__fsub_rn(jp[9], dE), dI);
     }
 };
 
@@ -89,7 +91,7 @@ __device__ __forceinline__ void x_over_expm1(float y, float e, float& g, float& 
         dg = fmaf(y, fmaf(y2, fmaf(y2, fmaf(y2, -1.0f / 151200.0f, 1.0f / 5040.0f), -1.0f / 180.0f), 1.0f / 6.0f),
                   0.5f);
     } else {
-        const float r = __fdividef(1.0f, 1.0f - e);
+        const float r = __fdividef(1.0f, __fsub_rn(1.0f, e));
         g = y * r;
         dg = fmaf(-e, 1.0f + y, 1.0f) * r * r;
     }
@@ -114,7 +116,7 @@ template <> struct Vjp<HH3> {
         constexpr float kE25 = 12.182493960703473f;  // e^2.5
         constexpr float kE1 = 2.718281828459045f;    // e^1
         constexpr float kE3 = 20.085536923187668f;   // e^3
-        float syn[3];
+        float syn[3], self_s[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const float V = x[5 * i], m = x[5 * i + 1], h = x[5 * i + 2], n = x[5 * i + 3], s = x[5 * i + 4];
@@ -158,7 +160,7 @@ template <> struct Vjp<HH3> {
             jx[5 * i + 1] = fmaf(uV * 3.0f * gNa * m2 * h, dNa, -vm * (am + bm));
             jx[5 * i + 2] = fmaf(uV * gNa * m3, dNa, -vh * (ah + bh));
             jx[5 * i + 3] = fmaf(uV * 4.0f * gK * n3, dK, -vn * (an + bn));
-            jx[5 * i + 4] = -vs * fmaf(act, inv_tr, inv_td);
+            self_s[i] = -vs * fmaf(act, inv_tr, inv_td);
             syn[i] = gsyn * dS * uV;
             // parameters
             jp[0] = fmaf(-I * invC, uV, jp[0]);
@@ -170,7 +172,7 @@ template <> struct Vjp<HH3> {
             jp[6] = fmaf(gL, uV, jp[6]);
             jp[7] = fmaf(dS * others, uV, jp[7]);
             jp[8] = fmaf(gsyn * others, uV, jp[8]);
-            jp[9 + i] += uV;
+            jp[9 + i] = __fadd_rn(jp[9 + i], uV);
             jp[12] = fmaf(-act * inv_tr, sv, jp[12]);
             jp[13] = fmaf(s * inv_td * inv_td, vs, jp[13]);
             jp[14] = fmaf(a1 * (V - theta), sv, jp[14]);
@@ -178,7 +180,7 @@ template <> struct Vjp<HH3> {
         }
         const float syn_sum = syn[0] + syn[1] + syn[2];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) jx[5 * i + 4] += syn_sum - syn[i];
+        for (int i = 0; i < 3; ++i) jx[5 * i + 4] = __fadd_rn(self_s[i], syn_sum - syn[i]);
     }
 };
 
@@ -245,7 +247,7 @@ __device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[
         for (int i = 0; i < D; ++i) l[i] = h * lam[i];
         Vjp<R>::apply(x, p, l, m, jp);
 #pragma unroll
-        for (int i = 0; i < D; ++i) lam[i] += m[i];
+        for (int i = 0; i < D; ++i) lam[i] = __fadd_rn(lam[i], m[i]);
         return;
     }
     const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
@@ -267,111 +269,189 @@ __device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[
     for (int i = 0; i < D; ++i) { sum[i] = m[i]; l[i] = fmaf(h3, lam[i], h * m[i]); }
     Vjp<R>::apply(x3, p, l, m, jp);
 #pragma unroll
-    for (int i = 0; i < D; ++i) { sum[i] += m[i]; l[i] = fmaf(h3, lam[i], h2 * m[i]); }
+    for (int i = 0; i < D; ++i) { sum[i] = __fadd_rn(sum[i], m[i]); l[i] = fmaf(h3, lam[i], h2 * m[i]); }
     Vjp<R>::apply(x2, p, l, m, jp);
 #pragma unroll
-    for (int i = 0; i < D; ++i) { sum[i] += m[i]; l[i] = fmaf(h6, lam[i], h2 * m[i]); }
+    for (int i = 0; i < D; ++i) { sum[i] = __fadd_rn(sum[i], m[i]); l[i] = fmaf(h6, lam[i], h2 * m[i]); }
     Vjp<R>::apply(x, p, l, m, jp);
 #pragma unroll
-    for (int i = 0; i < D; ++i) lam[i] = lam[i] + (sum[i] + m[i]);
+    for (int i = 0; i < D; ++i) lam[i] = __fadd_rn(lam[i], __fadd_rn(sum[i], m[i]));
+}
+
+// Reverse sweep of one particle i over all chunks: lambda from lam_in to
+// lam_out, parameter contributions added to gacc (FP64, per chunk).
+template <class R, int METHOD, bool PP, int M>
+__device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i, double (&gacc)[R::NP]) {
+    constexpr int D = R::DIM, NP = R::NP;
+    int g = 0;
+#pragma unroll
+    for (int q = 1; q < FF_MAX_GROUPS; ++q)
+        if (q < a.n_groups && i >= a.gstart[q]) g = q;
+    float lam[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) lam[k] = (k < a.dim) ? a.lam_in[k * a.n + i] : 0.0f;
+    const float pv = PP ? a.pparam[i] : 0.0f;
+    for (int c = a.n_chunks - 1; c >= 0; --c) {
+        const AdjChunk& ch = a.chunks[c];
+        float p[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) p[q] = (PP && q == a.pidx) ? pv : ch.p[q];
+        const float h = ch.gh[g];
+        const int L = ch.n_steps;
+        const float* ck = a.ckpt + (int64_t)ch.ckpt * a.dim * a.pitch;
+        float x[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[k] = (k < a.dim) ? ck[k * a.pitch + i] : 0.0f;
+        // sub-checkpoints every M steps
+        float cp[M][D];
+        int nsub = 0;
+        for (int base = 0; base < L; base += M, ++nsub) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) cp[nsub][k] = x[k];
+            const int nq = min(M, L - base);
+            for (int r = 0; r < nq; ++r) fwd_step<R, METHOD>(x, h, p);
+        }
+        float jp[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) jp[q] = 0.0f;
+        for (int sq = nsub - 1; sq >= 0; --sq) {
+            const int nq = min(M, L - sq * M);
+            float st[M][D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) x[k] = cp[sq][k];
+            if constexpr (D > 8) {
+                // large states: the sub-segment stays in local memory (indexed at run time)
+                for (int r = 0; r < nq; ++r) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) st[r][k] = x[k];
+                    if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
+                }
+                for (int r = nq - 1; r >= 0; --r) adj_step<R, METHOD>(st[r], lam, h, p, jp);
+            } else {
+#pragma unroll
+                for (int r = 0; r < M; ++r) {
+                    if (r < nq) {
+#pragma unroll
+                        for (int k = 0; k < D; ++k) st[r][k] = x[k];
+                        if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
+                    }
+                }
+#pragma unroll
+                for (int r = M - 1; r >= 0; --r)
+                    if (r < nq) adj_step<R, METHOD>(st[r], lam, h, p, jp);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) gacc[q] += (double)jp[q];
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+        if (k < a.dim) a.lam_out[k * a.n + i] = lam[k];
+}
+
+// Sum of gacc over the block into `row` (np_stride doubles), in a fixed order:
+// warps by shuffles, then warp results in warp order.  Every thread of the
+// block must call it.
+template <int NP, int NW>
+__device__ __forceinline__ void block_sum_to_row(double (&gacc)[NP], double (&red)[NW][NP], double* row) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        double v = gacc[q];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NP; q += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < nwarps; ++w) v += red[w][q];
+        row[q] = v;
+    }
+    __syncthreads();
 }
 
 template <class R, int METHOD, bool PP, int M>
 __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ AdjointArgs a) {
-    constexpr int D = R::DIM, NP = R::NP;
+    constexpr int NP = R::NP;
     __shared__ double red[8][NP > 16 ? 1 : NP];  // per-warp partials (blocks of at most 256 threads)
     double gacc[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) gacc[q] = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        int g = 0;
-#pragma unroll
-        for (int q = 1; q < FF_MAX_GROUPS; ++q)
-            if (q < a.n_groups && i >= a.gstart[q]) g = q;
-        float lam[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) lam[k] = (k < a.dim) ? a.lam_in[k * a.n + i] : 0.0f;
-        const float pv = PP ? a.pparam[i] : 0.0f;
-        for (int c = a.n_chunks - 1; c >= 0; --c) {
-            const AdjChunk& ch = a.chunks[c];
-            float p[NP];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) p[q] = (PP && q == a.pidx) ? pv : ch.p[q];
-            const float h = ch.gh[g];
-            const int L = ch.n_steps;
-            const float* ck = a.ckpt + (int64_t)ch.ckpt * a.dim * a.pitch;
-            float x[D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) x[k] = (k < a.dim) ? ck[k * a.pitch + i] : 0.0f;
-            // sub-checkpoints every M steps
-            float cp[M][D];
-            int nsub = 0;
-            for (int base = 0; base < L; base += M, ++nsub) {
-#pragma unroll
-                for (int k = 0; k < D; ++k) cp[nsub][k] = x[k];
-                const int nq = min(M, L - base);
-                for (int r = 0; r < nq; ++r) fwd_step<R, METHOD>(x, h, p);
-            }
-            float jp[NP];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) jp[q] = 0.0f;
-            for (int sq = nsub - 1; sq >= 0; --sq) {
-                const int nq = min(M, L - sq * M);
-                float st[M][D];
-#pragma unroll
-                for (int k = 0; k < D; ++k) x[k] = cp[sq][k];
-                if constexpr (D > 8) {
-                    // large states: the sub-segment stays in local memory (indexed at run time)
-                    for (int r = 0; r < nq; ++r) {
-#pragma unroll
-                        for (int k = 0; k < D; ++k) st[r][k] = x[k];
-                        if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
-                    }
-                    for (int r = nq - 1; r >= 0; --r) adj_step<R, METHOD>(st[r], lam, h, p, jp);
-                } else {
-#pragma unroll
-                    for (int r = 0; r < M; ++r) {
-                        if (r < nq) {
-#pragma unroll
-                            for (int k = 0; k < D; ++k) st[r][k] = x[k];
-                            if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
-                        }
-                    }
-#pragma unroll
-                    for (int r = M - 1; r >= 0; --r)
-                        if (r < nq) adj_step<R, METHOD>(st[r], lam, h, p, jp);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < NP; ++q) gacc[q] += (double)jp[q];
-        }
-#pragma unroll
-        for (int k = 0; k < D; ++k)
-            if (k < a.dim) a.lam_out[k * a.n + i] = lam[k];
-    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+        adjoint_particle<R, METHOD, PP, M>(a, i, gacc);
     // per-block partial sums of the parameter gradient, in a fixed order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     if constexpr (NP <= 16) {
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            double v = gacc[q];
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if (lane == 0) red[warp][q] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < NP) {
-            double v = 0.0;
-            for (int w = 0; w < nwarps; ++w) v += red[w][threadIdx.x];
-            a.partial[(int64_t)blockIdx.x * a.np_stride + threadIdx.x] = v;
-        }
+        block_sum_to_row<NP, 8>(gacc, red, a.partial + (int64_t)blockIdx.x * a.np_stride);
     } else {
-        // many parameters (the linear test system): one partial per thread, summed by the host-side pass
+        // many parameters (the linear test system): one partial per warp, summed by the host-side pass
         for (int q = 0; q < NP; ++q) {
             double v = gacc[q];
             for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
             if (lane == 0) a.partial[((int64_t)blockIdx.x * nwarps + warp) * a.np_stride + q] = v;
         }
+    }
+}
+
+// Batched adjoint: each block takes tiles round-robin; a tile is a run of
+// particles of one member, one per thread, and its parameter gradient is
+// reduced over the block into the tile's own row.
+template <class R, int METHOD, bool PP, int M>
+__global__ void __launch_bounds__(kAdjTile) batch_adjoint_kernel(const __grid_constant__ BatchAdjointArgs b) {
+    constexpr int NP = R::NP;
+    __shared__ double red[kAdjTile / 32][NP];
+    for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
+        const AdjTile T = b.tiles[tile];
+        const AdjointArgs& a = b.sys[T.sys];
+        double gacc[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) gacc[q] = 0.0;
+        const int64_t i = T.first + threadIdx.x;
+        if (i < T.first + T.count) adjoint_particle<R, METHOD, PP, M>(a, i, gacc);
+        block_sum_to_row<NP, kAdjTile / 32>(gacc, red, b.partial + (int64_t)tile * b.np_stride);
+    }
+}
+
+// dp[m * np_stride + q] = sum over rows [row0[m], row0[m + 1]) of partial[row][q], in row order.
+__global__ void reduce_member_rows_kernel(const double* partial, const int* row0, int n_members, int np,
+                                          int np_stride, double* dp) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_members * np) return;
+    const int m = idx / np, q = idx % np;
+    double s = 0.0;
+    for (int r = row0[m]; r < row0[m + 1]; ++r) s += partial[(int64_t)r * np_stride + q];
+    dp[(int64_t)m * np_stride + q] = s;
+}
+
+template <class R, int METHOD, bool PP, int M>
+static cudaError_t launch_batch_one(const BatchAdjointArgs& b, int num_sms, cudaStream_t s) {
+    auto kernel = batch_adjoint_kernel<R, METHOD, PP, M>;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kAdjTile, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int64_t cap = (int64_t)occ * num_sms;
+    const int grid = (int)((int64_t)b.n_tiles < cap ? b.n_tiles : cap);
+    if (grid < 1) return cudaSuccess;
+    kernel<<<grid, kAdjTile, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <class R, int M>
+static cudaError_t launch_batch_m(int method, bool pp, const BatchAdjointArgs& b, int num_sms, cudaStream_t s) {
+    if (method == FF_RK4)
+        return pp ? launch_batch_one<R, FF_RK4, true, M>(b, num_sms, s) : launch_batch_one<R, FF_RK4, false, M>(b, num_sms, s);
+    return pp ? launch_batch_one<R, FF_EULER, true, M>(b, num_sms, s) : launch_batch_one<R, FF_EULER, false, M>(b, num_sms, s);
+}
+
+template <class R>
+static cudaError_t launch_batch_r(int method, bool pp, int m, const BatchAdjointArgs& b, int num_sms, cudaStream_t s) {
+    switch (m) {
+    case 4: return launch_batch_m<R, 4>(method, pp, b, num_sms, s);
+    case 8: return launch_batch_m<R, 8>(method, pp, b, num_sms, s);
+    case 16: return launch_batch_m<R, 16>(method, pp, b, num_sms, s);
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -452,6 +532,26 @@ cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const Adjoint
     if (e != cudaSuccess) return e;
     reduce_partials_kernel<<<(n_params_kernel + 63) / 64, 64, 0, s>>>(a.partial, rows, n_params_kernel, a.np_stride,
                                                                        dL_dp_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_adjoint(int rhs_id, int method, bool pp, int m, const BatchAdjointArgs& b,
+                                 const int* row0_dev, int n_members, int n_params_kernel, int num_sms,
+                                 cudaStream_t s, double* dp_dev) {
+    cudaError_t e;
+    switch (rhs_id) {
+    case FF_RHS_LORENZ: e = launch_batch_r<Lorenz>(method, pp, m, b, num_sms, s); break;
+    case FF_RHS_WILSON_COWAN: e = launch_batch_r<WilsonCowan>(method, pp, m, b, num_sms, s); break;
+    case FF_RHS_HARMONIC: e = launch_batch_r<Harmonic>(method, pp, m, b, num_sms, s); break;
+    case FF_RHS_LINEAR: e = launch_batch_r<Linear>(method, pp, m, b, num_sms, s); break;
+    case FF_RHS_HH3: e = launch_batch_r<HH3>(method, pp, m, b, num_sms, s); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    const int items = n_members * n_params_kernel;
+    if (items > 0)
+        reduce_member_rows_kernel<<<(items + 127) / 128, 128, 0, s>>>(b.partial, row0_dev, n_members,
+                                                                      n_params_kernel, b.np_stride, dp_dev);
     return cudaGetLastError();
 }
 

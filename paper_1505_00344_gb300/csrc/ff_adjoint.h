@@ -36,10 +36,34 @@ struct AdjointArgs {
     int64_t gstart[FF_MAX_GROUPS];
 };
 
+// Batched adjoint: work tiles of consecutive particles of one member (one
+// particle per thread); the parameter gradient of tile t goes to row t of
+// `partial`, and rows [row0[m], row0[m + 1]) belong to member m.
+struct AdjTile {
+    int sys;
+    int pad_;
+    int64_t first;
+    int64_t count;
+};
+
+struct BatchAdjointArgs {
+    const AdjointArgs* sys;  // per member (its partial / max_blocks fields unused)
+    const AdjTile* tiles;
+    int n_tiles;
+    int np_stride;           // doubles per partial row
+    double* partial;         // n_tiles rows
+};
+
 bool adjoint_supported(int rhs_id);
 int adjoint_sub_steps(int64_t checkpoint_every);  // M with M * M >= checkpoint_every (at most 256)
 int64_t adjoint_partial_rows(int num_sms);
 cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const AdjointArgs& a, int num_sms,
                            cudaStream_t s, double* dL_dp_dev, int n_params_kernel);
+constexpr int kAdjTile = 128;  // particles per batched-adjoint tile = threads per block
+// One batched-adjoint launch over b.tiles, then dp[m * np_stride + q] = sum of
+// member m's rows in order, for m < n_members and q < n_params_kernel.
+cudaError_t launch_batch_adjoint(int rhs_id, int method, bool pp, int m, const BatchAdjointArgs& b,
+                                 const int* row0_dev, int n_members, int n_params_kernel, int num_sms,
+                                 cudaStream_t s, double* dp_dev);
 
 }  // namespace ff

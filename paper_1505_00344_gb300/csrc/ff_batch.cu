@@ -30,6 +30,7 @@ struct BatchArgs {
     const BatchTile* tiles;
     int n_tiles;
     int n_steps;
+    float* const* ckpt;  // taped runs: per member, where to store the state before the steps (or NULL)
 };
 
 // Each block takes tiles round-robin; a tile's system (and so its parameters,
@@ -40,8 +41,18 @@ __global__ void __launch_bounds__(R::MAX_BLOCK) batch_kernel(const __grid_consta
     for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
         const BatchTile T = b.tiles[tile];
         const IntegrateArgs& a = b.sys[T.sys];
-        for (int64_t t = T.first + threadIdx.x; t < T.first + T.count; t += blockDim.x)
+        float* ck = b.ckpt ? b.ckpt[T.sys] : nullptr;
+        for (int64_t t = T.first + threadIdx.x; t < T.first + T.count; t += blockDim.x) {
+            if (ck) {  // checkpoint of a taped chunk: the state this launch starts from
+                const int64_t i0 = t * PPT;
+                for (int k = 0; k < a.dim; ++k) {
+                    float v[PPT];
+                    Vec<PPT>::load(a.x + k * a.pitch + i0, v);
+                    Vec<PPT>::store(ck + k * a.pitch + i0, v);
+                }
+            }
             integrate_item<R, METHOD, false, PP, PPT, false>(a, t, b.n_steps);
+        }
     }
 }
 
@@ -107,6 +118,20 @@ struct ff_batch {
         cudaStream_t side = nullptr;
         cudaEvent_t done = nullptr;
         double tuned_rate = 0.0;  // particle-steps/s of the chosen shape, if tuned
+        // taped runs: per member, the checkpoint slot the next launch writes (or NULL)
+        std::vector<float*> h_ckpt;
+        float** d_ckpt = nullptr;
+        // batched adjoint
+        std::vector<ff::AdjointArgs> h_adj;
+        std::vector<ff::AdjTile> adj_tiles;
+        std::vector<int> row0;
+        std::vector<double> h_dp;
+        ff::AdjointArgs* d_adj = nullptr;
+        ff::AdjTile* d_adj_tiles = nullptr;
+        int* d_row0 = nullptr;
+        double* d_partial = nullptr;
+        double* d_dp = nullptr;
+        size_t adj_tiles_cap = 0;
     };
     int device = 0, num_sms = 1;
     cudaStream_t user = nullptr;   // the caller's stream
@@ -118,6 +143,8 @@ struct ff_batch {
     std::vector<Family> fams;
     cudaGraphExec_t exec = nullptr;
     int graph_steps = -1;
+    bool graph_taped = false;
+    bool taped = false;  // the members' tapes were started by ff_batch_tape_begin
 };
 
 namespace {
@@ -174,14 +201,14 @@ ff_status upload_args(ff_batch* b, ff_batch::Family& f, const double* dts) {
     return FF_OK;
 }
 
-cudaError_t launch_family(const ff_batch::Family& f, int n_steps, cudaStream_t st) {
-    ff::BatchArgs args{f.d_sys, f.d_tiles, (int)f.tiles.size(), n_steps};
+cudaError_t launch_family(const ff_batch::Family& f, int n_steps, cudaStream_t st, bool taped = false) {
+    ff::BatchArgs args{f.d_sys, f.d_tiles, (int)f.tiles.size(), n_steps, taped ? f.d_ckpt : nullptr};
     void* params[] = {&args};
     return cudaLaunchKernel(ff::family_kernel(f.rhs_id, f.method, f.ppt, f.pp), dim3(f.grid), dim3(f.block), params, 0, st);
 }
 
 // Capture the fork/join graph of all families for this step count.
-ff_status capture(ff_batch* b, int n_steps) {
+ff_status capture(ff_batch* b, int n_steps, bool taped) {
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
@@ -191,7 +218,7 @@ ff_status capture(ff_batch* b, int n_steps) {
     cudaError_t err = cudaEventRecord(b->fork, b->cap);
     for (auto& f : b->fams) {
         if (err == cudaSuccess) err = cudaStreamWaitEvent(f.side, b->fork, 0);
-        if (err == cudaSuccess) err = launch_family(f, n_steps, f.side);
+        if (err == cudaSuccess) err = launch_family(f, n_steps, f.side, taped);
         if (err == cudaSuccess) err = cudaEventRecord(f.done, f.side);
         if (err == cudaSuccess) err = cudaStreamWaitEvent(b->cap, f.done, 0);
     }
@@ -205,12 +232,38 @@ ff_status capture(ff_batch* b, int n_steps) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "ff_batch: graph instantiate");
     b->graph_steps = n_steps;
+    b->graph_taped = taped;
+    return FF_OK;
+}
+
+// One graph launch of n_steps for every member (taped: the families' checkpoint
+// tables were filled by the caller), ordered after and before the caller's stream.
+ff_status run_graph(ff_batch* b, int64_t n_steps, const double* dt, bool taped) {
+    for (auto& f : b->fams) {
+        ff_status st = upload_args(b, f, dt);
+        if (st != FF_OK) return st;
+        if (taped) {
+            cudaError_t e = cudaMemcpyAsync(f.d_ckpt, f.h_ckpt.data(), sizeof(float*) * f.h_ckpt.size(),
+                                            cudaMemcpyHostToDevice, b->user);
+            if (e != cudaSuccess) return cuda_fail(e, "ff_batch_step: checkpoint table upload");
+        }
+    }
+    if (!b->exec || b->graph_steps != (int)n_steps || b->graph_taped != taped) {
+        ff_status st = capture(b, (int)n_steps, taped);
+        if (st != FF_OK) return st;
+    }
+    cudaError_t e = cudaEventRecord(b->join, b->user);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->cap);
+    if (e == cudaSuccess) e = cudaEventRecord(b->join, b->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->user, b->join, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_batch_step: graph launch");
     return FF_OK;
 }
 
 ff_status check_members(ff_batch* b) {
     for (size_t i = 0; i < b->systems.size(); ++i)
-        if (b->systems[i]->n_particles != b->n_particles[i] || b->systems[i]->tape_on ||
+        if (b->systems[i]->n_particles != b->n_particles[i] || b->systems[i]->tape_on != b->taped ||
             b->systems[i]->check_every > 0 || (b->systems[i]->pparam_index >= 0) != b->has_pp[i])
             return fail(FF_ERR_STATE, "ff_batch: member %zu changed since the batch was created", i);
     return FF_OK;
@@ -221,6 +274,12 @@ void destroy_batch(ff_batch* b) {
     for (auto& f : b->fams) {
         cudaFree(f.d_sys);
         cudaFree(f.d_tiles);
+        cudaFree(f.d_ckpt);
+        cudaFree(f.d_adj);
+        cudaFree(f.d_adj_tiles);
+        cudaFree(f.d_row0);
+        cudaFree(f.d_partial);
+        cudaFree(f.d_dp);
         if (f.side) cudaStreamDestroy(f.side);
         if (f.done) cudaEventDestroy(f.done);
     }
@@ -284,7 +343,9 @@ ff_status ff_batch_create(ff_system* const* systems, int n_systems, void* cuda_s
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&f.side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming);
         f.h_sys.resize(f.members.size());
+        f.h_ckpt.assign(f.members.size(), nullptr);
         if (e == cudaSuccess) e = cudaMalloc(&f.d_sys, sizeof(ff::IntegrateArgs) * f.members.size());
+        if (e == cudaSuccess) e = cudaMalloc(&f.d_ckpt, sizeof(float*) * f.members.size());
     }
     if (e != cudaSuccess) {
         ff_status st = cuda_fail(e, "ff_batch_create: resources");
@@ -322,25 +383,178 @@ ff_status ff_batch_step(ff_batch* b, int64_t n_steps, const double* dt) {
     if (n_steps == 0) return FF_OK;
     DeviceScope dev(b->device);
     if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_batch_step: set device");
-    for (auto& f : b->fams) {
-        st = upload_args(b, f, dt);
+    if (!b->taped) {
+        st = run_graph(b, n_steps, dt, false);
         if (st != FF_OK) return st;
+        for (size_t i = 0; i < b->systems.size(); ++i) {
+            b->systems[i]->steps_total += n_steps;
+            ff::account_steps(b->systems[i], n_steps, dt[i]);
+        }
+        return FF_OK;
     }
-    if (!b->exec || b->graph_steps != (int)n_steps) {
-        st = capture(b, (int)n_steps);
+    // Taped: segments that end where any member's chunk ends (every checkpoint_every
+    // steps, and where a member's parameters or dt changed); the first launch of a
+    // member's chunk stores its checkpoint from the state it loads.
+    int64_t left = n_steps;
+    while (left > 0) {
+        int64_t take = left;
+        for (auto& f : b->fams) {
+            for (size_t m = 0; m < f.members.size(); ++m) {
+                const int idx = f.members[m];
+                ff_system* s = b->systems[idx];
+                const bool need_new = s->chunks.empty() || s->chunks.back().n_steps >= s->tape_every ||
+                                      s->chunk_version != s->params_version || s->chunk_dt != dt[idx];
+                f.h_ckpt[m] = nullptr;
+                if (need_new) {
+                    if ((int64_t)s->chunks.size() >= s->tape_slots)
+                        return fail(FF_ERR_STATE, "ff_batch_step: member %d's tape is full", idx);
+                    ff::AdjChunk c{};
+                    c.n_steps = 0;
+                    c.ckpt = (int)s->chunks.size();
+                    for (int q = 0; q < s->n_params; ++q) c.p[ff::kernel_param_index(s, q)] = (float)s->params[q];
+                    for (int g = 0; g < s->n_groups; ++g) c.gh[g] = (float)(s->groups[g].direction * dt[idx]);
+                    s->chunks.push_back(c);
+                    s->chunk_version = s->params_version;
+                    s->chunk_dt = dt[idx];
+                    f.h_ckpt[m] = s->d_ckpt + (int64_t)c.ckpt * s->dim * s->pitch;
+                }
+                const int64_t room = s->tape_every - s->chunks.back().n_steps;
+                if (room < take) take = room;
+            }
+        }
+        st = run_graph(b, take, dt, true);
         if (st != FF_OK) return st;
+        for (size_t i = 0; i < b->systems.size(); ++i) {
+            b->systems[i]->chunks.back().n_steps += (int)take;
+            b->systems[i]->steps_total += take;
+            ff::account_steps(b->systems[i], take, dt[i]);
+        }
+        left -= take;
     }
-    // order the graph after the caller's stream and the caller's stream after the graph
-    cudaError_t e = cudaEventRecord(b->join, b->user);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->join, 0);
-    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->cap);
-    if (e == cudaSuccess) e = cudaEventRecord(b->join, b->cap);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->user, b->join, 0);
-    if (e != cudaSuccess) return cuda_fail(e, "ff_batch_step: graph launch");
+    return FF_OK;
+}
+
+ff_status ff_batch_tape_begin(ff_batch* b, int64_t checkpoint_every, int64_t max_steps) {
+    if (!b) return fail(FF_ERR_INVALID_ARG, "ff_batch_tape_begin: batch is NULL");
+    if (b->taped) return fail(FF_ERR_STATE, "ff_batch_tape_begin: already taped (ff_batch_tape_end first)");
+    ff_status st = check_members(b);
+    if (st != FF_OK) return st;
+    DeviceScope dev(b->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_batch_tape_begin: set device");
+    cudaError_t e = cudaStreamSynchronize(b->user);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_batch_tape_begin: synchronise");
     for (size_t i = 0; i < b->systems.size(); ++i) {
-        b->systems[i]->steps_total += n_steps;
-        ff::account_steps(b->systems[i], n_steps, dt[i]);
+        st = ff_tape_begin(b->systems[i], checkpoint_every, max_steps);
+        if (st != FF_OK) {
+            for (size_t j = 0; j < i; ++j) ff_tape_end(b->systems[j]);
+            return st;
+        }
     }
+    b->taped = true;
+    return FF_OK;
+}
+
+ff_status ff_batch_tape_end(ff_batch* b) {
+    if (!b) return fail(FF_ERR_INVALID_ARG, "ff_batch_tape_end: batch is NULL");
+    DeviceScope dev(b->device);
+    cudaStreamSynchronize(b->user);
+    for (auto* s : b->systems) ff_tape_end(s);
+    b->taped = false;
+    return FF_OK;
+}
+
+ff_status ff_batch_backward(ff_batch* b, const float* const* dL_dxT_dev, float* const* dL_dx0_dev,
+                            double* dL_dp_host) {
+    if (!b) return fail(FF_ERR_INVALID_ARG, "ff_batch_backward: batch is NULL");
+    if (!dL_dxT_dev || !dL_dx0_dev || !dL_dp_host) return fail(FF_ERR_INVALID_ARG, "ff_batch_backward: NULL array");
+    for (size_t i = 0; i < b->systems.size(); ++i)
+        if (!dL_dxT_dev[i] || !dL_dx0_dev[i])
+            return fail(FF_ERR_INVALID_ARG, "ff_batch_backward: NULL buffer of member %zu", i);
+    if (!b->taped) return fail(FF_ERR_STATE, "ff_batch_backward: no tape (ff_batch_tape_begin before stepping)");
+    ff_status st = check_members(b);
+    if (st != FF_OK) return st;
+    DeviceScope dev(b->device);
+    if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_batch_backward: set device");
+    cudaError_t e = cudaSuccess;
+    for (auto& f : b->fams) {
+        const int nm = (int)f.members.size();
+        f.h_adj.assign(nm, ff::AdjointArgs{});
+        f.adj_tiles.clear();
+        f.row0.assign(nm + 1, 0);
+        for (int m = 0; m < nm && e == cudaSuccess; ++m) {
+            const int idx = f.members[m];
+            ff_system* s = b->systems[idx];
+            if (!s->chunks.empty())
+                e = cudaMemcpyAsync(s->d_chunks, s->chunks.data(), sizeof(ff::AdjChunk) * s->chunks.size(),
+                                    cudaMemcpyHostToDevice, b->user);
+            ff::AdjointArgs& a = f.h_adj[m];
+            a.ckpt = s->d_ckpt;
+            a.chunks = s->d_chunks;
+            a.n_chunks = (int)s->chunks.size();
+            a.dim = s->dim;
+            a.lam_in = dL_dxT_dev[idx];
+            a.lam_out = dL_dx0_dev[idx];
+            a.pparam = s->d_pparam;
+            a.pidx = s->pparam_index >= 0 ? ff::kernel_param_index(s, s->pparam_index) : -1;
+            a.np_stride = FF_MAX_PARAMS;
+            a.n = s->n_particles;
+            a.pitch = s->pitch;
+            a.n_groups = s->n_groups;
+            for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
+            f.row0[m] = (int)f.adj_tiles.size();
+            for (int64_t first = 0; first < s->n_particles; first += ff::kAdjTile) {
+                ff::AdjTile t{};
+                t.sys = m;
+                t.first = first;
+                t.count = s->n_particles - first < ff::kAdjTile ? s->n_particles - first : ff::kAdjTile;
+                f.adj_tiles.push_back(t);
+            }
+        }
+        f.row0[nm] = (int)f.adj_tiles.size();
+        if (e != cudaSuccess) break;
+        if (!f.d_adj) {
+            e = cudaMalloc(&f.d_adj, sizeof(ff::AdjointArgs) * nm);
+            if (e == cudaSuccess) e = cudaMalloc(&f.d_row0, sizeof(int) * (nm + 1));
+            if (e == cudaSuccess) e = cudaMalloc(&f.d_dp, sizeof(double) * FF_MAX_PARAMS * nm);
+        }
+        if (e == cudaSuccess && f.adj_tiles.size() > f.adj_tiles_cap) {
+            cudaFree(f.d_adj_tiles);
+            cudaFree(f.d_partial);
+            f.d_adj_tiles = nullptr;
+            f.d_partial = nullptr;
+            f.adj_tiles_cap = 0;
+            e = cudaMalloc(&f.d_adj_tiles, sizeof(ff::AdjTile) * f.adj_tiles.size());
+            if (e == cudaSuccess) e = cudaMalloc(&f.d_partial, sizeof(double) * FF_MAX_PARAMS * f.adj_tiles.size());
+            if (e == cudaSuccess) f.adj_tiles_cap = f.adj_tiles.size();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(f.d_adj, f.h_adj.data(), sizeof(ff::AdjointArgs) * nm, cudaMemcpyHostToDevice, b->user);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(f.d_adj_tiles, f.adj_tiles.data(), sizeof(ff::AdjTile) * f.adj_tiles.size(),
+                                cudaMemcpyHostToDevice, b->user);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(f.d_row0, f.row0.data(), sizeof(int) * (nm + 1), cudaMemcpyHostToDevice, b->user);
+        if (e != cudaSuccess) break;
+        ff::BatchAdjointArgs ba{f.d_adj, f.d_adj_tiles, (int)f.adj_tiles.size(), FF_MAX_PARAMS, f.d_partial};
+        const ff_system* s0 = b->systems[f.members[0]];
+        const int np_kernel = f.rhs_id == FF_RHS_LINEAR ? 64 : s0->n_params;
+        e = ff::launch_batch_adjoint(f.rhs_id, f.method, f.pp, ff::adjoint_sub_steps(s0->tape_every), ba, f.d_row0,
+                                     nm, np_kernel, b->num_sms, b->user, f.d_dp);
+        if (e != cudaSuccess) break;
+        f.h_dp.assign((size_t)FF_MAX_PARAMS * nm, 0.0);
+        e = cudaMemcpyAsync(f.h_dp.data(), f.d_dp, sizeof(double) * FF_MAX_PARAMS * nm, cudaMemcpyDeviceToHost,
+                            b->user);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->user);
+    if (e != cudaSuccess) return cuda_fail(e, "ff_batch_backward");
+    for (auto& f : b->fams)
+        for (size_t m = 0; m < f.members.size(); ++m) {
+            const int idx = f.members[m];
+            const ff_system* s = b->systems[idx];
+            for (int q = 0; q < FF_MAX_PARAMS; ++q)
+                dL_dp_host[(size_t)idx * FF_MAX_PARAMS + q] =
+                    q < s->n_params ? f.h_dp[m * FF_MAX_PARAMS + ff::kernel_param_index(s, q)] : 0.0;
+        }
     return FF_OK;
 }
 

@@ -114,6 +114,9 @@ def test_host_side_argument_errors(lib):
     assert lib.ff_batch_autotune(None, None, 8) == ff.FF_ERR_INVALID_ARG
     assert lib.ff_batch_describe(None, None, 0) == ff.FF_ERR_INVALID_ARG
     assert lib.ff_batch_destroy(None) == ff.FF_OK
+    assert lib.ff_batch_tape_begin(None, 10, 10) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_batch_tape_end(None) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_batch_backward(None, None, None, None) == ff.FF_ERR_INVALID_ARG
     sp = ff.make_sprite(2.0)
     assert lib.ff_project_sprites(None, None, ctypes.byref(sp), None, 1) == ff.FF_ERR_INVALID_ARG
 

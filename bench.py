@@ -67,6 +67,7 @@ def parse():
     # profiling cases only (a line taken with these is not the workload's number)
     ap.add_argument("--particles", type=int, default=0, help="scale the workload to this many particles")
     ap.add_argument("--frames", type=int, default=0, help="run only this many frames per step")
+    ap.add_argument("--frame-steps", type=int, default=0, help="RK4 steps per frame (profiling cases)")
     return ap.parse_args()
 
 
@@ -76,6 +77,8 @@ def workload_for(args, rank, world):
         w = W.scaled(w, args.particles)
     if args.frames:
         w = dict(w, frames=args.frames)
+    if args.frame_steps:
+        w = dict(w, steps_per_frame=args.frame_steps)
     return w
 
 
@@ -505,6 +508,86 @@ def run_adjoint(args, rank, world, local):
             "ms": {"plain": med(t_plain), "taped_forward": med(t_fwd), "backward": med(t_bwd)}}
 
 
+def run_batch_adjoint(args, rank, world, local):
+    """The differentiable batched ensemble: a taped ff_batch_step of --adjoint-steps RK4
+    steps (checkpoint every --checkpoint-every) and one ff_batch_backward, gradients of
+    L = sum_s (1/P_s) sum_i |x_i(T) - t_i|^2 w.r.t. every member's initial states and
+    parameters; against the plain batched forward."""
+    import torch
+    import paper_1505_00344_gb300 as ff
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream().cuda_stream
+    ws = W.batch_workload(args.batch)
+    systems = [ff.System.from_workload(w, stream=stream) for w in ws]
+    dts = [w["dt"] for w in ws]
+    n, K = args.adjoint_steps, args.checkpoint_every
+    b = ff.Batch(systems, stream=stream)
+    b.autotune(dts, trial_steps=16)
+    x0, tgt = [], []
+    for k, (s, w) in enumerate(zip(systems, ws)):
+        P, dim = total_particles(w), w["dim"]
+        x = torch.empty((dim, P), dtype=torch.float32, device=dev)
+        s.get_state(x)
+        x0.append(x)
+        g = torch.Generator(device=dev).manual_seed(7000 + k)
+        lo = torch.tensor(w["groups"][0]["lo"], dtype=torch.float32, device=dev)[:, None]
+        hi = torch.tensor(w["groups"][0]["hi"], dtype=torch.float32, device=dev)[:, None]
+        tgt.append(lo + (hi - lo) * torch.rand((dim, P), generator=g, device=dev))
+    units = sum(total_particles(w) for w in ws) * n
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(e)
+
+    def restore():
+        for s, x in zip(systems, x0):
+            s.set_state(x)
+
+    grads = [torch.empty_like(x) for x in x0]
+    outs = [torch.empty_like(x) for x in x0]
+
+    def loss_grads():
+        for s, x, t, g in zip(systems, x0, tgt, grads):
+            s.get_state(g)
+            g.sub_(t).mul_(2.0 / x.shape[1])
+
+    t_plain, t_fwd, t_bwd = [], [], []
+    for it in range(args.warmup + max(1, args.steps)):
+        restore()
+        tp = timed(lambda: b.step(n, dts))
+        restore()
+        b.tape_begin(K, n)
+        tf = timed(lambda: b.step(n, dts))
+        loss_grads()
+        tb = timed(lambda: b.backward(grads, outs))
+        b.tape_end()
+        if it >= args.warmup:
+            t_plain.append(tp)
+            t_fwd.append(tf)
+            t_bwd.append(tb)
+    med = statistics.median
+    return {"metric": "adjoint particle-RK4-steps/sec (batched ensemble, gradients w.r.t. all initial states "
+                      "and parameters)",
+            "value": units / (med(t_bwd) / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": med(t_bwd), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP64 parameter sums)", "data": "synthetic",
+            "config": {"workload": args.batch, "systems": len(ws), "particles": units // n, "rk4_steps": n,
+                       "checkpoint_every": K, "loss": "sum over systems of the mean squared endpoint distance "
+                                                     "to seeded targets",
+                       "launch": b.describe().strip().split("\n")},
+            "plain_forward": units / (med(t_plain) / 1e3), "taped_forward": units / (med(t_fwd) / 1e3),
+            "backward_over_plain_time": med(t_bwd) / med(t_plain),
+            "ms": {"plain": med(t_plain), "taped_forward": med(t_fwd), "backward": med(t_bwd)}}
+
+
 def run_batch(args, rank, world, local):
     """A batched workload: ff_batch_step (one graph launch, autotuned launch shapes) against
     stepping the same systems one after the other with ff_step."""
@@ -631,6 +714,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.batch and args.adjoint:
+        out = run_batch_adjoint(args, rank, world, local)
     elif args.adjoint:
         out = run_adjoint(args, rank, world, local)
     elif args.batch:

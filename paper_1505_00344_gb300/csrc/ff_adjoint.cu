@@ -215,6 +215,25 @@ __device__ __forceinline__ void fwd_step(float (&x)[R::DIM], float h, const floa
     }
     const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
     float k[D], xs[D], acc[D];
+    if constexpr (D > 8) {
+        // large systems: the four stages as a loop over one copy of f (same arithmetic)
+#pragma unroll
+        for (int i = 0; i < D; ++i) xs[i] = x[i];
+#pragma unroll 1
+        for (int st = 0; st < 4; ++st) {
+            R::f(xs, p, k);
+            const float c = (st == 2) ? h : h2;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                if (st == 0) acc[i] = k[i];
+                else if (st < 3) acc[i] = fmaf(2.0f, k[i], acc[i]);
+                xs[i] = fmaf(c, k[i], x[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) x[i] = fmaf(h6, acc[i] + k[i], x[i]);
+        return;
+    }
     R::f(x, p, k);
 #pragma unroll
     for (int i = 0; i < D; ++i) { acc[i] = k[i]; xs[i] = fmaf(h2, k[i], x[i]); }
@@ -251,6 +270,42 @@ __device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[
         return;
     }
     const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
+    if constexpr (D > 8) {
+        // large systems: stage points in a (local-memory) array, each pass one copy of f
+        // or of the vector-Jacobian product; the same operations in the same order as below
+        float xs[4][D], k[D], l[D], m[D], sum[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) xs[0][i] = x[i];
+#pragma unroll 1
+        for (int st = 0; st < 3; ++st) {
+            R::f(xs[st], p, k);
+            const float c = (st == 2) ? h : h2;
+#pragma unroll
+            for (int i = 0; i < D; ++i) xs[st + 1][i] = fmaf(c, k[i], x[i]);
+        }
+#pragma unroll 1
+        for (int st = 3; st >= 0; --st) {
+            if (st == 3) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) l[i] = h6 * lam[i];
+            } else {
+                const float cl = (st == 0) ? h6 : h3, cm = (st == 2) ? h : h2;
+#pragma unroll
+                for (int i = 0; i < D; ++i) l[i] = fmaf(cl, lam[i], cm * m[i]);
+            }
+            Vjp<R>::apply(xs[st], p, l, m, jp);
+            if (st == 3) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) sum[i] = m[i];
+            } else if (st > 0) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) sum[i] = __fadd_rn(sum[i], m[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) lam[i] = __fadd_rn(lam[i], __fadd_rn(sum[i], m[i]));
+        return;
+    }
     float k[D], x2[D], x3[D], x4[D];
     R::f(x, p, k);
 #pragma unroll

@@ -235,26 +235,18 @@ __device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c,
 }
 
 template <int NDV, bool MASKED>
-__global__ void __launch_bounds__(kSplatBlock, 5) sprite_kernel(const __grid_constant__ SpriteArgs a) {
+__global__ void __launch_bounds__(kSplatBlock) sprite_kernel(const __grid_constant__ SpriteArgs a) {
     const int64_t n4 = (a.n + 3) / 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float R = a.R, lo_c = -R - 1.0f, hi_c = a.v.Wf + R + 1.0f, hi_r = a.v.Hf + R + 1.0f;
-    // the coordinates of the next grid-stride step are loaded before this step's
-    // footprints are walked, so their latency overlaps the reductions
-    auto load = [&](int64_t t, float4& u4, float4& v4, float4& w4) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += stride) {
         const int64_t i0 = 4 * t;
-        u4 = __ldcs(reinterpret_cast<const float4*>(a.ax[0] + i0));
-        v4 = __ldcs(reinterpret_cast<const float4*>(a.ax[1] + i0));
+        const float4 u4 = __ldcs(reinterpret_cast<const float4*>(a.ax[0] + i0));
+        const float4 v4 = __ldcs(reinterpret_cast<const float4*>(a.ax[1] + i0));
+        float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (NDV == 3) w4 = __ldcs(reinterpret_cast<const float4*>(a.ax[2] + i0));
-    };
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float4 nu = make_float4(0.f, 0.f, 0.f, 0.f), nv = nu, nw = nu;
-    if (t < n4) load(t, nu, nv, nw);
-    for (; t < n4; t += stride) {
-        const int64_t i0 = 4 * t;
-        const float u[4] = {nu.x, nu.y, nu.z, nu.w}, v[4] = {nv.x, nv.y, nv.z, nv.w},
-                    w[4] = {nw.x, nw.y, nw.z, nw.w};
-        if (t + stride < n4) load(t + stride, nu, nv, nw);
+        const float u[4] = {u4.x, u4.y, u4.z, u4.w}, v[4] = {v4.x, v4.y, v4.z, v4.w},
+                    w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int64_t i = i0 + j;

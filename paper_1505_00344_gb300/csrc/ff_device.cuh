@@ -230,18 +230,39 @@ struct GenericRK4 {
     __device__ __forceinline__ void from_internal(float (&)[D]) const {}
     __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
         float k[D], xs[D];
-        R::f(x, p, k);
+        if constexpr (D > 8) {
+            // large systems: one copy of f in a loop over the four stages, so the step's
+            // code fits the instruction caches (the weights 1 make fmaf(1, k, a) = a + k,
+            // so the result is the same as the unrolled form's)
 #pragma unroll
-        for (int i = 0; i < D; ++i) { a[i] = k[i]; xs[i] = fmaf(h2, k[i], x[i]); }
-        R::f(xs, p, k);
+            for (int i = 0; i < D; ++i) xs[i] = x[i];
+#pragma unroll 1
+            for (int st = 0; st < 4; ++st) {
+                R::f(xs, p, k);
+                const float w = (st == 1 || st == 2) ? 2.0f : 1.0f;
+                const float c = (st == 2) ? h1 : h2;
 #pragma unroll
-        for (int i = 0; i < D; ++i) { a[i] = fmaf(2.0f, k[i], a[i]); xs[i] = fmaf(h2, k[i], x[i]); }
-        R::f(xs, p, k);
+                for (int i = 0; i < D; ++i) {
+                    a[i] = (st == 0) ? k[i] : fmaf(w, k[i], a[i]);
+                    xs[i] = fmaf(c, k[i], x[i]);
+                }
+            }
 #pragma unroll
-        for (int i = 0; i < D; ++i) { a[i] = fmaf(2.0f, k[i], a[i]); xs[i] = fmaf(h1, k[i], x[i]); }
-        R::f(xs, p, k);
+            for (int i = 0; i < D; ++i) sc[i] = h6;
+        } else {
+            R::f(x, p, k);
 #pragma unroll
-        for (int i = 0; i < D; ++i) { a[i] = a[i] + k[i]; sc[i] = h6; }
+            for (int i = 0; i < D; ++i) { a[i] = k[i]; xs[i] = fmaf(h2, k[i], x[i]); }
+            R::f(xs, p, k);
+#pragma unroll
+            for (int i = 0; i < D; ++i) { a[i] = fmaf(2.0f, k[i], a[i]); xs[i] = fmaf(h2, k[i], x[i]); }
+            R::f(xs, p, k);
+#pragma unroll
+            for (int i = 0; i < D; ++i) { a[i] = fmaf(2.0f, k[i], a[i]); xs[i] = fmaf(h1, k[i], x[i]); }
+            R::f(xs, p, k);
+#pragma unroll
+            for (int i = 0; i < D; ++i) { a[i] = a[i] + k[i]; sc[i] = h6; }
+        }
     }
 };
 
@@ -486,8 +507,7 @@ __device__ __forceinline__ void integrate_item(const IntegrateArgs& a, int64_t t
     const int n_steps = n_steps_run;  // the host splits launches at 2^30 steps
     // steps until the next reset check (global step numbers that are multiples of check_every)
     int countdown = RESET ? a.check_every - (int)(a.step0 % a.check_every) : 0;
-#pragma unroll 4
-    for (int s = 0; s < n_steps; ++s) {
+    auto step = [&]() {
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             float acc[D], sc[D];
@@ -510,6 +530,14 @@ __device__ __forceinline__ void integrate_item(const IntegrateArgs& a, int64_t t
 #pragma unroll
             for (int j = 0; j < PPT; ++j) reset_check<D>(a, st[j], x[j], c[j], age[j], nres[j], grp[j], i0 + j);
         }
+    };
+    if constexpr (D > 8) {
+        // a step of a large system is long enough on its own; unrolling only grows the code
+#pragma unroll 1
+        for (int s = 0; s < n_steps; ++s) step();
+    } else {
+#pragma unroll 4
+        for (int s = 0; s < n_steps; ++s) step();
     }
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {

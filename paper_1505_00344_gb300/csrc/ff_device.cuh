@@ -148,7 +148,7 @@ __device__ __forceinline__ float bernoulli_series(float y) {
 // The rate exponentials share one exp2: with u = V + 65 and q = exp(-u/80),
 // exp(-u/20) = q^4, exp(-u/10) = q^8, and exp(-(V+40)/10), exp(-(V+55)/10),
 // exp(-(V+35)/10) are e^2.5, e^1 and e^3 times q^8; beta_m and the synaptic
-// sigmoid take one exp2 each.  The four reciprocals are formed two at a time
+// sigmoid take one exp2 each, their constant factors folded into the exponent.  The four reciprocals are formed two at a time
 // (1/a = b / (a b)).  alpha_m, alpha_n = v / (1 - exp(-v/10)) switch to the
 // Bernoulli series for |v/10| < 0.5, where the FP32 difference would cancel.
 // 5 MUFU operations per neuron instead of 11.
@@ -160,33 +160,35 @@ struct HH3 {
         const float C = p[0], gNa = p[1], gK = p[2], gL = p[3];
         const float ENa = p[4], EK = p[5], EL = p[6], gsyn = p[7], Esyn = p[8];
         const float inv_tr = __fdividef(1.0f, p[12]), inv_td = __fdividef(1.0f, p[13]);
-        const float sig2 = p[14] * kLog2e, theta = p[15];
+        const float sig2 = p[14] * kLog2e, sig2_theta = sig2 * p[15];
         const float invC = __fdividef(1.0f, C);
         const float s_sum = x[4] + x[9] + x[14];
         constexpr float kE25 = 12.182493960703473f;  // e^2.5
         constexpr float kE1 = 2.718281828459045f;    // e^1
         constexpr float kE3 = 20.085536923187668f;   // e^3
+        // q = e^(-(V+65)/80) = 2^(kQ V + kQ0); beta_m = 4 e^(-(V+65)/18) = 2^(kB V + kB0)
+        constexpr float kQ = -kLog2e / 80.0f, kQ0 = 65.0f * (-kLog2e / 80.0f);
+        constexpr float kB = -kLog2e / 18.0f, kB0 = 65.0f * (-kLog2e / 18.0f) + 2.0f;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const float V = x[5 * i], m = x[5 * i + 1], h = x[5 * i + 2], n = x[5 * i + 3];
             const float s = x[5 * i + 4];
-            const float u = V + 65.0f;
-            const float q = exp2f(u * (-kLog2e / 80.0f));
+            const float q = exp2f(fmaf(V, kQ, kQ0));
             const float q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
-            const float em = kE25 * q8, en = kE1 * q8, eh = kE3 * q8;
-            const float bm = 4.0f * exp2f(u * (-kLog2e / 18.0f));
+            const float bm = exp2f(fmaf(V, kB, kB0));
             const float ah = 0.07f * q4;
             const float bn = 0.125f * q;
-            const float es = exp2f(sig2 * (theta - V));
-            // alpha_m, alpha_n: v / (1 - e) with v = V + 40, V + 55
-            const float vm = V + 40.0f, vn = V + 55.0f;
-            const bool sm = fabsf(vm) < 5.0f, sn = fabsf(vn) < 5.0f;  // |v/10| < 0.5: series
-            const float dm = sm ? 1.0f : 1.0f - em, dn = sn ? 1.0f : 1.0f - en;
+            const float es = exp2f(fmaf(-sig2, V, sig2_theta));  // e^(sig (theta - V))
+            // alpha_m = g(ym), alpha_n = g(yn) / 10 with g(y) = y / (1 - e^-y),
+            // ym = (V + 40) / 10, yn = (V + 55) / 10, e^-ym = e^2.5 q^8, e^-yn = e q^8
+            const float ym = fmaf(V, 0.1f, 4.0f), yn = fmaf(V, 0.1f, 5.5f);
+            const bool sm = fabsf(ym) < 0.5f, sn = fabsf(yn) < 0.5f;  // series there
+            const float dm = sm ? 1.0f : fmaf(-kE25, q8, 1.0f), dn = sn ? 1.0f : fmaf(-kE1, q8, 1.0f);
             const float rmn = __fdividef(1.0f, dm * dn);
-            const float am = 0.1f * (sm ? 10.0f * bernoulli_series(vm * 0.1f) : vm * dn * rmn);
-            const float an = 0.01f * (sn ? 10.0f * bernoulli_series(vn * 0.1f) : vn * dm * rmn);
-            // beta_h = 1 / (1 + eh), act = 1 / (1 + es)
-            const float ph = 1.0f + eh, ps = 1.0f + es;
+            const float am = sm ? bernoulli_series(ym) : ym * dn * rmn;
+            const float an = 0.1f * (sn ? bernoulli_series(yn) : yn * dm * rmn);
+            // beta_h = 1 / (1 + e^3 q^8), act = 1 / (1 + es)
+            const float ph = fmaf(kE3, q8, 1.0f), ps = 1.0f + es;
             const float rhs_ = __fdividef(1.0f, ph * ps);
             const float bh = ps * rhs_;
             const float act = ph * rhs_;
@@ -235,17 +237,17 @@ struct GenericRK4 {
             // code fits the instruction caches (the weights 1 make fmaf(1, k, a) = a + k,
             // so the result is the same as the unrolled form's)
 #pragma unroll
-            for (int i = 0; i < D; ++i) xs[i] = x[i];
+            for (int i = 0; i < D; ++i) { xs[i] = x[i]; a[i] = 0.0f; }
 #pragma unroll 1
             for (int st = 0; st < 4; ++st) {
                 R::f(xs, p, k);
-                const float w = (st == 1 || st == 2) ? 2.0f : 1.0f;
+                const float w = (st == 1 || st == 2) ? 2.0f : 1.0f;  // fmaf(1, k, 0) = k
+#pragma unroll
+                for (int i = 0; i < D; ++i) a[i] = fmaf(w, k[i], a[i]);
+                if (st == 3) break;
                 const float c = (st == 2) ? h1 : h2;
 #pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    a[i] = (st == 0) ? k[i] : fmaf(w, k[i], a[i]);
-                    xs[i] = fmaf(c, k[i], x[i]);
-                }
+                for (int i = 0; i < D; ++i) xs[i] = fmaf(c, k[i], x[i]);
             }
 #pragma unroll
             for (int i = 0; i < D; ++i) sc[i] = h6;

@@ -177,11 +177,28 @@ def traffic_from_profile(kernel_src_hash):
     return float(m.group(1))
 
 
+def _between(text, start, end):
+    """The part of text from the line holding `start` up to (not including) `end`."""
+    i = text.index(start)
+    i = text.rfind("\n", 0, i) + 1
+    return text[i:text.index(end, i)]
+
+
 def kernel_source_hash():
-    """Hash of the integrator's sources; a profile taken on other sources gives no traffic."""
+    """Hash of the source the fused Lorenz integrator is compiled from: its argument block,
+    the vector loads, the packed-pair section of ff_device.cuh, the view/pixel rule and
+    ff_integrate_lorenz.cu.  A profile taken on other sources gives no traffic."""
+    csrc = os.path.join(ROOT, "paper_1505_00344_gb300", "csrc")
+    dev = open(os.path.join(csrc, "ff_device.cuh")).read()
+    proj = open(os.path.join(csrc, "ff_project.cuh")).read()
+    parts = [_between(dev, "struct IntegrateArgs {", "\n};\n") ,
+             _between(dev, "// Vector access of PPT consecutive floats.", "// Reset test and re-draw"),
+             _between(dev, "// Packed-pair RK4 for Lorenz.", "// Host-side launch of one integrator"),
+             _between(proj, "struct ViewArgs {", "// Continuous pixel coordinates"),
+             open(os.path.join(csrc, "ff_integrate_lorenz.cu")).read()]
     h = hashlib.sha256()
-    for f in ("ff_device.cuh", "ff_integrate_lorenz.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1505_00344_gb300", "csrc", f), "rb").read())
+    for part in parts:
+        h.update(part.encode())
     return h.hexdigest()[:16]
 
 

@@ -332,8 +332,9 @@ ff_status ff_backward(ff_system* sys, const float* dL_dxT_dev, float* dL_dx0_dev
  *   take effect at the next call.  Asynchronous.
  * ff_batch_autotune: times every launch shape (particles per thread 1/2/4 for
  *   dimension <= 4, blocks of 64..512 threads) of each family on the members'
- *   own data for trial_steps steps (twice), keeps the fastest, and restores the
- *   members' states exactly.  Synchronises.
+ *   own data for trial_steps steps (twice), keeps the fastest, then times the
+ *   same trial split into 2 and 4 launches (steps per launch) and keeps a split
+ *   if it is faster; restores the members' states exactly.  Synchronises.
  * ff_batch_describe: one line per family: members, launch shape, tiles, tuned
  *   rate (NUL-terminated, truncated to text_len).
  *

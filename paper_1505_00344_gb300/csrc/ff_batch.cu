@@ -110,6 +110,7 @@ struct ff_batch {
         bool pp = false;  // members have a per-particle parameter
         std::vector<int> members;  // indices into systems
         int ppt = 1, block = 256, grid = 1;
+        int steps_per_launch = 0;  // 0: one launch per call; else launches of at most this many steps
         std::vector<ff::BatchTile> tiles;
         std::vector<ff::IntegrateArgs> h_sys;
         ff::IntegrateArgs* d_sys = nullptr;
@@ -218,7 +219,11 @@ ff_status capture(ff_batch* b, int n_steps, bool taped) {
     cudaError_t err = cudaEventRecord(b->fork, b->cap);
     for (auto& f : b->fams) {
         if (err == cudaSuccess) err = cudaStreamWaitEvent(f.side, b->fork, 0);
-        if (err == cudaSuccess) err = launch_family(f, n_steps, f.side, taped);
+        // the branch: launches of at most steps_per_launch steps; only the first of a taped
+        // segment stores the checkpoints
+        const int per = f.steps_per_launch > 0 ? f.steps_per_launch : n_steps;
+        for (int done = 0; done < n_steps && err == cudaSuccess; done += per)
+            err = launch_family(f, per < n_steps - done ? per : n_steps - done, f.side, taped && done == 0);
         if (err == cudaSuccess) err = cudaEventRecord(f.done, f.side);
         if (err == cudaSuccess) err = cudaStreamWaitEvent(b->cap, f.done, 0);
     }
@@ -612,6 +617,28 @@ ff_status ff_batch_autotune(ff_batch* b, const double* dt, int64_t trial_steps) 
                 }
             }
         }
+        // steps per launch at the best shape: the whole call, or the trial split into 2 or 4 launches
+        f.ppt = best_ppt;
+        f.block = best_block;
+        f.steps_per_launch = 0;
+        if (st == FF_OK && e == cudaSuccess) st = build_tiles(b, f);
+        if (st == FF_OK && e == cudaSuccess) st = upload_args(b, f, dt);
+        for (int parts = 2; parts <= 4 && st == FF_OK && e == cudaSuccess && trial_steps >= parts; parts *= 2) {
+            const int per = (int)((trial_steps + parts - 1) / parts);
+            e = cudaEventRecord(t0, b->user);
+            for (int64_t done = 0; done < trial_steps && e == cudaSuccess; done += per)
+                e = launch_family(f, (int)(per < trial_steps - done ? per : trial_steps - done), b->user);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, b->user);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            const double rate = (double)units * trial_steps / (ms * 1e-3);
+            if (e == cudaSuccess && rate > best) {
+                best = rate;
+                f.steps_per_launch = per;
+            }
+        }
+        // put the members' states back
         for (size_t m = 0; m < f.members.size(); ++m) {
             if (saved[m] && e == cudaSuccess) {
                 const ff_system* s = b->systems[f.members[m]];
@@ -620,10 +647,7 @@ ff_status ff_batch_autotune(ff_batch* b, const double* dt, int64_t trial_steps) 
             }
             cudaFree(saved[m]);
         }
-        f.ppt = best_ppt;
-        f.block = best_block;
         f.tuned_rate = best;
-        if (st == FF_OK && e == cudaSuccess) st = build_tiles(b, f);
         if (st != FF_OK || e != cudaSuccess) break;
     }
     cudaEventDestroy(t0);
@@ -646,6 +670,10 @@ ff_status ff_batch_describe(ff_batch* b, char* text, int text_len) {
                  names[f.rhs_id], f.method == FF_RK4 ? "rk4" : "euler", f.pp ? "/per-particle" : "",
                  f.members.size(), f.ppt, f.block, f.grid, f.tiles.size(), f.tuned_rate > 0 ? "" : " (untuned)");
         out += line;
+        if (f.steps_per_launch > 0) {
+            snprintf(line, sizeof(line), ", at most %d steps per launch", f.steps_per_launch);
+            out += line;
+        }
         if (f.tuned_rate > 0) {
             snprintf(line, sizeof(line), ", tuned %.3e particle-steps/s", f.tuned_rate);
             out += line;

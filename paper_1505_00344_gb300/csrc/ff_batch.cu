@@ -37,7 +37,7 @@ struct BatchArgs {
 // groups and step sizes) is the same for the whole block.  A family's members
 // either all have a per-particle parameter (PP) or none has.
 template <class R, int METHOD, bool PP, int PPT>
-__global__ void __launch_bounds__(R::MAX_BLOCK) batch_kernel(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(R::MAX_BLOCK, MinBlocks<R>::value) batch_kernel(const __grid_constant__ BatchArgs b) {
     for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
         const BatchTile T = b.tiles[tile];
         const IntegrateArgs& a = b.sys[T.sys];

@@ -135,77 +135,133 @@ struct Lorenz {
     }
 };
 
-// Bernoulli series of y / (1 - exp(-y)) = 1 + y/2 + y^2/12 - y^4/720 + y^6/30240
-// (the next term, -y^8/1209600, is below 3.3e-9 for |y| < 0.5).
-__device__ __forceinline__ float bernoulli_series(float y) {
-    const float y2 = y * y;
-    const float even = fmaf(y2, fmaf(y2, fmaf(y2, 1.0f / 30240.0f, -1.0f / 720.0f), 1.0f / 12.0f), 1.0f);
-    return fmaf(0.5f, y, even);
-}
-
 // Three Hodgkin-Huxley neurons (paper Eq. 6-11), state (V, m, h, n, s) per
 // neuron, all-to-all synapses; rates of Hodgkin & Huxley 1952, rest near -65 mV.
 // The rate exponentials share one exp2: with u = V + 65 and q = exp(-u/80),
 // exp(-u/20) = q^4, exp(-u/10) = q^8, and exp(-(V+40)/10), exp(-(V+55)/10),
 // exp(-(V+35)/10) are e^2.5, e^1 and e^3 times q^8; beta_m and the synaptic
-// sigmoid take one exp2 each, their constant factors folded into the exponent.  The four reciprocals are formed two at a time
-// (1/a = b / (a b)).  alpha_m, alpha_n = v / (1 - exp(-v/10)) switch to the
-// Bernoulli series for |v/10| < 0.5, where the FP32 difference would cancel.
-// 5 MUFU operations per neuron instead of 11.
+// sigmoid take one exp2 each, their constant factors folded into the exponent.
+// The four reciprocals are formed two at a time (1/a = b / (a b)).  alpha_m,
+// alpha_n = v / (1 - exp(-v/10)) switch to the Bernoulli series for |v/10| <
+// 0.5, where the FP32 difference would cancel.  5 MUFU operations per neuron.
+//
+// One neuron's right-hand side is written once over a lane type: O = HHScalar
+// (one neuron) or, further below, the packed pair type (two neurons of one
+// particle in one f32x2 register).  Every operation is explicit and rounded on
+// its own, so both forms give the same bits lane by lane.
+struct HHScalar {
+    using T = float;
+    using M = bool;
+    __device__ __forceinline__ static T k(float c) { return c; }
+    __device__ __forceinline__ static T add(T a, T b) { return __fadd_rn(a, b); }
+    __device__ __forceinline__ static T sub(T a, T b) { return __fsub_rn(a, b); }
+    __device__ __forceinline__ static T mul(T a, T b) { return __fmul_rn(a, b); }
+    __device__ __forceinline__ static T fma(T a, T b, T c) { return fmaf(a, b, c); }
+    __device__ __forceinline__ static T ex2(T a) { return exp2f(a); }
+    __device__ __forceinline__ static T rcp(T a) { return __fdividef(1.0f, a); }
+    __device__ __forceinline__ static M small(T y) { return fabsf(y) < 0.5f; }
+    __device__ __forceinline__ static T sel(M c, T a, T b) { return c ? a : b; }
+};
+
+// Parameter-derived constants of the neuron right-hand side.
+template <class O> struct HHConst {
+    typename O::T gNa, gK, gL, ENa, EK, EL, gsyn, Esyn, invC, inv_tr, neg_inv_td, neg_sig2, sig2_theta;
+};
+
+template <class O>
+__device__ __forceinline__ HHConst<O> hh_const(const float* p) {
+    HHConst<O> c;
+    c.gNa = O::k(p[1]);
+    c.gK = O::k(p[2]);
+    c.gL = O::k(p[3]);
+    c.ENa = O::k(p[4]);
+    c.EK = O::k(p[5]);
+    c.EL = O::k(p[6]);
+    c.gsyn = O::k(p[7]);
+    c.Esyn = O::k(p[8]);
+    c.invC = O::k(__fdividef(1.0f, p[0]));
+    c.inv_tr = O::k(__fdividef(1.0f, p[12]));
+    c.neg_inv_td = O::k(-__fdividef(1.0f, p[13]));
+    const float sig2 = p[14] * kLog2e;
+    c.neg_sig2 = O::k(-sig2);
+    c.sig2_theta = O::k(sig2 * p[15]);
+    return c;
+}
+
+// Bernoulli series of y / (1 - exp(-y)) = 1 + y/2 + y^2/12 - y^4/720 + y^6/30240
+// (the next term, -y^8/1209600, is below 3.3e-9 for |y| < 0.5).
+template <class O>
+__device__ __forceinline__ typename O::T bernoulli_series_t(typename O::T y) {
+    const auto y2 = O::mul(y, y);
+    const auto even = O::fma(y2, O::fma(y2, O::fma(y2, O::k(1.0f / 30240.0f), O::k(-1.0f / 720.0f)),
+                                        O::k(1.0f / 12.0f)), O::k(1.0f));
+    return O::fma(O::k(0.5f), y, even);
+}
+__device__ __forceinline__ float bernoulli_series(float y) { return bernoulli_series_t<HHScalar>(y); }
+
+// Derivatives of one neuron: V, m, h, n, s its state, `others` the sum of the
+// other neurons' s, `drive` its injected current.
+template <class O>
+__device__ __forceinline__ void hh_neuron(typename O::T V, typename O::T m, typename O::T h, typename O::T n,
+                                          typename O::T s, typename O::T others, typename O::T drive,
+                                          const HHConst<O>& c, typename O::T (&d)[5]) {
+    using T = typename O::T;
+    constexpr float kE25 = 12.182493960703473f;  // e^2.5
+    constexpr float kE1 = 2.718281828459045f;    // e^1
+    constexpr float kE3 = 20.085536923187668f;   // e^3
+    // q = e^(-(V+65)/80) = 2^(kQ V + kQ0); beta_m = 4 e^(-(V+65)/18) = 2^(kB V + kB0)
+    constexpr float kQ = -kLog2e / 80.0f, kQ0 = 65.0f * (-kLog2e / 80.0f);
+    constexpr float kB = -kLog2e / 18.0f, kB0 = 65.0f * (-kLog2e / 18.0f) + 2.0f;
+    const T one = O::k(1.0f);
+    const T q = O::ex2(O::fma(V, O::k(kQ), O::k(kQ0)));
+    const T q2 = O::mul(q, q), q4 = O::mul(q2, q2), q8 = O::mul(q4, q4);
+    const T bm = O::ex2(O::fma(V, O::k(kB), O::k(kB0)));
+    const T ah = O::mul(O::k(0.07f), q4);
+    const T bn = O::mul(O::k(0.125f), q);
+    const T es = O::ex2(O::fma(c.neg_sig2, V, c.sig2_theta));  // e^(sig (theta - V))
+    // alpha_m = g(ym), alpha_n = g(yn) / 10 with g(y) = y / (1 - e^-y),
+    // ym = (V + 40) / 10, yn = (V + 55) / 10, e^-ym = e^2.5 q^8, e^-yn = e q^8
+    const T ym = O::fma(V, O::k(0.1f), O::k(4.0f)), yn = O::fma(V, O::k(0.1f), O::k(5.5f));
+    const auto sm = O::small(ym), sn = O::small(yn);  // series there
+    const T dm = O::sel(sm, one, O::fma(O::k(-kE25), q8, one));
+    const T dn = O::sel(sn, one, O::fma(O::k(-kE1), q8, one));
+    const T rmn = O::rcp(O::mul(dm, dn));
+    const T am = O::sel(sm, bernoulli_series_t<O>(ym), O::mul(O::mul(ym, dn), rmn));
+    const T an = O::mul(O::k(0.1f), O::sel(sn, bernoulli_series_t<O>(yn), O::mul(O::mul(yn, dm), rmn)));
+    // beta_h = 1 / (1 + e^3 q^8), act = 1 / (1 + es)
+    const T ph = O::fma(O::k(kE3), q8, one), ps = O::add(one, es);
+    const T r = O::rcp(O::mul(ph, ps));
+    const T bh = O::mul(ps, r), act = O::mul(ph, r);
+    const T m3h = O::mul(O::mul(O::mul(m, m), m), h);
+    const T n2 = O::mul(n, n), n4 = O::mul(n2, n2);
+    T I = O::mul(c.gL, O::sub(c.EL, V));
+    I = O::fma(O::mul(c.gNa, m3h), O::sub(c.ENa, V), I);
+    I = O::fma(O::mul(c.gK, n4), O::sub(c.EK, V), I);
+    I = O::fma(O::mul(c.gsyn, others), O::sub(c.Esyn, V), I);
+    I = O::add(I, drive);
+    d[0] = O::mul(I, c.invC);
+    // gates: a (1 - y) - b y = a - (a + b) y
+    d[1] = O::sub(am, O::mul(O::add(am, bm), m));
+    d[2] = O::sub(ah, O::mul(O::add(ah, bh), h));
+    d[3] = O::sub(an, O::mul(O::add(an, bn), n));
+    d[4] = O::fma(O::mul(act, c.inv_tr), O::sub(one, s), O::mul(s, c.neg_inv_td));
+}
+
 struct HH3 {
     static constexpr int DIM = 15;
     static constexpr int NP = 16;
     static constexpr int MAX_BLOCK = 256;  // 15-dimensional state, stages and rates in registers
+    static constexpr int MIN_BLOCKS = 3;   // resident blocks of MAX_BLOCK threads the register budget aims at
     __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
-        const float C = p[0], gNa = p[1], gK = p[2], gL = p[3];
-        const float ENa = p[4], EK = p[5], EL = p[6], gsyn = p[7], Esyn = p[8];
-        const float inv_tr = __fdividef(1.0f, p[12]), inv_td = __fdividef(1.0f, p[13]);
-        const float sig2 = p[14] * kLog2e, sig2_theta = sig2 * p[15];
-        const float invC = __fdividef(1.0f, C);
-        const float s_sum = x[4] + x[9] + x[14];
-        constexpr float kE25 = 12.182493960703473f;  // e^2.5
-        constexpr float kE1 = 2.718281828459045f;    // e^1
-        constexpr float kE3 = 20.085536923187668f;   // e^3
-        // q = e^(-(V+65)/80) = 2^(kQ V + kQ0); beta_m = 4 e^(-(V+65)/18) = 2^(kB V + kB0)
-        constexpr float kQ = -kLog2e / 80.0f, kQ0 = 65.0f * (-kLog2e / 80.0f);
-        constexpr float kB = -kLog2e / 18.0f, kB0 = 65.0f * (-kLog2e / 18.0f) + 2.0f;
+        const HHConst<HHScalar> c = hh_const<HHScalar>(p);
+        const float s_sum = __fadd_rn(__fadd_rn(x[4], x[9]), x[14]);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const float V = x[5 * i], m = x[5 * i + 1], h = x[5 * i + 2], n = x[5 * i + 3];
-            const float s = x[5 * i + 4];
-            const float q = exp2f(fmaf(V, kQ, kQ0));
-            const float q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
-            const float bm = exp2f(fmaf(V, kB, kB0));
-            const float ah = 0.07f * q4;
-            const float bn = 0.125f * q;
-            const float es = exp2f(fmaf(-sig2, V, sig2_theta));  // e^(sig (theta - V))
-            // alpha_m = g(ym), alpha_n = g(yn) / 10 with g(y) = y / (1 - e^-y),
-            // ym = (V + 40) / 10, yn = (V + 55) / 10, e^-ym = e^2.5 q^8, e^-yn = e q^8
-            const float ym = fmaf(V, 0.1f, 4.0f), yn = fmaf(V, 0.1f, 5.5f);
-            const bool sm = fabsf(ym) < 0.5f, sn = fabsf(yn) < 0.5f;  // series there
-            const float dm = sm ? 1.0f : fmaf(-kE25, q8, 1.0f), dn = sn ? 1.0f : fmaf(-kE1, q8, 1.0f);
-            const float rmn = __fdividef(1.0f, dm * dn);
-            const float am = sm ? bernoulli_series(ym) : ym * dn * rmn;
-            const float an = 0.1f * (sn ? bernoulli_series(yn) : yn * dm * rmn);
-            // beta_h = 1 / (1 + e^3 q^8), act = 1 / (1 + es)
-            const float ph = fmaf(kE3, q8, 1.0f), ps = 1.0f + es;
-            const float rhs_ = __fdividef(1.0f, ph * ps);
-            const float bh = ps * rhs_;
-            const float act = ph * rhs_;
-            const float m3h = m * m * m * h;
-            const float n2 = n * n;
-            const float n4 = n2 * n2;
-            const float others = s_sum - s;
-            float I = gL * (EL - V);
-            I = fmaf(gNa * m3h, ENa - V, I);
-            I = fmaf(gK * n4, EK - V, I);
-            I = fmaf(gsyn * others, Esyn - V, I);
-            I = I + p[9 + i];
-            dx[5 * i] = I * invC;
-            dx[5 * i + 1] = fmaf(am, 1.0f - m, -bm * m);
-            dx[5 * i + 2] = fmaf(ah, 1.0f - h, -bh * h);
-            dx[5 * i + 3] = fmaf(an, 1.0f - n, -bn * n);
-            dx[5 * i + 4] = fmaf(act * inv_tr, 1.0f - s, -s * inv_td);
+            float d[5];
+            hh_neuron<HHScalar>(x[5 * i], x[5 * i + 1], x[5 * i + 2], x[5 * i + 3], x[5 * i + 4],
+                                __fsub_rn(s_sum, x[5 * i + 4]), p[9 + i], c, d);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) dx[5 * i + k] = d[k];
         }
     }
 };
@@ -561,8 +617,12 @@ __device__ __forceinline__ void integrate_item(const IntegrateArgs& a, int64_t t
     }
 }
 
+// Minimum resident blocks for a system's launch bound: R::MIN_BLOCKS where given, else 1.
+template <class R, class = void> struct MinBlocks { static constexpr int value = 1; };
+template <class R> struct MinBlocks<R, decltype((void)R::MIN_BLOCKS)> { static constexpr int value = R::MIN_BLOCKS; };
+
 template <class R, int METHOD, bool KAHAN, bool PP, int PPT, bool RESET = false>
-__global__ void __launch_bounds__(R::MAX_BLOCK) integrate_kernel(const __grid_constant__ IntegrateArgs a) {
+__global__ void __launch_bounds__(R::MAX_BLOCK, MinBlocks<R>::value) integrate_kernel(const __grid_constant__ IntegrateArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_vec; t += stride)
         integrate_item<R, METHOD, KAHAN, PP, PPT, RESET>(a, t, (int)a.n_steps);
@@ -887,5 +947,113 @@ inline cudaError_t launch_variants(int method, bool kahan, bool pp, const Integr
     if (kahan) return pp ? launch_ppt<R, FF_EULER, true, true>(a, s, st) : launch_ppt<R, FF_EULER, true, false>(a, s, st);
     return pp ? launch_ppt<R, FF_EULER, false, true>(a, s, st) : launch_ppt<R, FF_EULER, false, false>(a, s, st);
 }
+
+// ---------------------------------------------------------------------------
+// Packed-pair RK4 for HH3: neurons 0 and 1 of a particle share f32x2 registers
+// (lane 0 neuron 0, lane 1 neuron 1) and run the neuron right-hand side above
+// with packed add/sub/mul/fma, which halves the issue slots of their FP32
+// arithmetic; neuron 2 runs the scalar form.  The transcendental and compare
+// steps work lane by lane.  Lane by lane the arithmetic is that of HH3::f, so
+// the step equals the generic stepper's bit for bit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+struct HHPair {
+    using T = f2;
+    struct M {
+        bool a, b;
+    };
+    __device__ __forceinline__ static T k(float c) { return pack2(c, c); }
+    __device__ __forceinline__ static T add(T a, T b) { return add2(a, b); }
+    __device__ __forceinline__ static T sub(T a, T b) { return sub2(a, b); }
+    __device__ __forceinline__ static T mul(T a, T b) { return mul2(a, b); }
+    __device__ __forceinline__ static T fma(T a, T b, T c) { return fma2(a, b, c); }
+    __device__ __forceinline__ static T ex2(T v) {
+        float a, b;
+        unpack2(v, a, b);
+        return pack2(exp2f(a), exp2f(b));
+    }
+    __device__ __forceinline__ static T rcp(T v) {
+        float a, b;
+        unpack2(v, a, b);
+        return pack2(__fdividef(1.0f, a), __fdividef(1.0f, b));
+    }
+    __device__ __forceinline__ static M small(T y) {
+        float a, b;
+        unpack2(y, a, b);
+        return M{fabsf(a) < 0.5f, fabsf(b) < 0.5f};
+    }
+    __device__ __forceinline__ static T sel(M c, T x, T y) {
+        float xa, xb, ya, yb;
+        unpack2(x, xa, xb);
+        unpack2(y, ya, yb);
+        return pack2(c.a ? xa : ya, c.b ? xb : yb);
+    }
+};
+
+struct HH3RK4Packed {
+    static constexpr int D = 15;
+    float h1, h2, h6;
+    const float* p;
+    __device__ __forceinline__ void init(float h, const float* prm) {
+        h1 = h;
+        h2 = 0.5f * h;
+        h6 = h * (1.0f / 6.0f);
+        p = prm;
+    }
+    __device__ __forceinline__ void to_internal(float (&)[D]) const {}
+    __device__ __forceinline__ void from_internal(float (&)[D]) const {}
+    __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
+        const HHConst<HHPair> c2 = hh_const<HHPair>(p);
+        const HHConst<HHScalar> c1 = hh_const<HHScalar>(p);
+        const f2 drive01 = pack2(p[9], p[10]);
+        f2 X[5], XS[5], A[5], K[5];
+        float x2[5], xs2[5], a2[5], k2[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            X[k] = pack2(x[k], x[5 + k]);
+            XS[k] = X[k];
+            A[k] = pack2(0.0f, 0.0f);
+            x2[k] = x[10 + k];
+            xs2[k] = x2[k];
+            a2[k] = 0.0f;
+        }
+#pragma unroll 1
+        for (int st = 0; st < 4; ++st) {
+            float s0, s1;
+            unpack2(XS[4], s0, s1);
+            const float s_sum = __fadd_rn(__fadd_rn(s0, s1), xs2[4]);
+            hh_neuron<HHPair>(XS[0], XS[1], XS[2], XS[3], XS[4], sub2(pack2(s_sum, s_sum), XS[4]), drive01, c2, K);
+            hh_neuron<HHScalar>(xs2[0], xs2[1], xs2[2], xs2[3], xs2[4], __fsub_rn(s_sum, xs2[4]), p[11], c1, k2);
+            const float w = (st == 1 || st == 2) ? 2.0f : 1.0f;  // fmaf(1, k, 0) = k
+            const f2 W = pack2(w, w);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                A[k] = fma2(W, K[k], A[k]);
+                a2[k] = fmaf(w, k2[k], a2[k]);
+            }
+            if (st == 3) break;
+            const float cst = (st == 2) ? h1 : h2;
+            const f2 C = pack2(cst, cst);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                XS[k] = fma2(C, K[k], X[k]);
+                xs2[k] = fmaf(cst, k2[k], x2[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            unpack2(A[k], a[k], a[5 + k]);
+            a[10 + k] = a2[k];
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) sc[i] = h6;
+    }
+};
+template <bool KAHAN> struct StepperFor<HH3, FF_RK4, KAHAN> { using type = HH3RK4Packed; };
 
 }  // namespace ff

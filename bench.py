@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--checkpoint-every", type=int, default=100)
     ap.add_argument("--sprites", type=float, default=0.0,
                     help="render soft sprites of this radius (pixels) instead of counts, and time them")
+    ap.add_argument("--sprite-technique", choices=["auto", "direct", "tiled"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -670,7 +671,9 @@ def run_sprites(args, rank, world, local):
     view = ff.make_view(**v)
     groups = len(w["groups"])
     palette = [[1.0, 0.55, 0.15, 1.0], [0.2, 0.45, 1.0, 1.0], [0.3, 1.0, 0.4, 1.0], [1.0, 0.3, 0.8, 1.0]]
-    sprite = ff.make_sprite(args.sprites, 0.05, [palette[g % 4] for g in range(groups)])
+    technique = {"auto": ff.FF_SPRITE_AUTO, "direct": ff.FF_SPRITE_DIRECT, "tiled": ff.FF_SPRITE_TILED}[
+        args.sprite_technique]
+    sprite = ff.make_sprite(args.sprites, 0.05, [palette[g % 4] for g in range(groups)], technique)
     img = torch.zeros((Hd, Wd, 4), dtype=torch.float32, device=dev)
     counts = torch.zeros((Hd, Wd), dtype=torch.int32, device=dev)
     frames = args.frames or w["frames"]
@@ -716,14 +719,15 @@ def run_sprites(args, rank, world, local):
             "unit": "frames/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": med,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["name"], "particles": P, "frames": frames, "steps_per_frame": n,
-                       "sprite_radius": args.sprites, "image": [Hd, Wd, 4], "l2": "256 MB flush between steps"},
+                       "sprite_radius": args.sprites, "sprite_technique": args.sprite_technique,
+                       "image": [Hd, Wd, 4], "l2": "256 MB flush between steps"},
             "particle_steps_per_s": P * n * frames / (med / 1e3),
             "sprite_kernel": {"ms_per_frame": sprite_ms, "drawn_particles": drawn,
                               "fragments_per_frame_est": frags,
                               "fragments_per_s": frags / (sprite_ms / 1e3),
                               "reduction_GBps": 16.0 * frags / (sprite_ms / 1e3) / 1e9,
                               "share_of_frame": sprite_ms * frames / med},
-            "gpu_launches": 2 * frames}
+            "gpu_launches": (2 if args.sprite_technique == "direct" else 5) * frames}
 
 
 def main():

@@ -235,10 +235,21 @@ ff_status ff_step_splat(ff_system* sys, int64_t n_steps, double dt, const ff_vie
  * for a particle of group g; q >= 1 (the square's corners) gains nothing.
  * Colours may have any sign.  Sums are FP32 in an unspecified order. */
 #define FF_SPRITE_MAX_RADIUS 32.0f
+/* How the fragments are summed (the covered pixels and their weights are the
+ * same; only the order of the FP32 additions differs):
+ *   FF_SPRITE_DIRECT  one 16-byte global vector reduction per fragment;
+ *   FF_SPRITE_TILED   particles binned by 32 x 32 pixel tiles, each tile summed
+ *                     in shared memory and added to the image once (needs at
+ *                     most 8192 tiles; FF_ERR_UNSUPPORTED otherwise);
+ *   FF_SPRITE_AUTO    the direct technique, which measured faster on every
+ *                     workload tried (L2 vector reductions outrun shared-memory
+ *                     atomics on the dense tiles of an attractor). */
+enum { FF_SPRITE_AUTO = 0, FF_SPRITE_DIRECT = 1, FF_SPRITE_TILED = 2 };
 typedef struct ff_sprite {
     float radius;                    /* half-side of the square, pixels: 0 < radius <= 32 */
     float gain;                      /* factor on every contribution */
     float colour[FF_MAX_GROUPS][4];  /* channel weights of each group */
+    int technique;                   /* FF_SPRITE_AUTO / DIRECT / TILED */
 } ff_sprite;
 
 /* Draw every selected particle of `view` as a soft sprite into the float image
@@ -247,8 +258,9 @@ typedef struct ff_sprite {
  * device pointer aligned to 16 bytes (image_is_device = 1) or host memory (0;
  * the call then stages the image on the device and synchronises).
  * Errors: those of ff_project_splat; FF_ERR_INVALID_ARG for a NULL sprite, a
- * radius outside (0, 32], non-finite gain or colours, or a device image not
- * aligned to 16 bytes. */
+ * radius outside (0, 32], non-finite gain or colours, an unknown technique, or
+ * a device image not aligned to 16 bytes; FF_ERR_UNSUPPORTED for
+ * FF_SPRITE_TILED on an image of more than 8192 tiles. */
 ff_status ff_project_sprites(ff_system* sys, const ff_view* view, const ff_sprite* sprite, float* image,
                              int image_is_device);
 

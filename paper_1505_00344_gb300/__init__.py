@@ -45,17 +45,22 @@ class ff_view(ctypes.Structure):
                 ("height", ctypes.c_int), ("group_mask", ctypes.c_uint32), ("accumulate", ctypes.c_int)]
 
 
+FF_SPRITE_AUTO, FF_SPRITE_DIRECT, FF_SPRITE_TILED = 0, 1, 2
+
+
 class ff_sprite(ctypes.Structure):
     _fields_ = [("radius", ctypes.c_float), ("gain", ctypes.c_float),
-                ("colour", (ctypes.c_float * 4) * FF_MAX_GROUPS)]
+                ("colour", (ctypes.c_float * 4) * FF_MAX_GROUPS), ("technique", ctypes.c_int)]
 
 
-def make_sprite(radius=1.5, gain=1.0, colours=((1.0, 1.0, 1.0, 1.0),)):
-    """A soft-sprite description: radius in pixels, gain, and up to FF_MAX_GROUPS
-    rows of 4 channel weights (groups beyond the rows given get zeros)."""
+def make_sprite(radius=1.5, gain=1.0, colours=((1.0, 1.0, 1.0, 1.0),), technique=FF_SPRITE_AUTO):
+    """A soft-sprite description: radius in pixels, gain, up to FF_MAX_GROUPS rows of
+    4 channel weights (groups beyond the rows given get zeros) and the summation
+    technique (FF_SPRITE_AUTO / DIRECT / TILED)."""
     sp = ff_sprite()
     sp.radius = float(radius)
     sp.gain = float(gain)
+    sp.technique = int(technique)
     rows = np.asarray(colours, dtype=np.float64).reshape(-1, 4)
     if rows.shape[0] > FF_MAX_GROUPS:
         raise ValueError(f"at most {FF_MAX_GROUPS} colour rows")
@@ -321,6 +326,8 @@ def ff_backward(sys, dL_dxT, dL_dx0, dL_dp=None):
     n_params = ctypes.c_int(0)
     if dL_dp is None:
         dL_dp = np.zeros(FF_MAX_PARAMS, np.float64)
+    if dL_dp.size < FF_MAX_PARAMS:
+        raise ValueError(f"dL_dp needs room for FF_MAX_PARAMS = {FF_MAX_PARAMS} doubles")
     c, _, _kc = _buf(dL_dp, np.float64)
     _check(lib().ff_backward(sys, a, b, c))
     return dL_dp
@@ -491,7 +498,8 @@ class System:
         ff_tape_end(self.handle)
 
     def backward(self, dL_dxT, dL_dx0, n_params):
-        return ff_backward(self.handle, dL_dxT, dL_dx0, np.zeros(max(n_params, 1), np.float64))[:n_params]
+        # the call writes every parameter of the system: hand it room for FF_MAX_PARAMS
+        return ff_backward(self.handle, dL_dxT, dL_dx0)[:n_params]
 
     def set_reset(self, bound_lo=None, bound_hi=None, t_max=0.0, check_every=1):
         ff_set_reset(self.handle, bound_lo, bound_hi, t_max, check_every)

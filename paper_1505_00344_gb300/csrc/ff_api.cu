@@ -152,6 +152,8 @@ ff_status ff_destroy_system(ff_system* s) {
     cudaFree(s->d_pparam);
     cudaFree(s->d_counter);
     cudaFree(s->d_stage);
+    cudaFree(s->d_tiles);
+    cudaFree(s->d_entries);
     cudaFree(s->d_age);
     cudaFree(s->d_resets);
     cudaFree(s->d_reset_table);
@@ -726,6 +728,8 @@ ff_status ff_project_sprites(ff_system* s, const ff_view* v, const ff_sprite* sp
     if (!(sp->radius > 0.0f && sp->radius <= FF_SPRITE_MAX_RADIUS))
         return fail(FF_ERR_INVALID_ARG, "ff_project_sprites: radius %g outside (0, 32]", (double)sp->radius);
     if (!std::isfinite(sp->gain)) return fail(FF_ERR_INVALID_ARG, "ff_project_sprites: non-finite gain");
+    if (sp->technique < FF_SPRITE_AUTO || sp->technique > FF_SPRITE_TILED)
+        return fail(FF_ERR_INVALID_ARG, "ff_project_sprites: technique %d unknown", sp->technique);
     if (image_is_device && (reinterpret_cast<uintptr_t>(image) & 15u) != 0)
         return fail(FF_ERR_INVALID_ARG, "ff_project_sprites: device image not aligned to 16 bytes");
     ff::SpriteArgs a{};
@@ -749,6 +753,16 @@ ff_status ff_project_sprites(ff_system* s, const ff_view* v, const ff_sprite* sp
     a.inv_r2 = (float)(1.0 / ((double)sp->radius * (double)sp->radius));
     const uint32_t all = (s->n_groups >= 32) ? 0xffffffffu : ((1u << s->n_groups) - 1u);
     const bool masked = a.v.mask != all;
+    // tiled where it applies: the per-tile histograms fit, the tile lists index in 32 bits
+    // (decided before any device work, so a rejected call leaves the image untouched)
+    const int n_tiles = ff::sprite_tiles(v->width, v->height);
+    const int64_t entries = ff::sprite_entries_bound(s->n_particles, sp->radius);
+    const bool tiles_fit = n_tiles <= ff::kSpriteMaxTiles && entries < ((int64_t)1 << 31);
+    if (sp->technique == FF_SPRITE_TILED && !tiles_fit)
+        return fail(FF_ERR_UNSUPPORTED, "ff_project_sprites: %d tiles, more than the tiled technique takes", n_tiles);
+    // AUTO takes the direct technique: measured faster on every workload tried (the L2's
+    // vector reductions outrun shared-memory atomics on the dense tiles of an attractor)
+    const bool tiled = sp->technique == FF_SPRITE_TILED;
 
     DeviceScope dev(s->device);
     if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_project_sprites: set device");
@@ -770,8 +784,28 @@ ff_status ff_project_sprites(ff_system* s, const ff_view* v, const ff_sprite* sp
     if (e == cudaSuccess && !v->accumulate) e = cudaMemsetAsync(target, 0, bytes, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "ff_project_sprites: image clear/upload");
     a.image = reinterpret_cast<float4*>(target);
+    if (tiled) {
+        const size_t need_tiles = 4 * (size_t)n_tiles + 2;
+        if (s->tiles_cap < need_tiles) {
+            cudaFree(s->d_tiles);
+            s->d_tiles = nullptr;
+            s->tiles_cap = 0;
+            e = cudaMalloc(&s->d_tiles, sizeof(uint32_t) * need_tiles);
+            if (e != cudaSuccess) return cuda_fail(e, "ff_project_sprites: tile table");
+            s->tiles_cap = need_tiles;
+        }
+        if (s->entries_cap < (size_t)entries) {
+            cudaFree(s->d_entries);
+            s->d_entries = nullptr;
+            s->entries_cap = 0;
+            e = cudaMalloc(&s->d_entries, sizeof(uint32_t) * (size_t)entries);
+            if (e != cudaSuccess) return cuda_fail(e, "ff_project_sprites: tile lists");
+            s->entries_cap = (size_t)entries;
+        }
+    }
     if (s->n_particles > 0 && a.v.mask != 0) {
-        e = ff::launch_sprites(a, v->ndim_view, masked, s->num_sms, s->stream);
+        e = tiled ? ff::launch_sprites_tiled(a, v->ndim_view, masked, s->d_tiles, s->d_entries, s->num_sms, s->stream)
+                  : ff::launch_sprites(a, v->ndim_view, masked, s->num_sms, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sprite kernel launch");
     }
     if (!image_is_device) {

@@ -294,6 +294,229 @@ cudaError_t launch_sprites(const SpriteArgs& a, int ndim_view, bool masked, int 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Tiled sprites.  The same centre, bounding box and coverage arithmetic as
+// sprite_kernel, so the covered pixels and their weights are the same; only
+// the order of the FP32 sums differs.
+// ---------------------------------------------------------------------------
+int sprite_tiles(int W, int H) {
+    return ((W + kSpriteTile - 1) / kSpriteTile) * ((H + kSpriteTile - 1) / kSpriteTile);
+}
+
+int64_t sprite_entries_bound(int64_t n, float radius) {
+    // a bounding box spans at most 2R + 3 pixels, so at most ceil((2R + 3) / T) + 1 tiles per axis
+    const int per_axis = (int)ceilf((2.0f * radius + 3.0f) / kSpriteTile) + 1;
+    return n * per_axis * per_axis;
+}
+
+// Centre, group and the clipped pixel bounding box of particle i; false if it draws nothing.
+template <int NDV, bool MASKED>
+__device__ __forceinline__ bool sprite_box(const SpriteArgs& a, int64_t i, float& pc, float& pr, int& g, int& c0,
+                                           int& c1, int& r0, int& r1) {
+    g = 0;
+#pragma unroll
+    for (int q = 1; q < FF_MAX_GROUPS; ++q)
+        if (q < a.n_groups && i >= a.gstart[q]) g = q;
+    if (MASKED && !((a.v.mask >> g) & 1u)) return false;
+    const float w = NDV == 3 ? a.ax[2][i] : 0.0f;
+    if (!sprite_centre<NDV>(a.v, a.ax[0][i], a.ax[1][i], w, pc, pr)) return false;
+    const float R = a.R;
+    if (!(pc > -R - 1.0f && pc < a.v.Wf + R + 1.0f && pr > -R - 1.0f && pr < a.v.Hf + R + 1.0f)) return false;
+    c0 = max(0, (int)floorf(pc - R));
+    c1 = min(a.v.W - 1, (int)ceilf(pc + R));
+    r0 = max(0, (int)floorf(pr - R));
+    r1 = min(a.v.H - 1, (int)ceilf(pr + R));
+    return c0 <= c1 && r0 <= r1;
+}
+
+// Pass 1: per-tile particle counts (block histograms in shared memory).
+template <int NDV, bool MASKED>
+__global__ void __launch_bounds__(kSplatBlock) sprite_count_kernel(const __grid_constant__ SpriteArgs a,
+                                                                     uint32_t* count, int tiles_x, int n_tiles) {
+    __shared__ uint32_t hist[kSpriteMaxTiles];
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        float pc, pr;
+        int g, c0, c1, r0, r1;
+        if (!sprite_box<NDV, MASKED>(a, i, pc, pr, g, c0, c1, r0, r1)) continue;
+        for (int ty = r0 / kSpriteTile; ty <= r1 / kSpriteTile; ++ty)
+            for (int tx = c0 / kSpriteTile; tx <= c1 / kSpriteTile; ++tx) atomicAdd(&hist[ty * tiles_x + tx], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
+        if (hist[t]) atomicAdd(&count[t], hist[t]);
+}
+
+// Pass 2 (one block): offsets = exclusive prefix sum of the counts, cursors =
+// offsets, and chunk offsets = exclusive prefix sum of ceil(count / chunk): a
+// tile's list is rendered in chunks of kSpriteChunk entries by any block.
+constexpr uint32_t kSpriteChunk = 512;
+__global__ void __launch_bounds__(1024) sprite_scan_kernel(const uint32_t* count, uint32_t* offset, uint32_t* cursor,
+                                                           uint32_t* chunk_off, int n_tiles) {
+    __shared__ uint32_t part[1024], cpart[1024];
+    const int per = (n_tiles + blockDim.x - 1) / blockDim.x;
+    const int t0 = threadIdx.x * per;
+    uint32_t sum = 0, csum = 0;
+    for (int t = t0; t < t0 + per && t < n_tiles; ++t) {
+        sum += count[t];
+        csum += (count[t] + kSpriteChunk - 1) / kSpriteChunk;
+    }
+    part[threadIdx.x] = sum;
+    cpart[threadIdx.x] = csum;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // inclusive scans of the thread sums
+        const uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+        const uint32_t cv = threadIdx.x >= (unsigned)off ? cpart[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        cpart[threadIdx.x] += cv;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - sum, crun = cpart[threadIdx.x] - csum;
+    for (int t = t0; t < t0 + per && t < n_tiles; ++t) {
+        offset[t] = run;
+        cursor[t] = run;
+        chunk_off[t] = crun;
+        run += count[t];
+        crun += (count[t] + kSpriteChunk - 1) / kSpriteChunk;
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        offset[n_tiles] = part[threadIdx.x];
+        chunk_off[n_tiles] = cpart[threadIdx.x];
+    }
+}
+
+// Pass 3: the tile lists.  Each block counts its particles per tile again,
+// reserves one range per touched tile, then writes each particle's index into
+// its ranges.
+template <int NDV, bool MASKED>
+__global__ void __launch_bounds__(kSplatBlock) sprite_fill_kernel(const __grid_constant__ SpriteArgs a,
+                                                                    uint32_t* cursor, uint32_t* entries,
+                                                                    int tiles_x, int n_tiles, uint32_t cap) {
+    __shared__ uint32_t slot[kSpriteMaxTiles];
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) slot[t] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        float pc, pr;
+        int g, c0, c1, r0, r1;
+        if (!sprite_box<NDV, MASKED>(a, i, pc, pr, g, c0, c1, r0, r1)) continue;
+        for (int ty = r0 / kSpriteTile; ty <= r1 / kSpriteTile; ++ty)
+            for (int tx = c0 / kSpriteTile; tx <= c1 / kSpriteTile; ++tx) atomicAdd(&slot[ty * tiles_x + tx], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
+        if (slot[t]) slot[t] = atomicAdd(&cursor[t], slot[t]);  // the block's range starts here
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        float pc, pr;
+        int g, c0, c1, r0, r1;
+        if (!sprite_box<NDV, MASKED>(a, i, pc, pr, g, c0, c1, r0, r1)) continue;
+        for (int ty = r0 / kSpriteTile; ty <= r1 / kSpriteTile; ++ty)
+            for (int tx = c0 / kSpriteTile; tx <= c1 / kSpriteTile; ++tx) {
+                const uint32_t at = atomicAdd(&slot[ty * tiles_x + tx], 1u);
+                if (at < cap) entries[at] = (uint32_t)i;
+            }
+    }
+}
+
+// Pass 4: blocks take chunks of the tile lists round-robin; a chunk's fragments
+// accumulate in a shared-memory copy of its tile, which is then added to the
+// image with one 16-byte vector reduction per touched pixel (chunks of one tile
+// may run at the same time).
+template <int NDV, bool MASKED>
+__global__ void __launch_bounds__(kSplatBlock) sprite_tile_kernel(const __grid_constant__ SpriteArgs a,
+                                                                    const uint32_t* offset, const uint32_t* chunk_off,
+                                                                    const uint32_t* entries, int tiles_x, int n_tiles) {
+    __shared__ float4 acc[kSpriteTile * kSpriteTile];
+    const uint32_t total = chunk_off[n_tiles];
+    for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
+        // the tile of chunk c: the last t with chunk_off[t] <= c
+        int lo = 0, hi = n_tiles - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (chunk_off[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const int tile = lo;
+        const uint32_t e0 = offset[tile] + (c - chunk_off[tile]) * kSpriteChunk;
+        const uint32_t e1 = min(e0 + kSpriteChunk, offset[tile + 1]);
+        const int tx0 = (tile % tiles_x) * kSpriteTile, ty0 = (tile / tiles_x) * kSpriteTile;
+        for (int p = threadIdx.x; p < kSpriteTile * kSpriteTile; p += blockDim.x) acc[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        float* accf = reinterpret_cast<float*>(acc);
+        for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int64_t i = entries[e];
+            float pc, pr;
+            int g, c0, c1, r0, r1;
+            if (i >= a.n || !sprite_box<NDV, MASKED>(a, i, pc, pr, g, c0, c1, r0, r1)) continue;
+            c0 = max(c0, tx0);
+            c1 = min(c1, tx0 + kSpriteTile - 1);
+            r0 = max(r0, ty0);
+            r1 = min(r1, ty0 + kSpriteTile - 1);
+            const float4 col = a.colour[g];
+            for (int row = r0; row <= r1; ++row) {
+                const float dy = __fsub_rn(__fadd_rn((float)row, 0.5f), pr);
+                const float dy2 = __fmul_rn(dy, dy);
+                for (int x = c0; x <= c1; ++x) {
+                    const float dx = __fsub_rn(__fadd_rn((float)x, 0.5f), pc);
+                    const float q = __fmul_rn(__fadd_rn(__fmul_rn(dx, dx), dy2), a.inv_r2);
+                    if (q < 1.0f) {
+                        const float om = 1.0f - q;
+                        const float wgt = om * om;
+                        float* px = accf + 4 * ((row - ty0) * kSpriteTile + (x - tx0));
+                        atomicAdd(px + 0, wgt * col.x);
+                        atomicAdd(px + 1, wgt * col.y);
+                        atomicAdd(px + 2, wgt * col.z);
+                        atomicAdd(px + 3, wgt * col.w);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < kSpriteTile * kSpriteTile; p += blockDim.x) {
+            const int row = ty0 + p / kSpriteTile, x = tx0 + p % kSpriteTile;
+            const float4 t = acc[p];
+            if (row < a.v.H && x < a.v.W && (t.x != 0.f || t.y != 0.f || t.z != 0.f || t.w != 0.f))
+                red_add_v4(a.image + (int64_t)row * a.v.W + x, t.x, t.y, t.z, t.w);
+        }
+        __syncthreads();
+    }
+}
+
+template <int NDV, bool MASKED>
+static cudaError_t tiled_passes(const SpriteArgs& a, uint32_t* tiles, uint32_t* entries, int num_sms,
+                                cudaStream_t s) {
+    const int tiles_x = (a.v.W + kSpriteTile - 1) / kSpriteTile;
+    const int n_tiles = sprite_tiles(a.v.W, a.v.H);
+    uint32_t* count = tiles;
+    uint32_t* offset = tiles + n_tiles;             // n_tiles + 1 values
+    uint32_t* cursor = tiles + 2 * n_tiles + 1;
+    uint32_t* chunk_off = tiles + 3 * n_tiles + 1;  // n_tiles + 1 values
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint32_t) * n_tiles, s);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for(a.n, kSplatBlock, num_sms, 4);
+    sprite_count_kernel<NDV, MASKED><<<grid, kSplatBlock, 0, s>>>(a, count, tiles_x, n_tiles);
+    sprite_scan_kernel<<<1, 1024, 0, s>>>(count, offset, cursor, chunk_off, n_tiles);
+    const uint32_t cap = (uint32_t)sprite_entries_bound(a.n, a.R);
+    sprite_fill_kernel<NDV, MASKED><<<grid, kSplatBlock, 0, s>>>(a, cursor, entries, tiles_x, n_tiles, cap);
+    sprite_tile_kernel<NDV, MASKED><<<num_sms * 8, kSplatBlock, 0, s>>>(a, offset, chunk_off, entries, tiles_x,
+                                                                           n_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sprites_tiled(const SpriteArgs& a, int ndim_view, bool masked, uint32_t* tiles,
+                                 uint32_t* entries, int num_sms, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    if (ndim_view == 2)
+        return masked ? tiled_passes<2, true>(a, tiles, entries, num_sms, s)
+                      : tiled_passes<2, false>(a, tiles, entries, num_sms, s);
+    return masked ? tiled_passes<3, true>(a, tiles, entries, num_sms, s)
+                  : tiled_passes<3, false>(a, tiles, entries, num_sms, s);
+}
+
 cudaError_t launch_escape_count(const float* x, int64_t pitch, int dim, int64_t n,
                                 unsigned long long* counter, int num_sms, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);

@@ -49,6 +49,18 @@ struct SpriteArgs {
 
 cudaError_t launch_seed(const SeedArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_sprites(const SpriteArgs& a, int ndim_view, bool masked, int num_sms, cudaStream_t s);
+
+// Tiled sprites: particles are binned by the 32 x 32 pixel tiles their sprites
+// touch, then blocks take chunks of the tile lists, accumulate each in shared memory and add
+// it to the image.  Scratch: `tiles` holds 4 * n_tiles + 2 uint32 (counts,
+// offsets, cursors, chunk offsets), `entries` the tile lists (sprite_entries_bound
+// entries).
+constexpr int kSpriteTile = 32;
+constexpr int kSpriteMaxTiles = 8192;  // the shared-memory histograms' size
+int sprite_tiles(int W, int H);          // tiles covering a W x H image
+int64_t sprite_entries_bound(int64_t n, float radius);
+cudaError_t launch_sprites_tiled(const SpriteArgs& a, int ndim_view, bool masked, uint32_t* tiles,
+                                 uint32_t* entries, int num_sms, cudaStream_t s);
 cudaError_t launch_linspace(float* out, int64_t P, double lo, double hi, int num_sms,
                             cudaStream_t s);
 // strip: consecutive particles map to a narrow strip of the image (a linspace

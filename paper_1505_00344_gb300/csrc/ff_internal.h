@@ -72,6 +72,11 @@ struct ff_system {
     unsigned long long* d_counter = nullptr;
     uint32_t* d_stage = nullptr;  // device copy of a host image
     size_t stage_bytes = 0;
+    // tiled sprite rendering: per-tile counts / offsets / cursors and the tile lists
+    uint32_t* d_tiles = nullptr;
+    size_t tiles_cap = 0;  // uint32 entries
+    uint32_t* d_entries = nullptr;
+    size_t entries_cap = 0;
     // launch shape
     int ppt = 1, block = 256, blocks_per_sm = 0;
     int64_t max_steps = 0;

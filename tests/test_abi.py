@@ -62,13 +62,14 @@ def test_view_struct_layout_matches_c(tmp_path):
 def test_sprite_struct_layout_matches_c(tmp_path):
     src = tmp_path / "sprite.c"
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "ff.h"\nint main(void){\n'
-                   'printf("%zu %zu %zu %zu\\n", sizeof(ff_sprite), offsetof(ff_sprite, radius),'
-                   ' offsetof(ff_sprite, gain), offsetof(ff_sprite, colour));return 0;}\n')
+                   'printf("%zu %zu %zu %zu %zu\\n", sizeof(ff_sprite), offsetof(ff_sprite, radius),'
+                   ' offsetof(ff_sprite, gain), offsetof(ff_sprite, colour), offsetof(ff_sprite, technique));'
+                   'return 0;}\n')
     exe = tmp_path / "sprite"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     c_vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     S = ff.ff_sprite
-    assert c_vals == [ctypes.sizeof(S), S.radius.offset, S.gain.offset, S.colour.offset]
+    assert c_vals == [ctypes.sizeof(S), S.radius.offset, S.gain.offset, S.colour.offset, S.technique.offset]
 
 
 def _status(fn, *args):

@@ -69,15 +69,19 @@ def check(got, want, absum, frags, prefill=None):
     np.testing.assert_array_equal(got[untouched], base[untouched])
 
 
+TECHNIQUES = [ff.FF_SPRITE_DIRECT, ff.FF_SPRITE_TILED]
+
+
+@pytest.mark.parametrize("technique", TECHNIQUES)
 @pytest.mark.parametrize("radius", [0.75, 1.5, 4.0, 32.0])
-def test_2d_sprites_match_oracle(radius):
+def test_2d_sprites_match_oracle(radius, technique):
     counts = [2003, 1500, 1500]  # ragged: 5003 particles
     s = lorenz_system(counts)
     s.step(150, 0.001)
     W, H = 160, 96
     lo, hi = (-25.0, 2.0), (25.0, 55.0)  # particles spill over every edge of the window
     view = dict(ndim_view=2, axes=(0, 2), lo=lo, hi=hi, width=W, height=H)
-    sprite = ff.make_sprite(radius, 0.8, COLOURS)
+    sprite = ff.make_sprite(radius, 0.8, COLOURS, technique)
     got = gpu_sprites(s, view, sprite, W, H)
     x = state_of(s)
     want, absum, frags = oracle.sprites2d(x[0], x[2], lo, hi, W, H, radius, 0.8, COLOURS, group=groups_of(counts))
@@ -85,7 +89,8 @@ def test_2d_sprites_match_oracle(radius):
     check(got, want, absum, frags)
 
 
-def test_3d_perspective_masked_and_accumulated():
+@pytest.mark.parametrize("technique", TECHNIQUES)
+def test_3d_perspective_masked_and_accumulated(technique):
     counts = [1000, 777, 1201]
     s = lorenz_system(counts)
     s.step(300, 0.001)
@@ -95,7 +100,7 @@ def test_3d_perspective_masked_and_accumulated():
     view = dict(ndim_view=3, axes=(0, 1, 2), mvp=mvp, width=W, height=H, group_mask=0b101, accumulate=1)
     rng = np.random.default_rng(4)
     prefill = rng.uniform(-1, 1, (H, W, 4)).astype(np.float32)
-    sprite = ff.make_sprite(2.5, 1.3, COLOURS)
+    sprite = ff.make_sprite(2.5, 1.3, COLOURS, technique)
     got = gpu_sprites(s, view, sprite, W, H, prefill=prefill)
     x = state_of(s)
     g = groups_of(counts)
@@ -105,7 +110,8 @@ def test_3d_perspective_masked_and_accumulated():
     check(got, want, absum, frags, prefill=prefill)
 
 
-def test_host_image_and_parameter_axis():
+@pytest.mark.parametrize("technique", TECHNIQUES)
+def test_host_image_and_parameter_axis(technique):
     # bifurcation view: per-particle r on the x axis, z on y; host image, cleared by the call
     s = ff.System("lorenz", LORENZ_PARAMS, 4099, stream=stream())
     s.seed(4099, [-20, -20, 0], [20, 20, 40], 1, 21)
@@ -114,7 +120,7 @@ def test_host_image_and_parameter_axis():
     W, H = 200, 100
     view = dict(ndim_view=2, axes=(3, 2), lo=(0.0, 0.0), hi=(50.0, 80.0), width=W, height=H)
     img = np.full((H, W, 4), 7.0, np.float32)  # stale content: accumulate = 0 clears it
-    s.project_sprites(view, ff.make_sprite(1.25, 1.0, COLOURS), img)
+    s.project_sprites(view, ff.make_sprite(1.25, 1.0, COLOURS, technique), img)
     x = state_of(s)
     r = np.empty(4099, np.float32)
     s.get_particle_param(r)
@@ -122,7 +128,8 @@ def test_host_image_and_parameter_axis():
     check(img.astype(np.float64), want, absum, frags)
 
 
-def test_full_size_lorenz_frame():
+@pytest.mark.parametrize("technique", TECHNIQUES + [ff.FF_SPRITE_AUTO])
+def test_full_size_lorenz_frame(technique):
     # the lorenz_4M workload (4,194,304 particles, 75% forward / 25% backward) after 2 frames,
     # x-z view into 1920 x 1080, forward and backward groups in different colours
     w = workload("lorenz_4M")
@@ -134,7 +141,7 @@ def test_full_size_lorenz_frame():
     W, H = v["width"], v["height"]
     view = dict(ndim_view=2, axes=tuple(v["axes"]), lo=tuple(v["lo"]), hi=tuple(v["hi"]), width=W, height=H)
     cols = [[1.0, 0.6, 0.2, 1.0], [0.2, 0.4, 1.0, 1.0]]
-    got = gpu_sprites(s, view, ff.make_sprite(1.5, 0.05, cols), W, H)
+    got = gpu_sprites(s, view, ff.make_sprite(1.5, 0.05, cols, technique), W, H)
     x = state_of(s)
     counts = [g["count"] for g in w["groups"]]
     ax = v["axes"]
@@ -144,16 +151,17 @@ def test_full_size_lorenz_frame():
     check(got, want, absum, frags)
 
 
-def test_empty_and_masked_out():
+@pytest.mark.parametrize("technique", TECHNIQUES)
+def test_empty_and_masked_out(technique):
     s = ff.System("lorenz", LORENZ_PARAMS, 64, stream=stream())
     W, H = 32, 16
     view = dict(ndim_view=2, axes=(0, 2), lo=(-30.0, 0.0), hi=(30.0, 60.0), width=W, height=H)
     img = torch.full((H, W, 4), 3.0, device="cuda")
-    s.project_sprites(view, ff.make_sprite(2.0), img)  # no particles yet: the image is only cleared
+    s.project_sprites(view, ff.make_sprite(2.0, technique=technique), img)  # no particles: only cleared
     assert float(img.abs().max()) == 0.0
     s.seed(64, [-30, -30, 0], [30, 30, 60], 1, 1)
     img.fill_(3.0)
-    s.project_sprites(dict(view, group_mask=0), ff.make_sprite(2.0), img)
+    s.project_sprites(dict(view, group_mask=0), ff.make_sprite(2.0, technique=technique), img)
     assert float(img.abs().max()) == 0.0
 
 
@@ -170,3 +178,10 @@ def test_argument_errors():
     with pytest.raises(ff.FFError) as e:  # device image not 16-byte aligned: rejected on the host
         s.project_sprites(view, ff.make_sprite(1.0), img.data_ptr() + 4)
     assert e.value.status == ff.FF_ERR_INVALID_ARG
+    with pytest.raises(ff.FFError) as e:
+        s.project_sprites(view, ff.make_sprite(1.0, technique=3), img)
+    assert e.value.status == ff.FF_ERR_INVALID_ARG
+    big = dict(view, width=4096, height=4096)  # 16,384 tiles: more than the tiled technique takes
+    with pytest.raises(ff.FFError) as e:
+        s.project_sprites(big, ff.make_sprite(1.0, technique=ff.FF_SPRITE_TILED), torch.zeros(4, device="cuda"))
+    assert e.value.status == ff.FF_ERR_UNSUPPORTED

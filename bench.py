@@ -313,8 +313,11 @@ def run_ours(args, rank, world, local):
         packed = (args.ppt or 4) in (2, 4) and not (args.kahan or args.reset)
         kernel = ("lorenz_rk4_x2u_kernel<splat>" if fused and every else
                   "lorenz_rk4_x2u_kernel" if packed else "integrate_kernel<Lorenz,RK4>")
-        # DRAM bytes come from the committed ncu summary of the packed kernel on the same sources
-        traffic = traffic_from_profile(kernel_source_hash()) if packed and not args.particles else None
+        # DRAM bytes come from the committed ncu record, which is of the fused kernel on the full
+        # lorenz_4M frame: only that workload and variant, on the same sources, gets it
+        recorded = (w["name"] == "lorenz_4M" and fused and every and packed and not args.particles
+                    and not args.frame_steps)
+        traffic = traffic_from_profile(kernel_source_hash()) if recorded else None
         roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / peak_tflops, 4), "traffic": traffic, "kernel": kernel,
                 "peak_basis": f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
@@ -343,8 +346,10 @@ def run_ours(args, rank, world, local):
     }
     if roof:
         result["roofline"] = roof
-    if clk:
-        result["clocks"] = clk
+    # a timed region shorter than the sampling interval has no clock samples: say so
+    result["clocks"] = clk or {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": [],
+                               "note": "not sampled (--no-clocks)" if args.no_clocks else
+                               "timed region shorter than the 200 ms sampling interval"}
 
     if not args.no_e2e:
         result["e2e"] = e2e_ours(args, sysobj, w, view, image, P, world, dev)

@@ -632,6 +632,40 @@ ff_status ff_backward(ff_system* s, const float* dL_dxT_dev, float* dL_dx0_dev, 
     return FF_OK;
 }
 
+// The device image a render call draws into: the caller's device image, or the
+// system's staging buffer holding (when accumulating) a copy of the caller's host
+// image; cleared first unless accumulating.
+static ff_status image_begin(ff_system* s, void* image, int image_is_device, size_t bytes, int accumulate,
+                             void** target, const char* who) {
+    cudaError_t e = cudaSuccess;
+    *target = image;
+    if (!image_is_device) {
+        if (s->stage_bytes < bytes) {
+            cudaFree(s->d_stage);
+            s->d_stage = nullptr;
+            s->stage_bytes = 0;
+            e = cudaMalloc(&s->d_stage, bytes);
+            if (e != cudaSuccess) return cuda_fail(e, who);
+            s->stage_bytes = bytes;
+        }
+        *target = s->d_stage;
+        if (accumulate) e = cudaMemcpyAsync(*target, image, bytes, cudaMemcpyHostToDevice, s->stream);
+    }
+    if (e == cudaSuccess && !accumulate) e = cudaMemsetAsync(*target, 0, bytes, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return FF_OK;
+}
+
+// After the render kernels: a host image is copied back (and the call synchronises).
+static ff_status image_end(ff_system* s, void* image, int image_is_device, size_t bytes, void* target,
+                           const char* who) {
+    if (image_is_device) return FF_OK;
+    cudaError_t e = cudaMemcpyAsync(image, target, bytes, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return FF_OK;
+}
+
 // Checked view -> kernel view arguments (axes, window or camera, image size, group mask).
 static ff_status view_args(const ff_system* s, const ff_view* v, ff::ViewArgs* out) {
     ff::ViewArgs a{};
@@ -690,35 +724,18 @@ ff_status ff_project_splat(ff_system* s, const ff_view* v, uint32_t* image, int 
     DeviceScope dev(s->device);
     if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_project_splat: set device");
     const size_t bytes = sizeof(uint32_t) * (size_t)v->width * v->height;
-    uint32_t* target = image;
+    void* target = nullptr;
+    ff_status st = image_begin(s, image, image_is_device, bytes, v->accumulate, &target, "ff_project_splat");
+    if (st != FF_OK) return st;
     cudaError_t e = cudaSuccess;
-    if (!image_is_device) {
-        if (s->stage_bytes < bytes) {
-            cudaFree(s->d_stage);
-            s->d_stage = nullptr;
-            s->stage_bytes = 0;
-            e = cudaMalloc(&s->d_stage, bytes);
-            if (e != cudaSuccess) return cuda_fail(e, "ff_project_splat: staging image");
-            s->stage_bytes = bytes;
-        }
-        target = s->d_stage;
-        if (v->accumulate) e = cudaMemcpyAsync(target, image, bytes, cudaMemcpyHostToDevice, s->stream);
-    }
-    if (e == cudaSuccess && !v->accumulate) e = cudaMemsetAsync(target, 0, bytes, s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "ff_project_splat: image clear/upload");
-    a.v.image = target;
+    a.v.image = static_cast<uint32_t*>(target);
     bool strip = false;  // a linspace parameter on an axis: consecutive particles share a column or row
     for (int q = 0; q < v->ndim_view; ++q) strip = strip || (v->axes[q] == s->dim && s->pparam_linspace);
     if (s->n_particles > 0 && a.v.mask != 0) {
         e = ff::launch_splat(a, v->ndim_view, masked, strip, s->num_sms, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "splat kernel launch");
     }
-    if (!image_is_device) {
-        e = cudaMemcpyAsync(image, target, bytes, cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "ff_project_splat: image download");
-    }
-    return FF_OK;
+    return image_end(s, image, image_is_device, bytes, target, "ff_project_splat");
 }
 
 ff_status ff_project_sprites(ff_system* s, const ff_view* v, const ff_sprite* sp, float* image,
@@ -767,23 +784,11 @@ ff_status ff_project_sprites(ff_system* s, const ff_view* v, const ff_sprite* sp
     DeviceScope dev(s->device);
     if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_project_sprites: set device");
     const size_t bytes = sizeof(float) * 4 * (size_t)v->width * v->height;
-    float* target = image;
+    void* target = nullptr;
+    ff_status ist = image_begin(s, image, image_is_device, bytes, v->accumulate, &target, "ff_project_sprites");
+    if (ist != FF_OK) return ist;
     cudaError_t e = cudaSuccess;
-    if (!image_is_device) {
-        if (s->stage_bytes < bytes) {
-            cudaFree(s->d_stage);
-            s->d_stage = nullptr;
-            s->stage_bytes = 0;
-            e = cudaMalloc(&s->d_stage, bytes);
-            if (e != cudaSuccess) return cuda_fail(e, "ff_project_sprites: staging image");
-            s->stage_bytes = bytes;
-        }
-        target = reinterpret_cast<float*>(s->d_stage);
-        if (v->accumulate) e = cudaMemcpyAsync(target, image, bytes, cudaMemcpyHostToDevice, s->stream);
-    }
-    if (e == cudaSuccess && !v->accumulate) e = cudaMemsetAsync(target, 0, bytes, s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "ff_project_sprites: image clear/upload");
-    a.image = reinterpret_cast<float4*>(target);
+    a.image = static_cast<float4*>(target);
     if (tiled) {
         const size_t need_tiles = 4 * (size_t)n_tiles + 2;
         if (s->tiles_cap < need_tiles) {
@@ -808,12 +813,7 @@ ff_status ff_project_sprites(ff_system* s, const ff_view* v, const ff_sprite* sp
                   : ff::launch_sprites(a, v->ndim_view, masked, s->num_sms, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "sprite kernel launch");
     }
-    if (!image_is_device) {
-        e = cudaMemcpyAsync(image, target, bytes, cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "ff_project_sprites: image download");
-    }
-    return FF_OK;
+    return image_end(s, image, image_is_device, bytes, target, "ff_project_sprites");
 }
 
 ff_status ff_step_splat(ff_system* s, int64_t n_steps, double dt, const ff_view* v, uint32_t* image,

@@ -36,6 +36,6 @@ class EnsembleRK4(torch.autograd.Function):
     def backward(ctx, grad_xT):
         grad_xT = grad_xT.contiguous().to(torch.float32)
         dx0 = torch.empty_like(grad_xT)
-        dp = ff_backward(ctx.system.handle, grad_xT, dx0, np.zeros(max(ctx.n_params, 1), np.float64))
+        dp = ff_backward(ctx.system.handle, grad_xT, dx0)[:ctx.n_params]
         dparams = torch.from_numpy(np.ascontiguousarray(dp[:ctx.n_params])).to(ctx.params_dtype)
         return dx0, dparams, None, None, None, None

@@ -216,22 +216,14 @@ __device__ __forceinline__ void fwd_step(float (&x)[R::DIM], float h, const floa
     const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
     float k[D], xs[D], acc[D];
     if constexpr (D > 8) {
-        // large systems: the four stages as a loop over one copy of f (same arithmetic)
+        // large systems: the forward integrator's own RK4 stepper (for HH3 the packed
+        // neuron pairs), so the recomputed states are the taped forward's, bit for bit
+        typename StepperFor<R, FF_RK4, false>::type st;
+        float sc[D];
+        st.init(h, p);
+        st.acc(x, acc, sc);
 #pragma unroll
-        for (int i = 0; i < D; ++i) xs[i] = x[i];
-#pragma unroll 1
-        for (int st = 0; st < 4; ++st) {
-            R::f(xs, p, k);
-            const float c = (st == 2) ? h : h2;
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                if (st == 0) acc[i] = k[i];
-                else if (st < 3) acc[i] = fmaf(2.0f, k[i], acc[i]);
-                xs[i] = fmaf(c, k[i], x[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < D; ++i) x[i] = fmaf(h6, acc[i] + k[i], x[i]);
+        for (int i = 0; i < D; ++i) x[i] = fmaf(sc[i], acc[i], x[i]);
         return;
     }
     R::f(x, p, k);

@@ -4,7 +4,7 @@
 //
 // One thread per particle walks the chunks in reverse with the adjoint state
 // lambda = dL/dx in registers.  A chunk of L <= M*M steps is recomputed from its
-// checkpoint twice: once to place sub-checkpoints every M steps (local memory),
+// checkpoint twice (once when L <= M): once to place sub-checkpoints every M steps (local memory),
 // then per sub-segment (in reverse) to put its <= M states in registers (local
 // memory for the 15-dimensional system), which the reverse RK4 steps consume
 // from last to first.  Parameter gradients are
@@ -349,13 +349,15 @@ __device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i
         float x[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) x[k] = (k < a.dim) ? ck[k * a.pitch + i] : 0.0f;
-        // sub-checkpoints every M steps
+        // sub-checkpoints every M steps (nothing to advance past the last one: a chunk of at
+        // most M steps is recomputed once, by its only sub-segment)
         float cp[M][D];
         int nsub = 0;
         for (int base = 0; base < L; base += M, ++nsub) {
 #pragma unroll
             for (int k = 0; k < D; ++k) cp[nsub][k] = x[k];
-            const int nq = min(M, L - base);
+            const int nq = (base + M < L) ? M : 0;
+#pragma unroll 1
             for (int r = 0; r < nq; ++r) fwd_step<R, METHOD>(x, h, p);
         }
         float jp[NP];
@@ -556,7 +558,11 @@ bool adjoint_supported(int rhs_id) {
 }
 
 int adjoint_sub_steps(int64_t checkpoint_every) {
-    if (checkpoint_every <= 16) return 4;
+    // a chunk of up to 16 steps is one sub-segment (one recomputation); longer chunks take
+    // sub-checkpoints every M steps with M * M >= the chunk (two recomputations)
+    if (checkpoint_every <= 4) return 4;
+    if (checkpoint_every <= 8) return 8;
+    if (checkpoint_every <= 16) return 16;
     if (checkpoint_every <= 64) return 8;
     return 16;
 }

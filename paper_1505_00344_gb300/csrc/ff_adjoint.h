@@ -55,7 +55,7 @@ struct BatchAdjointArgs {
 };
 
 bool adjoint_supported(int rhs_id);
-int adjoint_sub_steps(int64_t checkpoint_every);  // M with M * M >= checkpoint_every (at most 256)
+int adjoint_sub_steps(int64_t checkpoint_every);  // M >= K up to 16, else M * M >= K (K at most 256)
 int64_t adjoint_partial_rows(int num_sms);
 cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const AdjointArgs& a, int num_sms,
                            cudaStream_t s, double* dL_dp_dev, int n_params_kernel);

@@ -443,6 +443,174 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed-pair adjoint for Lorenz RK4: two particles per thread in f32x2
+// registers (lane 0 particle 2t, lane 1 particle 2t + 1).  Every operation is
+// the scalar adjoint's, lane by lane (Lorenz::f, the RK4 step, Vjp<Lorenz> and
+// the reverse step; negations as 0 - x, which is exact), so dL/dx0 is the same
+// to the bit and the parameter sums differ only in their FP64 order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ f2 neg2(f2 a) { return sub2(pack2(0.0f, 0.0f), a); }
+__device__ __forceinline__ f2 mul2a(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+struct LorenzPairP {
+    f2 s, ns, r, nb;  // sigma, -sigma, r, -beta per lane
+};
+
+__device__ __forceinline__ void lorenz_f2(const f2 (&x)[3], const LorenzPairP& c, f2 (&k)[3]) {
+    k[0] = mul2a(c.s, sub2(x[1], x[0]));
+    k[1] = fma2(x[0], sub2(c.r, x[2]), neg2(x[1]));
+    k[2] = fma2(x[0], x[1], mul2a(c.nb, x[2]));
+}
+
+__device__ __forceinline__ void lorenz_fwd2(f2 (&x)[3], f2 h, f2 h2, f2 h6, const LorenzPairP& c) {
+    const f2 two = pack2(2.0f, 2.0f);
+    f2 k[3], xs[3], acc[3];
+    lorenz_f2(x, c, k);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { acc[i] = k[i]; xs[i] = fma2(h2, k[i], x[i]); }
+    lorenz_f2(xs, c, k);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { acc[i] = fma2(two, k[i], acc[i]); xs[i] = fma2(h2, k[i], x[i]); }
+    lorenz_f2(xs, c, k);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { acc[i] = fma2(two, k[i], acc[i]); xs[i] = fma2(h, k[i], x[i]); }
+    lorenz_f2(xs, c, k);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x[i] = fma2(h6, add2(acc[i], k[i]), x[i]);
+}
+
+// jx = J(x)^T v, jp += F_p(x)^T v (Vjp<Lorenz> lane by lane)
+__device__ __forceinline__ void lorenz_vjp2(const f2 (&x)[3], const LorenzPairP& c, const f2 (&v)[3], f2 (&jx)[3],
+                                            f2 (&jp)[3]) {
+    jx[0] = fma2(c.ns, v[0], fma2(sub2(c.r, x[2]), v[1], mul2a(x[1], v[2])));
+    jx[1] = fma2(c.s, v[0], fma2(x[0], v[2], neg2(v[1])));
+    jx[2] = fma2(neg2(x[0]), v[1], mul2a(c.nb, v[2]));
+    jp[0] = fma2(sub2(x[1], x[0]), v[0], jp[0]);
+    jp[1] = fma2(x[0], v[1], jp[1]);
+    jp[2] = fma2(neg2(x[2]), v[2], jp[2]);
+}
+
+__device__ __forceinline__ void lorenz_adj2(const f2 (&x)[3], f2 (&lam)[3], f2 h, f2 h2, f2 h3, f2 h6,
+                                            const LorenzPairP& c, f2 (&jp)[3]) {
+    f2 k[3], x2[3], x3[3], x4[3];
+    lorenz_f2(x, c, k);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x2[i] = fma2(h2, k[i], x[i]);
+    lorenz_f2(x2, c, k);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x3[i] = fma2(h2, k[i], x[i]);
+    lorenz_f2(x3, c, k);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x4[i] = fma2(h, k[i], x[i]);
+    f2 l[3], m[3], sum[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) l[i] = mul2a(h6, lam[i]);
+    lorenz_vjp2(x4, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { sum[i] = m[i]; l[i] = fma2(h3, lam[i], mul2a(h, m[i])); }
+    lorenz_vjp2(x3, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(h3, lam[i], mul2a(h2, m[i])); }
+    lorenz_vjp2(x2, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(h6, lam[i], mul2a(h2, m[i])); }
+    lorenz_vjp2(x, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) lam[i] = add2(lam[i], add2(sum[i], m[i]));
+}
+
+template <bool PP, int M>
+__global__ void __launch_bounds__(128, 3) adjoint_lorenz_x2_kernel(const __grid_constant__ AdjointArgs a) {
+    __shared__ double red[4][3];
+    double gacc[3] = {0.0, 0.0, 0.0};
+    const int64_t npair = (a.n + 1) / 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += stride) {
+        const int64_t i0 = 2 * t, i1 = 2 * t + 1;
+        const bool has1 = i1 < a.n;  // an odd count leaves the last pair half empty
+        int g0 = 0, g1 = 0;
+#pragma unroll
+        for (int q = 1; q < FF_MAX_GROUPS; ++q) {
+            if (q < a.n_groups && i0 >= a.gstart[q]) g0 = q;
+            if (q < a.n_groups && i1 >= a.gstart[q]) g1 = q;
+        }
+        f2 lam[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            lam[k] = pack2(a.lam_in[k * a.n + i0], has1 ? a.lam_in[k * a.n + i1] : 0.0f);
+        const float pv0 = PP ? a.pparam[i0] : 0.0f, pv1 = (PP && has1) ? a.pparam[i1] : 0.0f;
+        for (int c = a.n_chunks - 1; c >= 0; --c) {
+            const AdjChunk& ch = a.chunks[c];
+            float pa[3], pb[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                pa[q] = (PP && q == a.pidx) ? pv0 : ch.p[q];
+                pb[q] = (PP && q == a.pidx) ? pv1 : ch.p[q];
+            }
+            LorenzPairP cp2;
+            cp2.s = pack2(pa[0], pb[0]);
+            cp2.ns = pack2(-pa[0], -pb[0]);
+            cp2.r = pack2(pa[1], pb[1]);
+            cp2.nb = pack2(-pa[2], -pb[2]);
+            const float ha = ch.gh[g0], hb = ch.gh[g1];
+            const f2 h = pack2(ha, hb), h2 = pack2(0.5f * ha, 0.5f * hb);
+            const f2 h3 = pack2(ha * (1.0f / 3.0f), hb * (1.0f / 3.0f)), h6 = pack2(ha * (1.0f / 6.0f), hb * (1.0f / 6.0f));
+            const int L = ch.n_steps;
+            const float* ck = a.ckpt + (int64_t)ch.ckpt * a.dim * a.pitch;
+            f2 x[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) x[k] = pack2(ck[k * a.pitch + i0], ck[k * a.pitch + i1]);  // pitch covers i1
+            f2 cpt[M][3];
+            int nsub = 0;
+            for (int base = 0; base < L; base += M, ++nsub) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cpt[nsub][k] = x[k];
+                const int nq = (base + M < L) ? M : 0;
+#pragma unroll 1
+                for (int r = 0; r < nq; ++r) lorenz_fwd2(x, h, h2, h6, cp2);
+            }
+            f2 jp[3] = {pack2(0.f, 0.f), pack2(0.f, 0.f), pack2(0.f, 0.f)};
+            for (int sq = nsub - 1; sq >= 0; --sq) {
+                const int nq = min(M, L - sq * M);
+                f2 st[M][3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) x[k] = cpt[sq][k];
+#pragma unroll
+                for (int r = 0; r < M; ++r) {
+                    if (r < nq) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) st[r][k] = x[k];
+                        if (r + 1 < nq) lorenz_fwd2(x, h, h2, h6, cp2);
+                    }
+                }
+#pragma unroll
+                for (int r = M - 1; r >= 0; --r)
+                    if (r < nq) lorenz_adj2(st[r], lam, h, h2, h3, h6, cp2, jp);
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                float u, w;
+                unpack2(jp[q], u, w);
+                gacc[q] += (double)u;
+                if (has1) gacc[q] += (double)w;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float u, w;
+            unpack2(lam[k], u, w);
+            a.lam_out[k * a.n + i0] = u;
+            if (has1) a.lam_out[k * a.n + i1] = w;
+        }
+    }
+    block_sum_to_row<3, 4>(gacc, red, a.partial + (int64_t)blockIdx.x * a.np_stride);
+}
+
 // Batched adjoint: each block takes tiles round-robin; a tile is a run of
 // particles of one member, one per thread, and its parameter gradient is
 // reduced over the block into the tile's own row.
@@ -552,6 +720,33 @@ static cudaError_t launch_r(int method, bool pp, int m, const AdjointArgs& a, in
     }
 }
 
+template <bool PP, int M>
+static cudaError_t launch_lorenz_x2_one(const AdjointArgs& a, int num_sms, cudaStream_t s, int64_t* rows) {
+    auto kernel = adjoint_lorenz_x2_kernel<PP, M>;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int64_t need = ((a.n + 1) / 2 + 127) / 128;
+    int64_t cap = (int64_t)occ * num_sms;
+    if (cap > a.max_blocks) cap = a.max_blocks;  // rows of the partial-sum buffer
+    const int grid = (int)(need < cap ? need : cap);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    kernel<<<grid, 128, 0, s>>>(a);
+    *rows = grid;
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_lorenz_x2(bool pp, int m, const AdjointArgs& a, int num_sms, cudaStream_t s,
+                                    int64_t* rows) {
+    switch (m) {
+    case 4: return pp ? launch_lorenz_x2_one<true, 4>(a, num_sms, s, rows) : launch_lorenz_x2_one<false, 4>(a, num_sms, s, rows);
+    case 8: return pp ? launch_lorenz_x2_one<true, 8>(a, num_sms, s, rows) : launch_lorenz_x2_one<false, 8>(a, num_sms, s, rows);
+    case 16: return pp ? launch_lorenz_x2_one<true, 16>(a, num_sms, s, rows) : launch_lorenz_x2_one<false, 16>(a, num_sms, s, rows);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 bool adjoint_supported(int rhs_id) {
     return rhs_id == FF_RHS_LORENZ || rhs_id == FF_RHS_WILSON_COWAN || rhs_id == FF_RHS_HARMONIC ||
            rhs_id == FF_RHS_LINEAR || rhs_id == FF_RHS_HH3;
@@ -575,7 +770,10 @@ cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const Adjoint
     int64_t rows = 0;
     cudaError_t e;
     switch (rhs_id) {
-    case FF_RHS_LORENZ: e = launch_r<Lorenz>(method, pp, m, a, block, num_sms, s, &rows); break;
+    case FF_RHS_LORENZ:
+        e = method == FF_RK4 ? launch_lorenz_x2(pp, m, a, num_sms, s, &rows)
+                             : launch_r<Lorenz>(method, pp, m, a, block, num_sms, s, &rows);
+        break;
     case FF_RHS_WILSON_COWAN: e = launch_r<WilsonCowan>(method, pp, m, a, block, num_sms, s, &rows); break;
     case FF_RHS_HARMONIC: e = launch_r<Harmonic>(method, pp, m, a, block, num_sms, s, &rows); break;
     case FF_RHS_LINEAR: e = launch_r<Linear>(method, pp, m, a, block, num_sms, s, &rows); break;

@@ -22,6 +22,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -120,7 +121,7 @@ class ClockSampler:
     def __init__(self, device_index, enabled=True):
         self.proc = None
         self.device_index = device_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"ff_bench_clocks_{os.getpid()}_{device_index}.csv")
         if not enabled:
             return
         try:

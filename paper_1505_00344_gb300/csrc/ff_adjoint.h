@@ -60,6 +60,26 @@ int64_t adjoint_partial_rows(int num_sms);
 cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const AdjointArgs& a, int num_sms,
                            cudaStream_t s, double* dL_dp_dev, int n_params_kernel);
 constexpr int kAdjTile = 128;  // particles per batched-adjoint tile = threads per block
+
+// Per-family launchers (ff_adjoint_lorenz.cu, ff_adjoint_hh3.cu, ff_adjoint_small.cu,
+// ff_adjoint_linear.cu): the sweep
+// kernel only; `rows` receives the number of partial rows it wrote.
+cudaError_t launch_adjoint_lorenz(int method, bool pp, int m, const AdjointArgs& a, int block, int num_sms,
+                                  cudaStream_t s, int64_t* rows);
+cudaError_t launch_adjoint_hh3(int method, bool pp, int m, const AdjointArgs& a, int block, int num_sms,
+                               cudaStream_t s, int64_t* rows);
+cudaError_t launch_adjoint_small(int rhs_id, int method, bool pp, int m, const AdjointArgs& a, int block,
+                                 int num_sms, cudaStream_t s, int64_t* rows);
+cudaError_t launch_adjoint_linear(int method, bool pp, int m, const AdjointArgs& a, int block, int num_sms,
+                                  cudaStream_t s, int64_t* rows);
+cudaError_t launch_batch_adjoint_linear(int method, bool pp, int m, const BatchAdjointArgs& b, int num_sms,
+                                        cudaStream_t s);
+cudaError_t launch_batch_adjoint_lorenz(int method, bool pp, int m, const BatchAdjointArgs& b, int num_sms,
+                                        cudaStream_t s);
+cudaError_t launch_batch_adjoint_hh3(int method, bool pp, int m, const BatchAdjointArgs& b, int num_sms,
+                                     cudaStream_t s);
+cudaError_t launch_batch_adjoint_small(int rhs_id, int method, bool pp, int m, const BatchAdjointArgs& b,
+                                       int num_sms, cudaStream_t s);
 // One batched-adjoint launch over b.tiles, then dp[m * np_stride + q] = sum of
 // member m's rows in order, for m < n_members and q < n_params_kernel.
 cudaError_t launch_batch_adjoint(int rhs_id, int method, bool pp, int m, const BatchAdjointArgs& b,

@@ -137,7 +137,7 @@ ff_status ff_create_system(int rhs_id, int dim, const double* params, int n_para
         return st;
     }
     // default launch shape: plain RK4 on Lorenz runs packed pairs, 4 particles per thread
-    s->ppt = (rhs_id == FF_RHS_LORENZ && method == FF_RK4 && !(flags & FF_FLAG_KAHAN)) ? 4 : 1;
+    s->ppt = (rhs_id == FF_RHS_LORENZ && method == FF_RK4) ? 4 : 1;  // packed pairs, plain or compensated
     s->block = 256;
     *out = s;
     return FF_OK;
@@ -918,7 +918,9 @@ void set_last_error_message(const char* msg) { g_last_error = msg; }
 cudaError_t launch_integrate(int rhs_id, int method, bool kahan, bool pp, const IntegrateArgs& a,
                              const LaunchShape& shape, cudaStream_t stream) {
     switch (rhs_id) {
-    case FF_RHS_LORENZ: return launch_integrate_lorenz(method, kahan, pp, a, shape, stream);
+    case FF_RHS_LORENZ:
+        if (kahan && lorenz_kahan_packed(method, pp, a, shape)) return launch_integrate_lorenz_kahan(pp, a, shape, stream);
+        return launch_integrate_lorenz(method, kahan, pp, a, shape, stream);
     case FF_RHS_WILSON_COWAN: return launch_integrate_wc(method, kahan, pp, a, shape, stream);
     case FF_RHS_HH3: return launch_integrate_hh3(method, kahan, pp, a, shape, stream);
     case FF_RHS_LINEAR:

@@ -867,6 +867,11 @@ cudaError_t launch_integrate_lorenz(int method, bool kahan, bool pp, const Integ
 bool lorenz_uniform_packed(int method, bool kahan, bool pp, const IntegrateArgs& a, const LaunchShape& shape);
 cudaError_t launch_integrate_lorenz_splat(bool pp, const IntegrateArgs& a, const LaunchShape& shape,
                                           cudaStream_t stream);
+// Compensated RK4 for Lorenz as packed pairs (ff_integrate_lorenz_kahan.cu), where the
+// shape allows it (2 or 4 particles per thread, aligned groups, no reset, parameter r at most).
+bool lorenz_kahan_packed(int method, bool pp, const IntegrateArgs& a, const LaunchShape& shape);
+cudaError_t launch_integrate_lorenz_kahan(bool pp, const IntegrateArgs& a, const LaunchShape& shape,
+                                          cudaStream_t stream);
 cudaError_t launch_integrate_wc(int method, bool kahan, bool pp, const IntegrateArgs& a,
                                 const LaunchShape& shape, cudaStream_t stream);
 cudaError_t launch_integrate_hh3(int method, bool kahan, bool pp, const IntegrateArgs& a,
@@ -934,6 +939,41 @@ inline cudaError_t launch_reset_variants(int method, bool kahan, bool pp, const 
                          : persistent_launch(integrate_kernel<R, FF_EULER, true, false, 1, true>, a, s, st);
     return pp ? persistent_launch(integrate_kernel<R, FF_EULER, false, true, 1, true>, a, s, st)
               : persistent_launch(integrate_kernel<R, FF_EULER, false, false, 1, true>, a, s, st);
+}
+
+// Deal the persistent grid's blocks out to the groups in proportion to their
+// sizes (at least one block per group) and launch the group-uniform kernel.
+template <class Kernel>
+inline cudaError_t uniform_launch(Kernel kernel, const IntegrateArgs& a0, const LaunchShape& s0,
+                                  cudaStream_t stream) {
+    LaunchShape s = s0;
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, kernel);
+    if (e != cudaSuccess) return e;
+    if (s.block > attr.maxThreadsPerBlock) s.block = attr.maxThreadsPerBlock / 32 * 32;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, s.block, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int per_sm = (s.blocks_per_sm > 0 && s.blocks_per_sm < occ) ? s.blocks_per_sm : occ;
+    const int64_t total = (int64_t)per_sm * s.num_sms;
+    IntegrateArgs a = a0;
+    const int ppt = s.ppt;
+    int64_t items_all = 0;
+    for (int g = 0; g < a.n_groups; ++g) items_all += (a.gend[g] - a.gstart[g]) / ppt;
+    int next = 0;
+    for (int g = 0; g < a.n_groups; ++g) {
+        const int64_t items = (a.gend[g] - a.gstart[g]) / ppt;
+        int64_t nb = items_all > 0 ? (total * items + items_all / 2) / items_all : 1;
+        const int64_t need = (items + s.block - 1) / s.block;
+        if (nb > need) nb = need;
+        if (nb < 1) nb = 1;
+        a.gblk[g] = next;
+        next += (int)nb;
+    }
+    a.gblk[a.n_groups] = next;
+    kernel<<<next, s.block, 0, stream>>>(a);
+    return cudaGetLastError();
 }
 
 template <class R>

@@ -38,6 +38,7 @@ UNIT = "particle-steps/s"
 # FMA = 2 flops: RHS 6 instructions (8 flops) x 4 stages, 9 stage updates (18 flops), weighted
 # sum + update 12 instructions (21 flops).
 LORENZ_RK4_FLOPS = 71
+KAHAN_EXTRA_FLOPS = 9
 FP32_LANES_PER_SM = 128
 
 
@@ -309,7 +310,9 @@ def run_ours(args, rank, world, local):
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     avg_int_ms = statistics.mean(int_ms)
     n_work = (P + 3) // 4 * 4
-    flops_per_launch = LORENZ_RK4_FLOPS * n_work * w["steps_per_frame"] if w["rhs"] == "lorenz" else None
+    # the compensated update adds t = x + y, (t - x) - y per component: 9 flops per step
+    step_flops = LORENZ_RK4_FLOPS + (KAHAN_EXTRA_FLOPS if args.kahan else 0)
+    flops_per_launch = step_flops * n_work * w["steps_per_frame"] if w["rhs"] == "lorenz" else None
     roof = None
     if flops_per_launch:
         achieved = flops_per_launch / (avg_int_ms / 1e3) / 1e12

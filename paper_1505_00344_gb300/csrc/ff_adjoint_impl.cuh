@@ -84,106 +84,180 @@ template <> struct Vjp<WilsonCowan> {
     }
 };
 
-// g(y) = y / (1 - e^-y) and g'(y) = (1 - e^-y (1 + y)) / (1 - e^-y)^2, given e = e^-y.
-// For |y| < 0.5, where the differences cancel in FP32, the Bernoulli series
-// g' = 1/2 + y/6 - y^3/180 + y^5/5040 - y^7/151200 (next term below 1e-9).
-__device__ __forceinline__ void x_over_expm1(float y, float e, float& g, float& dg) {
-    if (fabsf(y) < 0.5f) {
-        const float y2 = y * y;
-        g = bernoulli_series(y);
-        dg = fmaf(y, fmaf(y2, fmaf(y2, fmaf(y2, -1.0f / 151200.0f, 1.0f / 5040.0f), -1.0f / 180.0f), 1.0f / 6.0f),
-                  0.5f);
-    } else {
-        const float r = __fdividef(1.0f, __fsub_rn(1.0f, e));
-        g = y * r;
-        dg = fmaf(-e, 1.0f + y, 1.0f) * r * r;
-    }
+// Parameter-derived constants of the HH3 vector-Jacobian product, per lane type.
+template <class O> struct HHVjpConst {
+    typename O::T gNa, gK, gL, ENa, EK, EL, gsyn, Esyn, invC, neg_invC, inv_tr, neg_inv_tr, neg_inv_td,
+        inv_td2, sig, neg_sig, neg_sig2, sig2_theta, theta, gNa3, gK4;
+};
+
+template <class O>
+__device__ __forceinline__ HHVjpConst<O> hh_vjp_const(const float* p) {
+    HHVjpConst<O> c;
+    const float invC = __fdividef(1.0f, p[0]), inv_tr = __fdividef(1.0f, p[12]), inv_td = __fdividef(1.0f, p[13]);
+    const float sig2 = p[14] * kLog2e;
+    c.gNa = O::k(p[1]);
+    c.gK = O::k(p[2]);
+    c.gL = O::k(p[3]);
+    c.ENa = O::k(p[4]);
+    c.EK = O::k(p[5]);
+    c.EL = O::k(p[6]);
+    c.gsyn = O::k(p[7]);
+    c.Esyn = O::k(p[8]);
+    c.invC = O::k(invC);
+    c.neg_invC = O::k(-invC);
+    c.inv_tr = O::k(inv_tr);
+    c.neg_inv_tr = O::k(-inv_tr);
+    c.neg_inv_td = O::k(-inv_td);
+    c.inv_td2 = O::k(inv_td * inv_td);
+    c.sig = O::k(p[14]);
+    c.neg_sig = O::k(-p[14]);
+    c.neg_sig2 = O::k(-sig2);
+    c.sig2_theta = O::k(sig2 * p[15]);
+    c.theta = O::k(p[15]);
+    c.gNa3 = O::k(3.0f * p[1]);
+    c.gK4 = O::k(4.0f * p[2]);
+    return c;
+}
+
+// d/dy of y / (1 - e^-y) by its series 1/2 + y/6 - y^3/180 + y^5/5040 - y^7/151200 (|y| < 0.5).
+template <class O>
+__device__ __forceinline__ typename O::T bernoulli_series_deriv_t(typename O::T y) {
+    const auto y2 = O::mul(y, y);
+    return O::fma(y, O::fma(y2, O::fma(y2, O::fma(y2, O::k(-1.0f / 151200.0f), O::k(1.0f / 5040.0f)),
+                                       O::k(-1.0f / 180.0f)), O::k(1.0f / 6.0f)), O::k(0.5f));
+}
+
+// One neuron of the HH3 vector-Jacobian product (Eq. 6-11 differentiated term by
+// term; the gate rates depend on V only), over a lane type.  With u = v_V / C:
+//   jx_V = sum over gates of v_y (a'(1 - y) - b' y) + v_s sig act (1 - act)(1 - s) / tau_r
+//          - u (gL + gNa m^3 h + gK n^4 + gsyn S)
+//   jx_y = (the current term's derivative) u - v_y (a + b)       for y = m, h, n
+//   self = -v_s (act / tau_r + 1 / tau_d)   (the own-s part of jx_s)
+//   syn  = gsyn (Esyn - V) u                 (added to the other neurons' jx_s)
+// and the neuron's contributions cp to dL/dp (indices 0..8, its drive, 12..15).
+template <class O>
+__device__ __forceinline__ void hh_neuron_vjp(typename O::T V, typename O::T m, typename O::T h, typename O::T n,
+                                              typename O::T s, typename O::T others, typename O::T drive,
+                                              typename O::T uV, typename O::T vm, typename O::T vh,
+                                              typename O::T vn, typename O::T vs, const HHVjpConst<O>& c,
+                                              typename O::T (&jx)[4], typename O::T& self, typename O::T& syn,
+                                              typename O::T (&cp)[14]) {
+    using T = typename O::T;
+    constexpr float kE25 = 12.182493960703473f;  // e^2.5
+    constexpr float kE1 = 2.718281828459045f;    // e^1
+    constexpr float kE3 = 20.085536923187668f;   // e^3
+    constexpr float kQ = -kLog2e / 80.0f, kQ0 = 65.0f * (-kLog2e / 80.0f);
+    constexpr float kB = -kLog2e / 18.0f, kB0 = 65.0f * (-kLog2e / 18.0f) + 2.0f;
+    const T one = O::k(1.0f);
+    // rates and their derivatives (the rates as in the forward right-hand side)
+    const T q = O::ex2(O::fma(V, O::k(kQ), O::k(kQ0)));
+    const T q2 = O::mul(q, q), q4 = O::mul(q2, q2), q8 = O::mul(q4, q4);
+    const T bm = O::ex2(O::fma(V, O::k(kB), O::k(kB0)));
+    const T ah = O::mul(O::k(0.07f), q4);
+    const T bn = O::mul(O::k(0.125f), q);
+    const T es = O::ex2(O::fma(c.neg_sig2, V, c.sig2_theta));
+    const T ym = O::fma(V, O::k(0.1f), O::k(4.0f)), yn = O::fma(V, O::k(0.1f), O::k(5.5f));
+    const auto sm = O::small(ym), sn = O::small(yn);
+    const T em = O::mul(O::k(kE25), q8), en = O::mul(O::k(kE1), q8);
+    const T dm = O::sel(sm, one, O::sub(one, em)), dn = O::sel(sn, one, O::sub(one, en));
+    const T rmn = O::rcp(O::mul(dm, dn));
+    const T rm = O::mul(dn, rmn), rn = O::mul(dm, rmn);  // 1 / dm, 1 / dn
+    // g(y) = y / (1 - e^-y), g'(y) = (1 - e^-y (1 + y)) / (1 - e^-y)^2; alpha_m = g(ym), alpha_n = g(yn) / 10
+    const T am = O::sel(sm, bernoulli_series_t<O>(ym), O::mul(ym, rm));
+    const T gn = O::sel(sn, bernoulli_series_t<O>(yn), O::mul(yn, rn));
+    const T dgm = O::sel(sm, bernoulli_series_deriv_t<O>(ym),
+                         O::mul(O::sub(one, O::mul(em, O::add(one, ym))), O::mul(rm, rm)));
+    const T dgn = O::sel(sn, bernoulli_series_deriv_t<O>(yn),
+                         O::mul(O::sub(one, O::mul(en, O::add(one, yn))), O::mul(rn, rn)));
+    const T an = O::mul(O::k(0.1f), gn);
+    const T dam = O::mul(O::k(0.1f), dgm), dan = O::mul(O::k(0.01f), dgn);
+    const T ph = O::fma(O::k(kE3), q8, one), ps = O::add(one, es);
+    const T r = O::rcp(O::mul(ph, ps));
+    const T bh = O::mul(ps, r), act = O::mul(ph, r);
+    const T a1 = O::mul(act, O::sub(one, act));
+    // minus the beta derivatives: beta_m' = -beta_m/18, beta_n' = -beta_n/80, beta_h' = beta_h (1 - beta_h)/10
+    const T nd_bm = O::mul(bm, O::k(1.0f / 18.0f)), nd_bn = O::mul(bn, O::k(1.0f / 80.0f));
+    const T nd_bh = O::mul(O::mul(O::k(0.1f), bh), O::sub(bh, one));
+    const T dah = O::mul(ah, O::k(-1.0f / 20.0f));
+    // currents
+    const T m2 = O::mul(m, m), m3 = O::mul(m2, m), m3h = O::mul(m3, h);
+    const T n2 = O::mul(n, n), n3 = O::mul(n2, n), n4 = O::mul(n2, n2);
+    const T dNa = O::sub(c.ENa, V), dK = O::sub(c.EK, V), dL = O::sub(c.EL, V), dS = O::sub(c.Esyn, V);
+    T I = O::mul(c.gL, dL);
+    I = O::fma(O::mul(c.gNa, m3h), dNa, I);
+    I = O::fma(O::mul(c.gK, n4), dK, I);
+    I = O::fma(O::mul(c.gsyn, others), dS, I);
+    I = O::add(I, drive);
+    const T gtot = O::fma(c.gsyn, others, O::fma(c.gK, n4, O::fma(c.gNa, m3h, c.gL)));
+    // state
+    const T sv = O::mul(O::mul(vs, c.inv_tr), O::sub(one, s));  // v_s (1 - s) / tau_r
+    const T gate_m = O::fma(dam, O::sub(one, m), O::mul(nd_bm, m));
+    const T gate_h = O::fma(dah, O::sub(one, h), O::mul(nd_bh, h));
+    const T gate_n = O::fma(dan, O::sub(one, n), O::mul(nd_bn, n));
+    const T jv = O::fma(vm, gate_m, O::fma(vh, gate_h, O::fma(vn, gate_n, O::mul(O::mul(c.sig, a1), sv))));
+    jx[0] = O::sub(jv, O::mul(uV, gtot));
+    jx[1] = O::sub(O::mul(O::mul(O::mul(O::mul(uV, c.gNa3), m2), h), dNa), O::mul(vm, O::add(am, bm)));
+    jx[2] = O::sub(O::mul(O::mul(O::mul(uV, c.gNa), m3), dNa), O::mul(vh, O::add(ah, bh)));
+    jx[3] = O::sub(O::mul(O::mul(O::mul(uV, c.gK4), n3), dK), O::mul(vn, O::add(an, bn)));
+    self = O::mul(vs, O::fma(act, c.neg_inv_tr, c.neg_inv_td));
+    syn = O::mul(O::mul(c.gsyn, dS), uV);
+    // parameters: C, gNa, gK, gL, ENa, EK, EL, gsyn, Esyn, drive, tau_r, tau_d, sig, theta
+    cp[0] = O::mul(O::mul(I, c.neg_invC), uV);
+    cp[1] = O::mul(O::mul(m3h, dNa), uV);
+    cp[2] = O::mul(O::mul(n4, dK), uV);
+    cp[3] = O::mul(dL, uV);
+    cp[4] = O::mul(O::mul(c.gNa, m3h), uV);
+    cp[5] = O::mul(O::mul(c.gK, n4), uV);
+    cp[6] = O::mul(c.gL, uV);
+    cp[7] = O::mul(O::mul(dS, others), uV);
+    cp[8] = O::mul(O::mul(c.gsyn, others), uV);
+    cp[9] = uV;
+    cp[10] = O::mul(O::mul(act, c.neg_inv_tr), sv);
+    cp[11] = O::mul(O::mul(s, c.inv_td2), vs);
+    cp[12] = O::mul(O::mul(a1, O::sub(V, c.theta)), sv);
+    cp[13] = O::mul(O::mul(c.neg_sig, a1), sv);
 }
 
 template <> struct Vjp<HH3> {
-    // Eq. 6-11 differentiated term by term; the gate rates depend on V only.
-    // Per neuron i with u_i = v_V,i / C:
-    //   d/dV_i: -u_i (gL + gNa m^3 h + gK n^4 + gsyn S_i) + sum over gates of
-    //           v_y (a'(1 - y) - b' y) + v_s sig act (1 - act)(1 - s) / tau_r
-    //   d/dm, d/dh, d/dn: the current terms' derivatives times u_i minus v_y (a + b)
-    //   d/ds_i: -v_s (act / tau_r + 1 / tau_d) + sum_{j != i} gsyn (Esyn - V_j) u_j
-    // where S_i is the sum of the other neurons' s.
+    // Neurons 0 and 1 run the neuron product above packed in f32x2 registers,
+    // neuron 2 on floats; lane by lane the arithmetic is the same.
     __device__ __forceinline__ static void apply(const float (&x)[15], const float* p, const float (&v)[15],
                                                  float (&jx)[15], float* jp) {
-        const float C = p[0], gNa = p[1], gK = p[2], gL = p[3];
-        const float ENa = p[4], EK = p[5], EL = p[6], gsyn = p[7], Esyn = p[8];
-        const float inv_tr = __fdividef(1.0f, p[12]), inv_td = __fdividef(1.0f, p[13]);
-        const float sig = p[14], theta = p[15];
-        const float invC = __fdividef(1.0f, C);
-        const float s_sum = x[4] + x[9] + x[14];
-        constexpr float kE25 = 12.182493960703473f;  // e^2.5
-        constexpr float kE1 = 2.718281828459045f;    // e^1
-        constexpr float kE3 = 20.085536923187668f;   // e^3
-        float syn[3], self_s[3];
+        const HHVjpConst<HHPair> c2 = hh_vjp_const<HHPair>(p);
+        const HHVjpConst<HHScalar> c1 = hh_vjp_const<HHScalar>(p);
+        const float s_sum = __fadd_rn(__fadd_rn(x[4], x[9]), x[14]);
+        const f2 S01 = pack2(x[4], x[9]);
+        const f2 uV01 = mul2(pack2(v[0], v[5]), c2.invC);
+        f2 jx01[4], self01, syn01, cp01[14];
+        hh_neuron_vjp<HHPair>(pack2(x[0], x[5]), pack2(x[1], x[6]), pack2(x[2], x[7]), pack2(x[3], x[8]), S01,
+                              sub2(pack2(s_sum, s_sum), S01), pack2(p[9], p[10]), uV01, pack2(v[1], v[6]),
+                              pack2(v[2], v[7]), pack2(v[3], v[8]), pack2(v[4], v[9]), c2, jx01, self01, syn01, cp01);
+        float jx2[4], self2, syn2, cp2[14];
+        hh_neuron_vjp<HHScalar>(x[10], x[11], x[12], x[13], x[14], __fsub_rn(s_sum, x[14]), p[11],
+                                __fmul_rn(v[10], c1.invC), v[11], v[12], v[13], v[14], c1, jx2, self2, syn2, cp2);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const float V = x[5 * i], m = x[5 * i + 1], h = x[5 * i + 2], n = x[5 * i + 3], s = x[5 * i + 4];
-            const float uV = v[5 * i] * invC, vm = v[5 * i + 1], vh = v[5 * i + 2], vn = v[5 * i + 3];
-            const float vs = v[5 * i + 4];
-            // rates (same formulation as the forward right-hand side)
-            const float u = V + 65.0f;
-            const float q = exp2f(u * (-kLog2e / 80.0f));
-            const float q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
-            const float bm = 4.0f * exp2f(u * (-kLog2e / 18.0f));
-            const float ah = 0.07f * q4;
-            const float bn = 0.125f * q;
-            const float bh = __fdividef(1.0f, fmaf(kE3, q8, 1.0f));
-            const float act = __fdividef(1.0f, 1.0f + exp2f(sig * kLog2e * (theta - V)));
-            float gm, dgm, gn, dgn;
-            x_over_expm1((V + 40.0f) * 0.1f, kE25 * q8, gm, dgm);
-            x_over_expm1((V + 55.0f) * 0.1f, kE1 * q8, gn, dgn);
-            const float am = gm, dam = 0.1f * dgm;   // alpha_m = 0.1 (V+40) / (1 - e^{-(V+40)/10})
-            const float an = 0.1f * gn, dan = 0.01f * dgn;
-            const float dbm = bm * (-1.0f / 18.0f), dah = ah * (-1.0f / 20.0f), dbn = bn * (-1.0f / 80.0f);
-            const float dbh = 0.1f * bh * (1.0f - bh);
-            const float a1 = act * (1.0f - act);
-            // currents
-            const float m2 = m * m, m3 = m2 * m, m3h = m3 * h;
-            const float n2 = n * n, n3 = n2 * n, n4 = n2 * n2;
-            const float others = s_sum - s;
-            const float dNa = ENa - V, dK = EK - V, dL = EL - V, dS = Esyn - V;
-            float I = gL * dL;
-            I = fmaf(gNa * m3h, dNa, I);
-            I = fmaf(gK * n4, dK, I);
-            I = fmaf(gsyn * others, dS, I);
-            I = I + p[9 + i];
-            const float gtot = fmaf(gsyn, others, fmaf(gK, n4, fmaf(gNa, m3h, gL)));
-            float jv = -uV * gtot;
-            jv = fmaf(vm, fmaf(dam, 1.0f - m, -dbm * m), jv);
-            jv = fmaf(vh, fmaf(dah, 1.0f - h, -dbh * h), jv);
-            jv = fmaf(vn, fmaf(dan, 1.0f - n, -dbn * n), jv);
-            const float sv = vs * inv_tr * (1.0f - s);  // v_s (1 - s) / tau_r
-            jv = fmaf(sig * a1, sv, jv);
-            jx[5 * i] = jv;
-            jx[5 * i + 1] = fmaf(uV * 3.0f * gNa * m2 * h, dNa, -vm * (am + bm));
-            jx[5 * i + 2] = fmaf(uV * gNa * m3, dNa, -vh * (ah + bh));
-            jx[5 * i + 3] = fmaf(uV * 4.0f * gK * n3, dK, -vn * (an + bn));
-            self_s[i] = -vs * fmaf(act, inv_tr, inv_td);
-            syn[i] = gsyn * dS * uV;
-            // parameters
-            jp[0] = fmaf(-I * invC, uV, jp[0]);
-            jp[1] = fmaf(m3h * dNa, uV, jp[1]);
-            jp[2] = fmaf(n4 * dK, uV, jp[2]);
-            jp[3] = fmaf(dL, uV, jp[3]);
-            jp[4] = fmaf(gNa * m3h, uV, jp[4]);
-            jp[5] = fmaf(gK * n4, uV, jp[5]);
-            jp[6] = fmaf(gL, uV, jp[6]);
-            jp[7] = fmaf(dS * others, uV, jp[7]);
-            jp[8] = fmaf(gsyn * others, uV, jp[8]);
-            jp[9 + i] = __fadd_rn(jp[9 + i], uV);
-            jp[12] = fmaf(-act * inv_tr, sv, jp[12]);
-            jp[13] = fmaf(s * inv_td * inv_td, vs, jp[13]);
-            jp[14] = fmaf(a1 * (V - theta), sv, jp[14]);
-            jp[15] = fmaf(-sig * a1, sv, jp[15]);
+        for (int k = 0; k < 4; ++k) {
+            unpack2(jx01[k], jx[k], jx[5 + k]);
+            jx[10 + k] = jx2[k];
         }
-        const float syn_sum = syn[0] + syn[1] + syn[2];
+        float self0, self1, syn0, syn1;
+        unpack2(self01, self0, self1);
+        unpack2(syn01, syn0, syn1);
+        const float syn_sum = __fadd_rn(__fadd_rn(syn0, syn1), syn2);
+        jx[4] = __fadd_rn(self0, __fsub_rn(syn_sum, syn0));
+        jx[9] = __fadd_rn(self1, __fsub_rn(syn_sum, syn1));
+        jx[14] = __fadd_rn(self2, __fsub_rn(syn_sum, syn2));
+        // parameter contributions: neuron 0 + neuron 1 + neuron 2 (drives: one each)
+        float a0[14], a1[14];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) jx[5 * i + 4] = __fadd_rn(self_s[i], syn_sum - syn[i]);
+        for (int k = 0; k < 14; ++k) unpack2(cp01[k], a0[k], a1[k]);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) jp[k] = __fadd_rn(jp[k], __fadd_rn(__fadd_rn(a0[k], a1[k]), cp2[k]));
+        jp[9] = __fadd_rn(jp[9], a0[9]);
+        jp[10] = __fadd_rn(jp[10], a1[9]);
+        jp[11] = __fadd_rn(jp[11], cp2[9]);
+#pragma unroll
+        for (int k = 10; k < 14; ++k) jp[k + 2] = __fadd_rn(jp[k + 2], __fadd_rn(__fadd_rn(a0[k], a1[k]), cp2[k]));
     }
 };
 

@@ -230,7 +230,7 @@ def run_ours(args, rank, world, local):
     H, Wd = w["view"]["height"], w["view"]["width"]
     sysobj = ff.System.from_workload(w, kahan=args.kahan, stream=stream)
     if args.ppt or args.block or args.blocks_per_sm:
-        sysobj.set_launch(args.ppt or 1, args.block or 256, args.blocks_per_sm, 0)
+        sysobj.set_launch(args.ppt, args.block, args.blocks_per_sm, 0)  # 0: the library's default
     if args.reset:
         rs = w["reset"]
         sysobj.set_reset(rs["lo"], rs["hi"], rs["t_max"], rs["check_every"])

@@ -531,7 +531,8 @@ class System:
     def info(self):
         return ff_system_info(self.handle)
 
-    def set_launch(self, particles_per_thread=1, block=256, blocks_per_sm=0, max_steps_per_launch=0):
+    def set_launch(self, particles_per_thread=0, block=0, blocks_per_sm=0, max_steps_per_launch=0):
+        """Launch shape (0 keeps the current particles per thread or block size)."""
         ff_set_launch(self.handle, particles_per_thread, block, blocks_per_sm, max_steps_per_launch)
 
     @property

@@ -312,6 +312,8 @@ ff_status ff_set_params(ff_system* s, const double* params, int n_params) {
 
 ff_status ff_set_launch(ff_system* s, int ppt, int block, int blocks_per_sm, int64_t max_steps) {
     if (!s) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: system is NULL");
+    if (ppt == 0) ppt = s->ppt;
+    if (block == 0) block = s->block;
     if (ppt != 1 && ppt != 2 && ppt != 4) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: ppt %d not 1, 2 or 4", ppt);
     if (ppt != 1 && s->dim > 4 && s->rhs_id != FF_RHS_LINEAR)
         return fail(FF_ERR_INVALID_ARG, "ff_set_launch: ppt > 1 needs dim <= 4");

@@ -4,7 +4,8 @@ The CUDA path runs the whole workload; the oracle recomputes sampled particles
 one by one from its own seeding (and, for the chaotic long runs, compares
 attractor-density statistics instead of trajectories):
 
-* lorenz_4M: first 100 steps per sampled trajectory (state-relative error
+* lorenz_4M (4 particles per thread, packed pairs, splat fused into the
+  integrator, as timed): first 100 steps per sampled trajectory (state-relative error
   <= max(1e-5, 5x the FP64 oracle's one-ulp sensitivity), 99% <= 1e-5);
   after the full 100 frames x 200 steps, the forward group's coarse density
   matches the oracle's (total variation <= 0.05 and <= 3x the distance between
@@ -43,9 +44,8 @@ def _cuda():
 
 
 def system(w, kahan=False):
-    s = ff.System.from_workload(w, kahan=kahan, stream=torch.cuda.current_stream().cuda_stream)
-    s.set_launch(1, 256, 0, 0)  # bench.py's default launch shape
-    return s
+    # the library's default launch shape, which bench.py times (4 particles per thread for RK4 on Lorenz)
+    return ff.System.from_workload(w, kahan=kahan, stream=torch.cuda.current_stream().cuda_stream)
 
 
 def state(s):
@@ -159,8 +159,7 @@ def test_lorenz_4M_full_job_statistics():
     image = torch.zeros((w["view"]["height"], w["view"]["width"]), dtype=torch.int32, device="cuda")
     n_fwd = w["groups"][0]["count"]
     for f in range(w["frames"]):
-        s.step(w["steps_per_frame"], w["dt"])
-        s.project_splat(view, image)
+        s.step_splat(w["steps_per_frame"], w["dt"], view, image)  # the timed path: splat fused into the integrator
         if f == 4:  # 1000 steps: the backward group is escaping
             st = state(s)
             idx = n_fwd + np.arange(0, w["groups"][1]["count"], 256)
@@ -172,6 +171,10 @@ def test_lorenz_4M_full_job_statistics():
     assert abs(t_fwd - 20.0) < 1e-9 and abs(t_bwd + 20.0) < 1e-9
     img = image.cpu().numpy().view(np.uint32)
     assert 0.9 * n_fwd < img.sum() <= n_fwd
+    # the fused splat of the last frame is the projection of the final states
+    again = torch.zeros_like(image)
+    s.project_splat(view, again)
+    np.testing.assert_array_equal(again.cpu().numpy(), image.cpu().numpy())
     gpu = _coarse_density(s, w, group_mask=0b01)
     N = 65536
     A, _ = oracle_sample(w, np.arange(N), 20000)

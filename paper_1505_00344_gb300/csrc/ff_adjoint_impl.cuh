@@ -64,8 +64,8 @@ template <> struct Vjp<WilsonCowan> {
         const float aE = fmaf(wEE, E, fmaf(-wEI, I, p[4]));
         const float aI = fmaf(wIE, E, fmaf(-wII, I, p[5]));
         const float g2 = g * kLog2e;
-        const float SE = __fdividef(1.0f, 1.0f + exp2f(g2 * (th - aE)));
-        const float SI = __fdividef(1.0f, 1.0f + exp2f(g2 * (th - aI)));
+        const float SE = rcp_ftz(1.0f + ex2_ftz(g2 * (th - aE)));
+        const float SI = rcp_ftz(1.0f + ex2_ftz(g2 * (th - aI)));
         const float sE = SE * (1.0f - SE), sI = SI * (1.0f - SI);  // S'/gain
         const float uE = __fdividef(v[0], tE), uI = __fdividef(v[1], tI);  // v_k / tau_k
         const float dE = g * sE * uE, dI = g * sI * uI;                   // S'(a) v / tau
@@ -601,9 +601,17 @@ __device__ __forceinline__ void lorenz_adj2(const f2 (&x)[3], f2 (&lam)[3], f2 h
     for (int i = 0; i < 3; ++i) lam[i] = add2(lam[i], add2(sum[i], m[i]));
 }
 
+// The states of the sub-segment being reversed live in shared memory, one
+// 8-byte slot per thread and component ([step][component][thread], so a warp's
+// accesses are consecutive), which keeps the register file for the arithmetic:
+// 64-thread blocks, up to 8 resident per SM.
+constexpr int kLx2Block = 64;
+
 template <bool PP, int M>
-__global__ void __launch_bounds__(128, 3) adjoint_lorenz_x2_kernel(const __grid_constant__ AdjointArgs a) {
-    __shared__ double red[4][3];
+__global__ void __launch_bounds__(kLx2Block, 8) adjoint_lorenz_x2_kernel(const __grid_constant__ AdjointArgs a) {
+    __shared__ double red[kLx2Block / 32][3];
+    __shared__ f2 st[M][3][kLx2Block];
+    const int tid = threadIdx.x;
     double gacc[3] = {0.0, 0.0, 0.0};
     const int64_t npair = (a.n + 1) / 2;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -654,20 +662,24 @@ __global__ void __launch_bounds__(128, 3) adjoint_lorenz_x2_kernel(const __grid_
             f2 jp[3] = {pack2(0.f, 0.f), pack2(0.f, 0.f), pack2(0.f, 0.f)};
             for (int sq = nsub - 1; sq >= 0; --sq) {
                 const int nq = min(M, L - sq * M);
-                f2 st[M][3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) x[k] = cpt[sq][k];
 #pragma unroll
                 for (int r = 0; r < M; ++r) {
                     if (r < nq) {
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) st[r][k] = x[k];
+                        for (int k = 0; k < 3; ++k) st[r][k][tid] = x[k];
                         if (r + 1 < nq) lorenz_fwd2(x, h, h2, h6, cp2);
                     }
                 }
 #pragma unroll
                 for (int r = M - 1; r >= 0; --r)
-                    if (r < nq) lorenz_adj2(st[r], lam, h, h2, h3, h6, cp2, jp);
+                    if (r < nq) {
+                        f2 xr[3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) xr[k] = st[r][k][tid];
+                        lorenz_adj2(xr, lam, h, h2, h3, h6, cp2, jp);
+                    }
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -685,7 +697,7 @@ __global__ void __launch_bounds__(128, 3) adjoint_lorenz_x2_kernel(const __grid_
             if (has1) a.lam_out[k * a.n + i1] = w;
         }
     }
-    block_sum_to_row<3, 4>(gacc, red, a.partial + (int64_t)blockIdx.x * a.np_stride);
+    block_sum_to_row<3, kLx2Block / 32>(gacc, red, a.partial + (int64_t)blockIdx.x * a.np_stride);
 }
 
 // Batched adjoint: each block takes tiles round-robin; a tile is a run of
@@ -780,16 +792,20 @@ static cudaError_t launch_r(int method, bool pp, int m, const AdjointArgs& a, in
 template <bool PP, int M>
 static cudaError_t launch_lorenz_x2_one(const AdjointArgs& a, int num_sms, cudaStream_t s, int64_t* rows) {
     auto kernel = adjoint_lorenz_x2_kernel<PP, M>;
+    // the sub-segment states take shared memory, so favour it over L1
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kLx2Block, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    const int64_t need = ((a.n + 1) / 2 + 127) / 128;
+    const int64_t need = ((a.n + 1) / 2 + kLx2Block - 1) / kLx2Block;
     int64_t cap = (int64_t)occ * num_sms;
-    if (cap > a.max_blocks) cap = a.max_blocks;  // rows of the partial-sum buffer
+    if (cap > 8 * a.max_blocks) cap = 8 * a.max_blocks;  // rows of the partial-sum buffer (one per block here)
     const int grid = (int)(need < cap ? need : cap);
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    kernel<<<grid, 128, 0, s>>>(a);
+    kernel<<<grid, kLx2Block, 0, s>>>(a);
     *rows = grid;
     return cudaGetLastError();
 }

@@ -21,6 +21,22 @@ namespace ff {
 
 constexpr float kLog2e = 1.4426950408889634f;
 
+// Base-2 exponential and reciprocal as the single PTX approximations with
+// subnormal inputs and results flushed to zero (ex2: at most 2 ulp, rcp: 1 ulp
+// over the normal range).  The non-flushing forms that exp2f and __fdividef
+// lower to add range scaling around the same instruction; no argument here
+// is subnormal, and a subnormal exponential only meets 1 + e, which is 1 either way.
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct IntegrateArgs {
     float* x;              // state planes
     float* comp;           // Kahan compensation planes (KAHAN only)
@@ -69,8 +85,8 @@ __device__ __forceinline__ uint64_t reset_splitmix64(uint64_t seed, uint64_t n) 
 
 // ---------------------------------------------------------------------------
 // Right-hand sides.  Each has DIM (registers per particle state), NP (params)
-// and f(x, p, dx).  All arithmetic in FP32; exp via exp2f with the log2(e)
-// factor folded into the argument, quotients via __fdividef.
+// and f(x, p, dx).  All arithmetic in FP32; exp via ex2_ftz with the log2(e)
+// factor folded into the argument, reciprocals via rcp_ftz.
 // ---------------------------------------------------------------------------
 
 // Linear test system dx/dt = A x, A padded to 8x8 (row-major) by the host;
@@ -110,8 +126,8 @@ struct WilsonCowan {
     static constexpr int MAX_BLOCK = 512;
     __device__ __forceinline__ static float S(float a, float g2, float g2th) {
         // exp(-gain (a - th)) = 2^(g2 th - g2 a) with g2 = gain * log2(e)
-        float e = exp2f(fmaf(-g2, a, g2th));
-        return __fdividef(1.0f, 1.0f + e);
+        const float e = ex2_ftz(fmaf(-g2, a, g2th));
+        return rcp_ftz(1.0f + e);
     }
     __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
         const float E = x[0], I = x[1];
@@ -157,8 +173,8 @@ struct HHScalar {
     __device__ __forceinline__ static T sub(T a, T b) { return __fsub_rn(a, b); }
     __device__ __forceinline__ static T mul(T a, T b) { return __fmul_rn(a, b); }
     __device__ __forceinline__ static T fma(T a, T b, T c) { return fmaf(a, b, c); }
-    __device__ __forceinline__ static T ex2(T a) { return exp2f(a); }
-    __device__ __forceinline__ static T rcp(T a) { return __fdividef(1.0f, a); }
+    __device__ __forceinline__ static T ex2(T a) { return ex2_ftz(a); }
+    __device__ __forceinline__ static T rcp(T a) { return rcp_ftz(a); }
     __device__ __forceinline__ static M small(T y) { return fabsf(y) < 0.5f; }
     __device__ __forceinline__ static T sel(M c, T a, T b) { return c ? a : b; }
 };
@@ -1015,12 +1031,12 @@ struct HHPair {
     __device__ __forceinline__ static T ex2(T v) {
         float a, b;
         unpack2(v, a, b);
-        return pack2(exp2f(a), exp2f(b));
+        return pack2(ex2_ftz(a), ex2_ftz(b));
     }
     __device__ __forceinline__ static T rcp(T v) {
         float a, b;
         unpack2(v, a, b);
-        return pack2(__fdividef(1.0f, a), __fdividef(1.0f, b));
+        return pack2(rcp_ftz(a), rcp_ftz(b));
     }
     __device__ __forceinline__ static M small(T y) {
         float a, b;

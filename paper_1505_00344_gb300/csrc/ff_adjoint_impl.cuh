@@ -280,6 +280,113 @@ template <> struct Vjp<Linear> {
 };
 
 // One forward step (plain FP32, unshifted) used by the recomputation.
+// ---------------------------------------------------------------------------
+// Lorenz RK4 in the shifted variable zt = z - r, the integrator's LorenzRK4Shift:
+// the sweep keeps a chunk's states in (x, y, zt), so a recomputed step costs 37
+// instead of 49 operations and a stage point 7 instead of 10.  The shift is a
+// translation, so the Jacobian is the unshifted map's; it is evaluated with
+// r - z = -zt and -z = -r - zt.  Every operation is explicit (no contraction),
+// and the packed-pair sweep below repeats them lane by lane.
+// ---------------------------------------------------------------------------
+template <class R> struct IsLorenz { static constexpr bool value = false; };
+template <> struct IsLorenz<Lorenz> { static constexpr bool value = true; };
+
+struct LorenzShiftC {
+    float s, ns, nb, nbr, nr, h1, h2, h3, h6, nh1, nh2, nh6, sh1, sh2, sh6;
+    __device__ __forceinline__ void init(float h, const float* p) {
+        s = p[0];
+        ns = -p[0];
+        nb = -p[2];
+        nbr = __fmul_rn(nb, p[1]);
+        nr = -p[1];
+        h1 = h;
+        h2 = __fmul_rn(0.5f, h);
+        h3 = __fmul_rn(h, 1.0f / 3.0f);
+        h6 = __fmul_rn(h, 1.0f / 6.0f);
+        nh1 = -h1;
+        nh2 = -h2;
+        nh6 = -h6;
+        sh1 = __fmul_rn(s, h1);
+        sh2 = __fmul_rn(s, h2);
+        sh6 = __fmul_rn(s, h6);
+    }
+};
+
+// One RK4 step of (x, y, zt): the operations of LorenzRK4Shift::acc and the plain update.
+__device__ __forceinline__ void lorenz_shift_fwd(float (&x)[3], const LorenzShiftC& c) {
+    float d, A, kz, X, Y, Z, a0, a1, a2;
+    d = __fsub_rn(x[1], x[0]);
+    A = fmaf(x[0], x[2], x[1]);
+    kz = fmaf(x[0], x[1], fmaf(c.nb, x[2], c.nbr));
+    a0 = d; a1 = A; a2 = kz;
+    X = fmaf(c.sh2, d, x[0]); Y = fmaf(c.nh2, A, x[1]); Z = fmaf(c.h2, kz, x[2]);
+    d = __fsub_rn(Y, X);
+    A = fmaf(X, Z, Y);
+    kz = fmaf(X, Y, fmaf(c.nb, Z, c.nbr));
+    a0 = fmaf(2.0f, d, a0); a1 = fmaf(2.0f, A, a1); a2 = fmaf(2.0f, kz, a2);
+    X = fmaf(c.sh2, d, x[0]); Y = fmaf(c.nh2, A, x[1]); Z = fmaf(c.h2, kz, x[2]);
+    d = __fsub_rn(Y, X);
+    A = fmaf(X, Z, Y);
+    kz = fmaf(X, Y, fmaf(c.nb, Z, c.nbr));
+    a0 = fmaf(2.0f, d, a0); a1 = fmaf(2.0f, A, a1); a2 = fmaf(2.0f, kz, a2);
+    X = fmaf(c.sh1, d, x[0]); Y = fmaf(c.nh1, A, x[1]); Z = fmaf(c.h1, kz, x[2]);
+    d = __fsub_rn(Y, X);
+    A = fmaf(X, Z, Y);
+    kz = fmaf(X, Y, fmaf(c.nb, Z, c.nbr));
+    a0 = __fadd_rn(a0, d); a1 = __fadd_rn(a1, A); a2 = __fadd_rn(a2, kz);
+    x[0] = fmaf(c.sh6, a0, x[0]); x[1] = fmaf(c.nh6, a1, x[1]); x[2] = fmaf(c.h6, a2, x[2]);
+}
+
+// The stage point x + c k(P) of the step from x, and d = y - x at P.
+__device__ __forceinline__ void lorenz_shift_stage(const float (&P)[3], const float (&x)[3], float cs, float cn,
+                                                   float ch, const LorenzShiftC& c, float (&out)[3], float& d) {
+    d = __fsub_rn(P[1], P[0]);
+    const float A = fmaf(P[0], P[2], P[1]);
+    const float kz = fmaf(P[0], P[1], fmaf(c.nb, P[2], c.nbr));
+    out[0] = fmaf(cs, d, x[0]);
+    out[1] = fmaf(cn, A, x[1]);
+    out[2] = fmaf(ch, kz, x[2]);
+}
+
+// jx = J^T v, jp += F_p^T v at the shifted point P with d = y - x there:
+// J^T v = (-s v0 - zt v1 + y v2, s v0 - v1 + x v2, -x v1 - b v2),
+// F_p^T v = ((y - x) v0, x v1, -z v2).
+__device__ __forceinline__ void lorenz_shift_vjp(const float (&P)[3], float d, const LorenzShiftC& c,
+                                                 const float (&v)[3], float (&jx)[3], float* jp) {
+    const float nv1 = __fsub_rn(0.0f, v[1]);
+    jx[0] = fmaf(c.ns, v[0], fmaf(P[2], nv1, __fmul_rn(P[1], v[2])));
+    jx[1] = fmaf(c.s, v[0], fmaf(P[0], v[2], nv1));
+    jx[2] = fmaf(P[0], nv1, __fmul_rn(c.nb, v[2]));
+    jp[0] = fmaf(d, v[0], jp[0]);
+    jp[1] = fmaf(P[0], v[1], jp[1]);
+    jp[2] = fmaf(__fsub_rn(c.nr, P[2]), v[2], jp[2]);
+}
+
+// Reverse RK4 step from the shifted state x: the combination of adj_step below.
+__device__ __forceinline__ void lorenz_shift_adj(const float (&x)[3], float (&lam)[3], const LorenzShiftC& c,
+                                                 float* jp) {
+    float x2[3], x3[3], x4[3], d1, d2, d3;
+    lorenz_shift_stage(x, x, c.sh2, c.nh2, c.h2, c, x2, d1);
+    lorenz_shift_stage(x2, x, c.sh2, c.nh2, c.h2, c, x3, d2);
+    lorenz_shift_stage(x3, x, c.sh1, c.nh1, c.h1, c, x4, d3);
+    const float d4 = __fsub_rn(x4[1], x4[0]);
+    float l[3], m[3], sum[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) l[i] = __fmul_rn(c.h6, lam[i]);
+    lorenz_shift_vjp(x4, d4, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { sum[i] = m[i]; l[i] = fmaf(c.h3, lam[i], __fmul_rn(c.h1, m[i])); }
+    lorenz_shift_vjp(x3, d3, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { sum[i] = __fadd_rn(sum[i], m[i]); l[i] = fmaf(c.h3, lam[i], __fmul_rn(c.h2, m[i])); }
+    lorenz_shift_vjp(x2, d2, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { sum[i] = __fadd_rn(sum[i], m[i]); l[i] = fmaf(c.h6, lam[i], __fmul_rn(c.h2, m[i])); }
+    lorenz_shift_vjp(x, d1, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) lam[i] = __fadd_rn(lam[i], __fadd_rn(sum[i], m[i]));
+}
+
 template <class R, int METHOD>
 __device__ __forceinline__ void fwd_step(float (&x)[R::DIM], float h, const float* p) {
     constexpr int D = R::DIM;
@@ -288,6 +395,12 @@ __device__ __forceinline__ void fwd_step(float (&x)[R::DIM], float h, const floa
         R::f(x, p, k);
 #pragma unroll
         for (int i = 0; i < D; ++i) x[i] = fmaf(h, k[i], x[i]);
+        return;
+    }
+    if constexpr (IsLorenz<R>::value) {
+        LorenzShiftC c;
+        c.init(h, p);
+        lorenz_shift_fwd(x, c);
         return;
     }
     const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
@@ -336,6 +449,12 @@ __device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[
         Vjp<R>::apply(x, p, l, m, jp);
 #pragma unroll
         for (int i = 0; i < D; ++i) lam[i] = __fadd_rn(lam[i], m[i]);
+        return;
+    }
+    if constexpr (IsLorenz<R>::value) {
+        LorenzShiftC c;
+        c.init(h, p);
+        lorenz_shift_adj(x, lam, c, jp);
         return;
     }
     const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
@@ -426,6 +545,7 @@ __device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i
         float x[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) x[k] = (k < a.dim) ? ck[k * a.pitch + i] : 0.0f;
+        if constexpr (IsLorenz<R>::value && METHOD == FF_RK4) x[2] = __fsub_rn(x[2], p[1]);  // zt = z - r
         // sub-checkpoints every M steps (nothing to advance past the last one: a chunk of at
         // most M steps is recomputed once, by its only sub-segment)
         float cp[M][D];
@@ -523,80 +643,111 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
 // ---------------------------------------------------------------------------
 // Packed-pair adjoint for Lorenz RK4: two particles per thread in f32x2
 // registers (lane 0 particle 2t, lane 1 particle 2t + 1).  Every operation is
-// the scalar adjoint's, lane by lane (Lorenz::f, the RK4 step, Vjp<Lorenz> and
-// the reverse step; negations as 0 - x, which is exact), so dL/dx0 is the same
-// to the bit and the parameter sums differ only in their FP64 order.
+// the scalar adjoint's, lane by lane (the shifted step, stage points, Jacobian
+// products and reverse combination above), so dL/dx0 is the same to the bit
+// and the parameter sums differ only in their FP64 order.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ f2 neg2(f2 a) { return sub2(pack2(0.0f, 0.0f), a); }
 __device__ __forceinline__ f2 mul2a(f2 a, f2 b) {
     f2 r;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
     return r;
 }
 
-struct LorenzPairP {
-    f2 s, ns, r, nb;  // sigma, -sigma, r, -beta per lane
+// LorenzShiftC per lane (lane 0 and lane 1 may differ in r, with a per-particle
+// parameter, and in h, across a group boundary).
+struct LorenzPairS {
+    f2 s, ns, nb, nbr, nr, h1, h2, h3, h6, nh1, nh2, nh6, sh1, sh2, sh6;
 };
 
-__device__ __forceinline__ void lorenz_f2(const f2 (&x)[3], const LorenzPairP& c, f2 (&k)[3]) {
-    k[0] = mul2a(c.s, sub2(x[1], x[0]));
-    k[1] = fma2(x[0], sub2(c.r, x[2]), neg2(x[1]));
-    k[2] = fma2(x[0], x[1], mul2a(c.nb, x[2]));
+__device__ __forceinline__ LorenzPairS lorenz_pair(const LorenzShiftC& a, const LorenzShiftC& b) {
+    LorenzPairS c;
+    c.s = pack2(a.s, b.s);
+    c.ns = pack2(a.ns, b.ns);
+    c.nb = pack2(a.nb, b.nb);
+    c.nbr = pack2(a.nbr, b.nbr);
+    c.nr = pack2(a.nr, b.nr);
+    c.h1 = pack2(a.h1, b.h1);
+    c.h2 = pack2(a.h2, b.h2);
+    c.h3 = pack2(a.h3, b.h3);
+    c.h6 = pack2(a.h6, b.h6);
+    c.nh1 = pack2(a.nh1, b.nh1);
+    c.nh2 = pack2(a.nh2, b.nh2);
+    c.nh6 = pack2(a.nh6, b.nh6);
+    c.sh1 = pack2(a.sh1, b.sh1);
+    c.sh2 = pack2(a.sh2, b.sh2);
+    c.sh6 = pack2(a.sh6, b.sh6);
+    return c;
 }
 
-__device__ __forceinline__ void lorenz_fwd2(f2 (&x)[3], f2 h, f2 h2, f2 h6, const LorenzPairP& c) {
+// lorenz_shift_fwd lane by lane
+__device__ __forceinline__ void lorenz_fwd2(f2 (&x)[3], const LorenzPairS& c) {
     const f2 two = pack2(2.0f, 2.0f);
-    f2 k[3], xs[3], acc[3];
-    lorenz_f2(x, c, k);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) { acc[i] = k[i]; xs[i] = fma2(h2, k[i], x[i]); }
-    lorenz_f2(xs, c, k);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) { acc[i] = fma2(two, k[i], acc[i]); xs[i] = fma2(h2, k[i], x[i]); }
-    lorenz_f2(xs, c, k);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) { acc[i] = fma2(two, k[i], acc[i]); xs[i] = fma2(h, k[i], x[i]); }
-    lorenz_f2(xs, c, k);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) x[i] = fma2(h6, add2(acc[i], k[i]), x[i]);
+    f2 d, A, kz, X, Y, Z, a0, a1, a2;
+    d = sub2(x[1], x[0]);
+    A = fma2(x[0], x[2], x[1]);
+    kz = fma2(x[0], x[1], fma2(c.nb, x[2], c.nbr));
+    a0 = d; a1 = A; a2 = kz;
+    X = fma2(c.sh2, d, x[0]); Y = fma2(c.nh2, A, x[1]); Z = fma2(c.h2, kz, x[2]);
+    d = sub2(Y, X);
+    A = fma2(X, Z, Y);
+    kz = fma2(X, Y, fma2(c.nb, Z, c.nbr));
+    a0 = fma2(two, d, a0); a1 = fma2(two, A, a1); a2 = fma2(two, kz, a2);
+    X = fma2(c.sh2, d, x[0]); Y = fma2(c.nh2, A, x[1]); Z = fma2(c.h2, kz, x[2]);
+    d = sub2(Y, X);
+    A = fma2(X, Z, Y);
+    kz = fma2(X, Y, fma2(c.nb, Z, c.nbr));
+    a0 = fma2(two, d, a0); a1 = fma2(two, A, a1); a2 = fma2(two, kz, a2);
+    X = fma2(c.sh1, d, x[0]); Y = fma2(c.nh1, A, x[1]); Z = fma2(c.h1, kz, x[2]);
+    d = sub2(Y, X);
+    A = fma2(X, Z, Y);
+    kz = fma2(X, Y, fma2(c.nb, Z, c.nbr));
+    a0 = add2(a0, d); a1 = add2(a1, A); a2 = add2(a2, kz);
+    x[0] = fma2(c.sh6, a0, x[0]); x[1] = fma2(c.nh6, a1, x[1]); x[2] = fma2(c.h6, a2, x[2]);
 }
 
-// jx = J(x)^T v, jp += F_p(x)^T v (Vjp<Lorenz> lane by lane)
-__device__ __forceinline__ void lorenz_vjp2(const f2 (&x)[3], const LorenzPairP& c, const f2 (&v)[3], f2 (&jx)[3],
-                                            f2 (&jp)[3]) {
-    jx[0] = fma2(c.ns, v[0], fma2(sub2(c.r, x[2]), v[1], mul2a(x[1], v[2])));
-    jx[1] = fma2(c.s, v[0], fma2(x[0], v[2], neg2(v[1])));
-    jx[2] = fma2(neg2(x[0]), v[1], mul2a(c.nb, v[2]));
-    jp[0] = fma2(sub2(x[1], x[0]), v[0], jp[0]);
-    jp[1] = fma2(x[0], v[1], jp[1]);
-    jp[2] = fma2(neg2(x[2]), v[2], jp[2]);
+// lorenz_shift_stage lane by lane
+__device__ __forceinline__ void lorenz_stage2(const f2 (&P)[3], const f2 (&x)[3], f2 cs, f2 cn, f2 ch,
+                                              const LorenzPairS& c, f2 (&out)[3], f2& d) {
+    d = sub2(P[1], P[0]);
+    const f2 A = fma2(P[0], P[2], P[1]);
+    const f2 kz = fma2(P[0], P[1], fma2(c.nb, P[2], c.nbr));
+    out[0] = fma2(cs, d, x[0]);
+    out[1] = fma2(cn, A, x[1]);
+    out[2] = fma2(ch, kz, x[2]);
 }
 
-__device__ __forceinline__ void lorenz_adj2(const f2 (&x)[3], f2 (&lam)[3], f2 h, f2 h2, f2 h3, f2 h6,
-                                            const LorenzPairP& c, f2 (&jp)[3]) {
-    f2 k[3], x2[3], x3[3], x4[3];
-    lorenz_f2(x, c, k);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) x2[i] = fma2(h2, k[i], x[i]);
-    lorenz_f2(x2, c, k);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) x3[i] = fma2(h2, k[i], x[i]);
-    lorenz_f2(x3, c, k);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) x4[i] = fma2(h, k[i], x[i]);
+// lorenz_shift_vjp lane by lane (0 - v1 is the scalar's negation, also for a zero)
+__device__ __forceinline__ void lorenz_vjp2(const f2 (&P)[3], f2 d, const LorenzPairS& c, const f2 (&v)[3],
+                                            f2 (&jx)[3], f2 (&jp)[3]) {
+    const f2 nv1 = sub2(pack2(0.0f, 0.0f), v[1]);
+    jx[0] = fma2(c.ns, v[0], fma2(P[2], nv1, mul2a(P[1], v[2])));
+    jx[1] = fma2(c.s, v[0], fma2(P[0], v[2], nv1));
+    jx[2] = fma2(P[0], nv1, mul2a(c.nb, v[2]));
+    jp[0] = fma2(d, v[0], jp[0]);
+    jp[1] = fma2(P[0], v[1], jp[1]);
+    jp[2] = fma2(sub2(c.nr, P[2]), v[2], jp[2]);
+}
+
+// lorenz_shift_adj lane by lane
+__device__ __forceinline__ void lorenz_adj2(const f2 (&x)[3], f2 (&lam)[3], const LorenzPairS& c, f2 (&jp)[3]) {
+    f2 x2[3], x3[3], x4[3], d1, d2, d3;
+    lorenz_stage2(x, x, c.sh2, c.nh2, c.h2, c, x2, d1);
+    lorenz_stage2(x2, x, c.sh2, c.nh2, c.h2, c, x3, d2);
+    lorenz_stage2(x3, x, c.sh1, c.nh1, c.h1, c, x4, d3);
+    const f2 d4 = sub2(x4[1], x4[0]);
     f2 l[3], m[3], sum[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) l[i] = mul2a(h6, lam[i]);
-    lorenz_vjp2(x4, c, l, m, jp);
+    for (int i = 0; i < 3; ++i) l[i] = mul2a(c.h6, lam[i]);
+    lorenz_vjp2(x4, d4, c, l, m, jp);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { sum[i] = m[i]; l[i] = fma2(h3, lam[i], mul2a(h, m[i])); }
-    lorenz_vjp2(x3, c, l, m, jp);
+    for (int i = 0; i < 3; ++i) { sum[i] = m[i]; l[i] = fma2(c.h3, lam[i], mul2a(c.h1, m[i])); }
+    lorenz_vjp2(x3, d3, c, l, m, jp);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(h3, lam[i], mul2a(h2, m[i])); }
-    lorenz_vjp2(x2, c, l, m, jp);
+    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(c.h3, lam[i], mul2a(c.h2, m[i])); }
+    lorenz_vjp2(x2, d2, c, l, m, jp);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(h6, lam[i], mul2a(h2, m[i])); }
-    lorenz_vjp2(x, c, l, m, jp);
+    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(c.h6, lam[i], mul2a(c.h2, m[i])); }
+    lorenz_vjp2(x, d1, c, l, m, jp);
 #pragma unroll
     for (int i = 0; i < 3; ++i) lam[i] = add2(lam[i], add2(sum[i], m[i]));
 }
@@ -637,19 +788,16 @@ __global__ void __launch_bounds__(kLx2Block, 8) adjoint_lorenz_x2_kernel(const _
                 pa[q] = (PP && q == a.pidx) ? pv0 : ch.p[q];
                 pb[q] = (PP && q == a.pidx) ? pv1 : ch.p[q];
             }
-            LorenzPairP cp2;
-            cp2.s = pack2(pa[0], pb[0]);
-            cp2.ns = pack2(-pa[0], -pb[0]);
-            cp2.r = pack2(pa[1], pb[1]);
-            cp2.nb = pack2(-pa[2], -pb[2]);
-            const float ha = ch.gh[g0], hb = ch.gh[g1];
-            const f2 h = pack2(ha, hb), h2 = pack2(0.5f * ha, 0.5f * hb);
-            const f2 h3 = pack2(ha * (1.0f / 3.0f), hb * (1.0f / 3.0f)), h6 = pack2(ha * (1.0f / 6.0f), hb * (1.0f / 6.0f));
+            LorenzShiftC ca, cb;
+            ca.init(ch.gh[g0], pa);
+            cb.init(ch.gh[g1], pb);
+            const LorenzPairS cp2 = lorenz_pair(ca, cb);
             const int L = ch.n_steps;
             const float* ck = a.ckpt + (int64_t)ch.ckpt * a.dim * a.pitch;
             f2 x[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) x[k] = pack2(ck[k * a.pitch + i0], ck[k * a.pitch + i1]);  // pitch covers i1
+            x[2] = sub2(x[2], pack2(pa[1], pb[1]));  // zt = z - r
             f2 cpt[M][3];
             int nsub = 0;
             for (int base = 0; base < L; base += M, ++nsub) {
@@ -657,7 +805,7 @@ __global__ void __launch_bounds__(kLx2Block, 8) adjoint_lorenz_x2_kernel(const _
                 for (int k = 0; k < 3; ++k) cpt[nsub][k] = x[k];
                 const int nq = (base + M < L) ? M : 0;
 #pragma unroll 1
-                for (int r = 0; r < nq; ++r) lorenz_fwd2(x, h, h2, h6, cp2);
+                for (int r = 0; r < nq; ++r) lorenz_fwd2(x, cp2);
             }
             f2 jp[3] = {pack2(0.f, 0.f), pack2(0.f, 0.f), pack2(0.f, 0.f)};
             for (int sq = nsub - 1; sq >= 0; --sq) {
@@ -669,7 +817,7 @@ __global__ void __launch_bounds__(kLx2Block, 8) adjoint_lorenz_x2_kernel(const _
                     if (r < nq) {
 #pragma unroll
                         for (int k = 0; k < 3; ++k) st[r][k][tid] = x[k];
-                        if (r + 1 < nq) lorenz_fwd2(x, h, h2, h6, cp2);
+                        if (r + 1 < nq) lorenz_fwd2(x, cp2);
                     }
                 }
 #pragma unroll
@@ -678,7 +826,7 @@ __global__ void __launch_bounds__(kLx2Block, 8) adjoint_lorenz_x2_kernel(const _
                         f2 xr[3];
 #pragma unroll
                         for (int k = 0; k < 3; ++k) xr[k] = st[r][k][tid];
-                        lorenz_adj2(xr, lam, h, h2, h3, h6, cp2, jp);
+                        lorenz_adj2(xr, lam, cp2, jp);
                     }
             }
 #pragma unroll

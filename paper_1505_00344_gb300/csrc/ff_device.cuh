@@ -633,6 +633,15 @@ __device__ __forceinline__ void integrate_item(const IntegrateArgs& a, int64_t t
     }
 }
 
+// First item of this thread in a grid-stride loop of nb blocks (stride nb *
+// blockDim, items in runs of 32 per warp).  Runs go out warp-major -- warp k of
+// every block before warp k + 1 of any -- so the last, partial round of a
+// persistent grid spreads over all blocks and SMs instead of falling on the
+// first blocks whole.  Needs blockDim a multiple of 32.
+__device__ __forceinline__ int64_t warp_major_first(int64_t block_in_range, int64_t nb) {
+    return ((int64_t)(threadIdx.x >> 5) * nb + block_in_range) * 32 + (threadIdx.x & 31);
+}
+
 // Minimum resident blocks for a system's launch bound: R::MIN_BLOCKS where given, else 1.
 template <class R, class = void> struct MinBlocks { static constexpr int value = 1; };
 template <class R> struct MinBlocks<R, decltype((void)R::MIN_BLOCKS)> { static constexpr int value = R::MIN_BLOCKS; };
@@ -640,7 +649,7 @@ template <class R> struct MinBlocks<R, decltype((void)R::MIN_BLOCKS)> { static c
 template <class R, int METHOD, bool KAHAN, bool PP, int PPT, bool RESET = false>
 __global__ void __launch_bounds__(R::MAX_BLOCK, MinBlocks<R>::value) integrate_kernel(const __grid_constant__ IntegrateArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_vec; t += stride)
+    for (int64_t t = warp_major_first(blockIdx.x, gridDim.x); t < a.n_vec; t += stride)
         integrate_item<R, METHOD, KAHAN, PP, PPT, RESET>(a, t, (int)a.n_steps);
 }
 
@@ -717,7 +726,7 @@ __global__ void __launch_bounds__(512) lorenz_rk4_x2_kernel(const __grid_constan
     constexpr int PPT = 2 * NPAIR;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const f2 two = pack2(2.0f, 2.0f);
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_vec; t += stride) {
+    for (int64_t t = warp_major_first(blockIdx.x, gridDim.x); t < a.n_vec; t += stride) {
         const int64_t i0 = t * PPT;
         float xs[PPT], ys[PPT], zs[PPT];
         Vec<PPT>::load(a.x + i0, xs);
@@ -811,7 +820,7 @@ __global__ void __launch_bounds__(512) lorenz_rk4_x2u_kernel(const __grid_consta
     const float nbr_sys = -b * a.p[1];
     const f2 two = pack2(2.0f, 2.0f);
     const int64_t stride = nb * blockDim.x;
-    for (int64_t t = first + (int64_t)(blockIdx.x - a.gblk[g]) * blockDim.x + threadIdx.x; t < last; t += stride) {
+    for (int64_t t = first + warp_major_first(blockIdx.x - a.gblk[g], nb); t < last; t += stride) {
         const int64_t i0 = t * PPT;
         float xs[PPT], ys[PPT], zs[PPT], r[PPT];
         Vec<PPT>::load(a.x + i0, xs);

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(512) lorenz_rk4_kahan_x2u_kernel(const __grid_
     c.nb = pack2(-b, -b);
     const f2 two = pack2(2.0f, 2.0f);
     const int64_t stride = nb * blockDim.x;
-    for (int64_t t = first + (int64_t)(blockIdx.x - a.gblk[g]) * blockDim.x + threadIdx.x; t < last; t += stride) {
+    for (int64_t t = first + warp_major_first(blockIdx.x - a.gblk[g], nb); t < last; t += stride) {
         const int64_t i0 = t * PPT;
         float xs[PPT], ys[PPT], zs[PPT], cx[PPT], cy[PPT], cz[PPT], r[PPT];
         Vec<PPT>::load(a.x + i0, xs);

@@ -190,16 +190,19 @@ def _between(text, start, end):
 def kernel_source_hash():
     """Hash of the source the fused Lorenz integrator is compiled and launched from: its
     argument block, the vector loads, the packed-pair section, the group-uniform launch and the
-    warp-major item order of ff_device.cuh, the view/pixel rule and ff_integrate_lorenz.cu.  A profile taken on other
+    warp-major item order of ff_device.cuh, the view/pixel rule, ff_integrate_lorenz.cu and the
+    default launch shape in ff_api.cu.  A profile taken on other
     sources gives no traffic."""
     csrc = os.path.join(ROOT, "paper_1505_00344_gb300", "csrc")
     dev = open(os.path.join(csrc, "ff_device.cuh")).read()
     proj = open(os.path.join(csrc, "ff_project.cuh")).read()
+    api = open(os.path.join(csrc, "ff_api.cu")).read()
     parts = [_between(dev, "struct IntegrateArgs {", "\n};\n") ,
              _between(dev, "// Vector access of PPT consecutive floats.", "// Reset test and re-draw"),
              _between(dev, "// Packed-pair RK4 for Lorenz.", "// Host-side launch of one integrator"),
              _between(dev, "// Deal the persistent grid's blocks out to the groups", "inline cudaError_t launch_variants("),
              _between(dev, "// First item of this thread in a grid-stride loop", "// Minimum resident blocks"),
+             _between(api, "const bool packed_lorenz", "s->blocks_per_sm"),  # default launch shape
              _between(proj, "struct ViewArgs {", "// Continuous pixel coordinates"),
              open(os.path.join(csrc, "ff_integrate_lorenz.cu")).read()]
     h = hashlib.sha256()

@@ -285,9 +285,10 @@ ff_status ff_system_info(ff_system* sys, int64_t* n_particles, int64_t* pitch, i
  * each plane is read with one 8- or 16-byte access, and RK4 on Lorenz, plain or
  * compensated, then runs two particles per packed f32x2 instruction; the
  * default is 4 for RK4 on Lorenz and 1 otherwise; 0 keeps the current value),
- * threads per block (a multiple of 32 up to 1024, default 256, 0 keeps the
- * current value; clamped to the kernel's maximum, 512 for the 2- and
- * 3-dimensional systems and 256 for LINEAR and HH3), resident blocks per
+ * threads per block (a multiple of 32 up to 1024, default 512 for RK4 on
+ * Lorenz and 256 otherwise, 0 keeps the current value; clamped to the kernel's
+ * maximum, 512 for the 2- and 3-dimensional systems and 256 for LINEAR and
+ * HH3), resident blocks per
  * SM of the persistent grid (0 = as many as fit), and the most steps per
  * launch (0 = all steps of an ff_step call in one launch; launches are also
  * split at 2^30 steps).  Errors: FF_ERR_INVALID_ARG for values out of range. */

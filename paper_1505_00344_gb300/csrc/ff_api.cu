@@ -137,8 +137,9 @@ ff_status ff_create_system(int rhs_id, int dim, const double* params, int n_para
         return st;
     }
     // default launch shape: plain RK4 on Lorenz runs packed pairs, 4 particles per thread
-    s->ppt = (rhs_id == FF_RHS_LORENZ && method == FF_RK4) ? 4 : 1;  // packed pairs, plain or compensated
-    s->block = 256;
+    const bool packed_lorenz = rhs_id == FF_RHS_LORENZ && method == FF_RK4;
+    s->ppt = packed_lorenz ? 4 : 1;  // packed pairs, plain or compensated
+    s->block = packed_lorenz ? 512 : 256;
     *out = s;
     return FF_OK;
 }

@@ -288,7 +288,8 @@ ff_status ff_system_info(ff_system* sys, int64_t* n_particles, int64_t* pitch, i
  * threads per block (a multiple of 32 up to 1024, default 512 for RK4 on
  * Lorenz and 256 otherwise, 0 keeps the current value; clamped to the kernel's
  * maximum, 512 for the 2- and 3-dimensional systems and 256 for LINEAR and
- * HH3), resident blocks per
+ * HH3, and narrowed in whole warps when the particles would not give every SM
+ * a block, so that a small ensemble spreads over all SMs), resident blocks per
  * SM of the persistent grid (0 = as many as fit), and the most steps per
  * launch (0 = all steps of an ff_step call in one launch; launches are also
  * split at 2^30 steps).  Errors: FF_ERR_INVALID_ARG for values out of range. */

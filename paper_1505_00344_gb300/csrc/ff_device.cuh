@@ -905,6 +905,17 @@ cudaError_t launch_integrate_linear(int rhs_id, int method, bool kahan, bool pp,
                                     const IntegrateArgs& a, const LaunchShape& shape,
                                     cudaStream_t stream);
 
+// Block size for work too small to give every SM a block: narrowed, in whole
+// warps down to one, until the blocks cover the SMs.  A small ensemble then runs
+// one or a few warps per SM instead of crowding a few SMs, whose sub-partitions
+// would share their MUFU and FP32 pipes between the warps of one step chain.
+inline int spread_block(int block, int64_t items, int num_sms) {
+    if (num_sms < 1 || items >= (int64_t)block * num_sms) return block;
+    const int64_t per_sm = (items + num_sms - 1) / num_sms;
+    const int64_t b = (per_sm + 31) / 32 * 32;
+    return b < 32 ? 32 : (b < block ? (int)b : block);
+}
+
 // Grid for a persistent launch: enough blocks to cover the work, at most
 // blocks_per_sm (or the occupancy limit) per SM.  The block size is clamped to
 // the kernel's compiled maximum (its launch bound).
@@ -916,6 +927,7 @@ inline cudaError_t persistent_launch(Kernel kernel, const IntegrateArgs& a, cons
     cudaError_t e = cudaFuncGetAttributes(&attr, kernel);
     if (e != cudaSuccess) return e;
     if (s.block > attr.maxThreadsPerBlock) s.block = attr.maxThreadsPerBlock / 32 * 32;
+    s.block = spread_block(s.block, a.n_vec, s.num_sms);
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, s.block, 0);
     if (e != cudaSuccess) return e;
@@ -976,16 +988,17 @@ inline cudaError_t uniform_launch(Kernel kernel, const IntegrateArgs& a0, const 
     cudaError_t e = cudaFuncGetAttributes(&attr, kernel);
     if (e != cudaSuccess) return e;
     if (s.block > attr.maxThreadsPerBlock) s.block = attr.maxThreadsPerBlock / 32 * 32;
+    IntegrateArgs a = a0;
+    const int ppt = s.ppt;
+    int64_t items_all = 0;
+    for (int g = 0; g < a.n_groups; ++g) items_all += (a.gend[g] - a.gstart[g]) / ppt;
+    s.block = spread_block(s.block, items_all, s.num_sms);
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, s.block, 0);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int per_sm = (s.blocks_per_sm > 0 && s.blocks_per_sm < occ) ? s.blocks_per_sm : occ;
     const int64_t total = (int64_t)per_sm * s.num_sms;
-    IntegrateArgs a = a0;
-    const int ppt = s.ppt;
-    int64_t items_all = 0;
-    for (int g = 0; g < a.n_groups; ++g) items_all += (a.gend[g] - a.gstart[g]) / ppt;
     int next = 0;
     for (int g = 0; g < a.n_groups; ++g) {
         const int64_t items = (a.gend[g] - a.gstart[g]) / ppt;

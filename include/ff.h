@@ -303,7 +303,9 @@ ff_status ff_set_launch(ff_system* sys, int particles_per_thread, int block, int
  * stores a checkpoint of the state every checkpoint_every steps (1..256) and
  * whenever the parameters or dt changed since the last checkpoint, up to
  * max_steps steps in total; the checkpoints take
- * (ceil(max_steps / checkpoint_every) + 16) * dim * pitch floats.  Every
+ * (ceil(max_steps / checkpoint_every) + 16) * dim * pitch floats (a later
+ * ff_tape_begin reuses them when they are enough; ff_tape_end releases them).
+ * The integrator writes the checkpoints inside its launches.  Every
  * system has an adjoint; FF_ERR_UNSUPPORTED while particle reset is on (a
  * re-draw is not differentiable).  ff_reset and ff_set_state end the tape.
  * Errors: FF_ERR_INVALID_ARG for checkpoint_every outside 1..256 or

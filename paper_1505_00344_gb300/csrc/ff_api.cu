@@ -452,7 +452,15 @@ void account_steps(ff_system* s, int64_t n_steps, double dt) {
 
 extern "C" {
 
-static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const ff::ViewArgs* fuse = nullptr) {
+// Checkpoints of a taped call: before step first + k * every of the call (k < count)
+// the state goes to checkpoint slot slot0 + k.
+struct TapePlan {
+    int64_t first, every, count;
+    int slot0;
+};
+
+static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const ff::ViewArgs* fuse = nullptr,
+                                 const TapePlan* tape = nullptr) {
     ff::IntegrateArgs a{};
     ff::fill_integrate_args(s, dt, &a);
     const int ppt = s->ppt;
@@ -477,6 +485,20 @@ static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const
         if (chunk > ((int64_t)1 << 30)) chunk = (int64_t)1 << 30;  // kernels count steps in 32 bits
         a.n_steps = chunk;
         a.step0 = s->steps_total;
+        a.ckpt = nullptr;
+        if (tape && tape->count > 0) {
+            // the plan's first checkpoint at or after this launch's first step
+            const int64_t done = n_steps - left;
+            const int64_t k0 = done <= tape->first ? 0 : (done - tape->first + tape->every - 1) / tape->every;
+            const int64_t at = tape->first + k0 * tape->every;
+            if (k0 < tape->count && at < done + chunk) {
+                a.ckpt = s->d_ckpt;
+                a.ck_stride = (int64_t)s->dim * s->pitch;
+                a.ck_first = (int)(at - done);
+                a.ck_every = (int)tape->every;
+                a.ck_slot0 = tape->slot0 + (int)k0;
+            }
+        }
         cudaError_t e;
         if (fuse && chunk == left) {
             a.view = *fuse;
@@ -491,36 +513,33 @@ static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const
     return FF_OK;
 }
 
-// Taped stepping: checkpoint the state at every chunk start; a chunk ends after
-// tape_every steps or when the parameters or dt change.
+// Taped stepping: a checkpoint of the state at the start of every chunk; a chunk
+// ends after tape_every steps or when the parameters or dt change.  The integrator
+// writes the checkpoints inside its launches (run_steps), so a call is as many
+// launches as an untaped one.  The tape's capacity is checked before any step.
 static ff_status taped_steps(ff_system* s, int64_t n_steps, double dt) {
-    int64_t left = n_steps;
-    while (left > 0) {
-        const bool need_new = s->chunks.empty() || s->chunks.back().n_steps >= s->tape_every ||
-                              s->chunk_version != s->params_version || s->chunk_dt != dt;
-        if (need_new) {
-            if ((int64_t)s->chunks.size() >= s->tape_slots)
-                return fail(FF_ERR_STATE, "ff_step: the tape is full (raise max_steps in ff_tape_begin)");
-            ff::AdjChunk c{};
-            c.n_steps = 0;
-            c.ckpt = (int)s->chunks.size();
-            for (int q = 0; q < s->n_params; ++q) c.p[kernel_param_index(s, q)] = (float)s->params[q];
-            for (int g = 0; g < s->n_groups; ++g) c.gh[g] = (float)(s->groups[g].direction * dt);
-            const size_t bytes = sizeof(float) * (size_t)s->pitch * s->dim;
-            cudaError_t e = cudaMemcpyAsync(s->d_ckpt + (int64_t)c.ckpt * s->dim * s->pitch, s->d_state, bytes,
-                                            cudaMemcpyDeviceToDevice, s->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "ff_step: checkpoint copy");
-            s->chunks.push_back(c);
-            s->chunk_version = s->params_version;
-            s->chunk_dt = dt;
-        }
-        int64_t take = s->tape_every - s->chunks.back().n_steps;
-        if (take > left) take = left;
-        ff_status st = integrate_steps(s, take, dt);
-        if (st != FF_OK) return st;
-        s->chunks.back().n_steps += (int)take;
-        left -= take;
+    const bool open = !s->chunks.empty() && s->chunk_version == s->params_version && s->chunk_dt == dt;
+    int64_t cont = open ? s->tape_every - s->chunks.back().n_steps : 0;  // steps left in the open chunk
+    if (cont > n_steps) cont = n_steps;
+    const int64_t rest = n_steps - cont;
+    const int64_t fresh = (rest + s->tape_every - 1) / s->tape_every;  // chunks this call starts
+    if ((int64_t)s->chunks.size() + fresh > s->tape_slots)
+        return fail(FF_ERR_STATE, "ff_step: the tape is full (raise max_steps in ff_tape_begin)");
+    const TapePlan plan{cont, s->tape_every, fresh, (int)s->chunks.size()};
+    ff_status st = integrate_steps(s, n_steps, dt, nullptr, &plan);
+    if (st != FF_OK) return st;
+    if (cont > 0) s->chunks.back().n_steps += (int)cont;
+    for (int64_t k = 0; k < fresh; ++k) {
+        ff::AdjChunk c{};
+        c.ckpt = plan.slot0 + (int)k;
+        const int64_t left = rest - k * s->tape_every;
+        c.n_steps = (int)(left < s->tape_every ? left : s->tape_every);
+        for (int q = 0; q < s->n_params; ++q) c.p[kernel_param_index(s, q)] = (float)s->params[q];
+        for (int g = 0; g < s->n_groups; ++g) c.gh[g] = (float)(s->groups[g].direction * dt);
+        s->chunks.push_back(c);
     }
+    s->chunk_version = s->params_version;
+    s->chunk_dt = dt;
     return FF_OK;
 }
 
@@ -547,6 +566,7 @@ static void free_tape(ff_system* s) {
     s->d_chunks = nullptr;
     s->d_partial = nullptr;
     s->d_dp = nullptr;
+    s->ckpt_capacity = 0;
     s->chunks.clear();
     s->tape_on = false;
 }
@@ -562,18 +582,25 @@ ff_status ff_tape_begin(ff_system* s, int64_t checkpoint_every, int64_t max_step
     if (s->n_particles < 1) return fail(FF_ERR_STATE, "ff_tape_begin: no particles seeded");
     DeviceScope dev(s->device);
     if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_tape_begin: set device");
-    cudaError_t e = cudaStreamSynchronize(s->stream);  // earlier work may still read the old tape
-    if (e != cudaSuccess) return cuda_fail(e, "ff_tape_begin: synchronise");
-    free_tape(s);
     const int64_t slots = (max_steps + checkpoint_every - 1) / checkpoint_every + 16;
-    s->partial_blocks = ff::adjoint_partial_rows(s->num_sms);
-    e = cudaMalloc(&s->d_ckpt, sizeof(float) * (size_t)slots * s->dim * s->pitch);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_chunks, sizeof(ff::AdjChunk) * (size_t)slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_partial, sizeof(double) * (size_t)s->partial_blocks * FF_MAX_PARAMS);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_dp, sizeof(double) * FF_MAX_PARAMS);
-    if (e != cudaSuccess) {
+    if (s->d_ckpt && s->ckpt_capacity >= slots) {
+        // the previous tape's buffers are large enough: reuse them (work that still reads
+        // them is ordered before the new tape's steps on the system's stream)
+        s->chunks.clear();
+    } else {
+        cudaError_t e = cudaStreamSynchronize(s->stream);  // earlier work may still read the old tape
+        if (e != cudaSuccess) return cuda_fail(e, "ff_tape_begin: synchronise");
         free_tape(s);
-        return cuda_fail(e, "ff_tape_begin: allocation");
+        s->partial_blocks = ff::adjoint_partial_rows(s->num_sms);
+        e = cudaMalloc(&s->d_ckpt, sizeof(float) * (size_t)slots * s->dim * s->pitch);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_chunks, sizeof(ff::AdjChunk) * (size_t)slots);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_partial, sizeof(double) * (size_t)s->partial_blocks * FF_MAX_PARAMS);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_dp, sizeof(double) * FF_MAX_PARAMS);
+        if (e != cudaSuccess) {
+            free_tape(s);
+            return cuda_fail(e, "ff_tape_begin: allocation");
+        }
+        s->ckpt_capacity = slots;
     }
     s->tape_every = checkpoint_every;
     s->tape_slots = slots;

@@ -64,7 +64,46 @@ struct IntegrateArgs {
     // fused projection + splat after the last step (group-uniform packed Lorenz kernel only)
     int64_t n_real;                  // seeded particles (the rest are padding)
     ViewArgs view;
+    // taped runs: before step ck_first + k * ck_every of this launch (k = 0, 1, ... while below
+    // n_steps) the state is written to checkpoint slot ck_slot0 + k; ckpt null: no checkpoints
+    float* ckpt;                     // slot q at ckpt + q * ck_stride (dim planes of pitch floats)
+    int64_t ck_stride;
+    int ck_first, ck_every, ck_slot0, ck_pad_;
 };
+
+// Checkpoint slot for the state as the launch loads it (a chunk that starts with
+// the launch), or null.  The kernels write it before any step or change of form.
+__device__ __forceinline__ float* start_checkpoint(const IntegrateArgs& a) {
+    return (a.ckpt && a.ck_first == 0) ? a.ckpt + (int64_t)a.ck_slot0 * a.ck_stride : nullptr;
+}
+
+// The step loop of one launch.  step() advances the state one step; before each
+// later checkpoint step of a taped run, save(slot) writes the state to its slot
+// in the form, and with the roundings, of a launch that ends there followed by
+// one that starts there, so a taped run passes through the states of a run split
+// into launches at its checkpoints.
+// TAPE false compiles the checkpoints out (kernels that never run taped).
+template <int UNROLL, bool TAPE = true, class Step, class Save>
+__device__ __forceinline__ void run_steps(const IntegrateArgs& a, int n_steps, Step&& step, Save&& save) {
+    if constexpr (!TAPE) {
+#pragma unroll UNROLL
+        for (int s = 0; s < n_steps; ++s) step();
+        return;
+    }
+    const bool at0 = a.ckpt && a.ck_first == 0;  // written at load (start_checkpoint)
+    int next = a.ckpt ? (at0 ? a.ck_every : a.ck_first) : n_steps;
+    int slot = a.ck_slot0 + (at0 ? 1 : 0);
+    int s = 0;
+    for (;;) {
+        const int end = next < n_steps ? next : n_steps;
+#pragma unroll UNROLL
+        for (; s < end; ++s) step();
+        if (s >= n_steps) break;
+        save(slot);
+        ++slot;
+        next += a.ck_every;
+    }
+}
 
 // Reset data of a system, in device memory (read only when a particle resets).
 struct ResetTable {
@@ -555,6 +594,7 @@ __device__ __forceinline__ void integrate_item(const IntegrateArgs& a, int64_t t
             x[j][k] = v[j];
             c[j][k] = KAHAN ? w[j] : 0.f;
         }
+        if (float* ck0 = start_checkpoint(a); ck0 && k < a.dim) Vec<PPT>::store(ck0 + k * a.pitch + i0, v);
     }
     float prm[PPT][R::NP];
     Stepper st[PPT];
@@ -606,14 +646,25 @@ __device__ __forceinline__ void integrate_item(const IntegrateArgs& a, int64_t t
             for (int j = 0; j < PPT; ++j) reset_check<D>(a, st[j], x[j], c[j], age[j], nres[j], grp[j], i0 + j);
         }
     };
-    if constexpr (D > 8) {
-        // a step of a large system is long enough on its own; unrolling only grows the code
-#pragma unroll 1
-        for (int s = 0; s < n_steps; ++s) step();
-    } else {
-#pragma unroll 4
-        for (int s = 0; s < n_steps; ++s) step();
-    }
+    auto save = [&](int slot) {
+        // the end of a launch (back from the stepper's internal form) and the start of the next
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) st[j].from_internal(x[j]);
+        float* ck = a.ckpt + (int64_t)slot * a.ck_stride;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (k < a.dim) {
+                float v[PPT];
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) v[j] = x[j][k];
+                Vec<PPT>::store(ck + k * a.pitch + i0, v);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) st[j].to_internal(x[j]);
+    };
+    // a step of a large system is long enough on its own; unrolling only grows the code
+    run_steps<(D > 8) ? 1 : 4>(a, n_steps, step, save);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
         st[j].from_internal(x[j]);
@@ -733,6 +784,11 @@ __global__ void __launch_bounds__(512) lorenz_rk4_x2_kernel(const __grid_constan
         Vec<PPT>::load(a.x + i0, xs);
         Vec<PPT>::load(a.x + a.pitch + i0, ys);
         Vec<PPT>::load(a.x + 2 * a.pitch + i0, zs);
+        if (float* ck0 = start_checkpoint(a)) {
+            Vec<PPT>::store(ck0 + i0, xs);
+            Vec<PPT>::store(ck0 + a.pitch + i0, ys);
+            Vec<PPT>::store(ck0 + 2 * a.pitch + i0, zs);
+        }
         float h[PPT], sg[PPT], r[PPT], b[PPT];
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
@@ -768,12 +824,27 @@ __global__ void __launch_bounds__(512) lorenz_rk4_x2_kernel(const __grid_constan
             c[q].nb = pack2(-b[u], -b[v]);
             c[q].nbr = pack2(-b[u] * r[u], -b[v] * r[v]);
         }
-        const int n_steps = (int)a.n_steps;
-#pragma unroll 2
-        for (int s = 0; s < n_steps; ++s) {
+        auto save = [&](int slot) {
+            float* ck = a.ckpt + (int64_t)slot * a.ck_stride;
+            float cx[PPT], cy[PPT], cz[PPT];
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) {
+                const int u = 2 * q, v = 2 * q + 1;
+                unpack2(X[q], cx[u], cx[v]);
+                unpack2(Y[q], cy[u], cy[v]);
+                unpack2(Z[q], cz[u], cz[v]);
+                cz[u] = cz[u] + r[u];
+                cz[v] = cz[v] + r[v];
+                Z[q] = pack2(cz[u] - r[u], cz[v] - r[v]);
+            }
+            Vec<PPT>::store(ck + i0, cx);
+            Vec<PPT>::store(ck + a.pitch + i0, cy);
+            Vec<PPT>::store(ck + 2 * a.pitch + i0, cz);
+        };
+        run_steps<2>(a, (int)a.n_steps, [&]() {
 #pragma unroll
             for (int q = 0; q < NPAIR; ++q) lorenz_rk4_pair(X[q], Y[q], Z[q], c[q], two);
-        }
+        }, save);
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
             const int u = 2 * q, v = 2 * q + 1;
@@ -828,6 +899,11 @@ __global__ void __launch_bounds__(512) lorenz_rk4_x2u_kernel(const __grid_consta
         Vec<PPT>::load(a.x + a.pitch + i0, ys);
         Vec<PPT>::load(a.x + 2 * a.pitch + i0, zs);
         if (PP_R) Vec<PPT>::load(a.pparam + i0, r);
+        if (float* ck0 = SPLAT ? nullptr : start_checkpoint(a)) {  // the fused frame is never taped
+            Vec<PPT>::store(ck0 + i0, xs);
+            Vec<PPT>::store(ck0 + a.pitch + i0, ys);
+            Vec<PPT>::store(ck0 + 2 * a.pitch + i0, zs);
+        }
         f2 X[NPAIR], Y[NPAIR], Z[NPAIR], NBR[NPAIR];
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
@@ -838,16 +914,32 @@ __global__ void __launch_bounds__(512) lorenz_rk4_x2u_kernel(const __grid_consta
             Z[q] = pack2(zs[u] - ru, zs[v] - rv);
             NBR[q] = PP_R ? pack2(-b * ru, -b * rv) : pack2(nbr_sys, nbr_sys);
         }
-        const int n_steps = (int)a.n_steps;
-#pragma unroll 2
-        for (int s = 0; s < n_steps; ++s) {
+        auto save = [&](int slot) {
+            float* ck = a.ckpt + (int64_t)slot * a.ck_stride;
+            float cx[PPT], cy[PPT], cz[PPT];
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) {
+                const int u = 2 * q, v = 2 * q + 1;
+                const float ru = PP_R ? r[u] : a.p[1], rv = PP_R ? r[v] : a.p[1];
+                unpack2(X[q], cx[u], cx[v]);
+                unpack2(Y[q], cy[u], cy[v]);
+                unpack2(Z[q], cz[u], cz[v]);
+                cz[u] = cz[u] + ru;
+                cz[v] = cz[v] + rv;
+                Z[q] = pack2(cz[u] - ru, cz[v] - rv);
+            }
+            Vec<PPT>::store(ck + i0, cx);
+            Vec<PPT>::store(ck + a.pitch + i0, cy);
+            Vec<PPT>::store(ck + 2 * a.pitch + i0, cz);
+        };
+        run_steps<2, !SPLAT>(a, (int)a.n_steps, [&]() {
 #pragma unroll
             for (int q = 0; q < NPAIR; ++q) {
                 LorenzPairConsts cq = c;
                 cq.nbr = NBR[q];
                 lorenz_rk4_pair(X[q], Y[q], Z[q], cq, two);
             }
-        }
+        }, save);
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
             const int u = 2 * q, v = 2 * q + 1;

@@ -84,6 +84,11 @@ __global__ void __launch_bounds__(512) lorenz_rk4_kahan_x2u_kernel(const __grid_
         Vec<PPT>::load(a.comp + a.pitch + i0, cy);
         Vec<PPT>::load(a.comp + 2 * a.pitch + i0, cz);
         if (PP_R) Vec<PPT>::load(a.pparam + i0, r);
+        if (float* ck0 = start_checkpoint(a)) {
+            Vec<PPT>::store(ck0 + i0, xs);
+            Vec<PPT>::store(ck0 + a.pitch + i0, ys);
+            Vec<PPT>::store(ck0 + 2 * a.pitch + i0, zs);
+        }
         f2 X[NPAIR], Y[NPAIR], Z[NPAIR], NCX[NPAIR], NCY[NPAIR], NCZ[NPAIR], R[NPAIR];
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
@@ -96,12 +101,24 @@ __global__ void __launch_bounds__(512) lorenz_rk4_kahan_x2u_kernel(const __grid_
             NCZ[q] = pack2(-cz[u], -cz[v]);
             R[q] = PP_R ? pack2(r[u], r[v]) : pack2(a.p[1], a.p[1]);
         }
-        const int n_steps = (int)a.n_steps;
-#pragma unroll 2
-        for (int s = 0; s < n_steps; ++s) {
+        auto save = [&](int slot) {
+            // the state is kept unshifted; the compensation stays in registers
+            float* ck = a.ckpt + (int64_t)slot * a.ck_stride;
+            float sx[PPT], sy[PPT], sz[PPT];
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) {
+                unpack2(X[q], sx[2 * q], sx[2 * q + 1]);
+                unpack2(Y[q], sy[2 * q], sy[2 * q + 1]);
+                unpack2(Z[q], sz[2 * q], sz[2 * q + 1]);
+            }
+            Vec<PPT>::store(ck + i0, sx);
+            Vec<PPT>::store(ck + a.pitch + i0, sy);
+            Vec<PPT>::store(ck + 2 * a.pitch + i0, sz);
+        };
+        run_steps<2>(a, (int)a.n_steps, [&]() {
 #pragma unroll
             for (int q = 0; q < NPAIR; ++q) lorenz_rk4_pair_kahan(X[q], Y[q], Z[q], NCX[q], NCY[q], NCZ[q], R[q], c, two);
-        }
+        }, save);
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
             const int u = 2 * q, v = 2 * q + 1;

@@ -94,6 +94,7 @@ struct ff_system {
     // adjoint tape
     bool tape_on = false;
     int64_t tape_every = 0, tape_slots = 0;
+    int64_t ckpt_capacity = 0;  // checkpoint slots allocated (kept across tapes)
     float* d_ckpt = nullptr;
     ff::AdjChunk* d_chunks = nullptr;
     double* d_partial = nullptr;

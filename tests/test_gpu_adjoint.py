@@ -189,6 +189,46 @@ def test_autograd_function():
     check(p.grad.numpy(), dp_ref)
 
 
+@pytest.mark.parametrize("ppt,kahan", [(1, False), (4, False), (4, True)])
+def test_checkpoints_inside_launches_match_split_launches(ppt, kahan):
+    """The integrator writes a taped run's checkpoints inside its launches, re-basing
+    there as a launch boundary would: one 95-step call and the same steps as calls of
+    one chunk each give the same states, checkpoints and gradients, bit for bit; so do
+    launches capped at 7 steps and calls of 7 steps (checkpoints inside launches)."""
+    box = ([-20, -20, 0], [20, 20, 40])
+    groups = [G(1000, *box, 1, 11), G(24, *box, -1, 12)]
+    P = sum(g["count"] for g in groups)
+
+    def run(calls, max_steps=0):
+        s = ff.System("lorenz", LORENZ_PARAMS, P, kahan=kahan, stream=torch.cuda.current_stream().cuda_stream)
+        for g in groups:
+            s.seed(g["count"], g["lo"], g["hi"], g["direction"], g["seed"])
+        s.set_launch(ppt, 0, 0, max_steps)
+        s.tape_begin(10, 200)
+        for n in calls:
+            s.step(n, 0.001)
+        xT = torch.empty((3, P), dtype=torch.float32, device="cuda")
+        s.get_state(xT)
+        g = xT - 1.0
+        dx0 = torch.empty_like(g)
+        dp = s.backward(g, dx0, 3)
+        torch.cuda.synchronize()
+        return xT.cpu().numpy(), dx0.cpu().numpy(), np.asarray(dp)
+
+    one = run([95])
+    split = run([10] * 9 + [5])
+    np.testing.assert_array_equal(one[0], split[0])
+    np.testing.assert_array_equal(one[1], split[1])
+    np.testing.assert_allclose(one[2], split[2], rtol=1e-12)
+    capped = run([95], max_steps=7)
+    sevens = run([7] * 13 + [4])
+    np.testing.assert_array_equal(capped[0], sevens[0])
+    np.testing.assert_array_equal(capped[1], sevens[1])
+    np.testing.assert_allclose(capped[2], sevens[2], rtol=1e-12)
+    # re-basing at other places changes only roundings
+    assert np.abs(capped[0] - one[0]).max() <= 1e-4 * np.abs(one[0]).max()
+
+
 def test_tape_errors():
     s = build("lorenz", LORENZ_PARAMS, [G(64, [0, 0, 0], [1, 1, 1], 1, 1)], 3)
     g = torch.zeros((3, 64), device="cuda")

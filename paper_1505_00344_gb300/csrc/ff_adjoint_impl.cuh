@@ -292,7 +292,7 @@ template <class R> struct IsLorenz { static constexpr bool value = false; };
 template <> struct IsLorenz<Lorenz> { static constexpr bool value = true; };
 
 struct LorenzShiftC {
-    float s, ns, nb, nbr, nr, h1, h2, h3, h6, nh1, nh2, nh6, sh1, sh2, sh6;
+    float s, ns, nb, nbr, nr, h1, h2, h6, nh1, nh2, nh6, sh1, sh2, sh6;
     __device__ __forceinline__ void init(float h, const float* p) {
         s = p[0];
         ns = -p[0];
@@ -301,7 +301,6 @@ struct LorenzShiftC {
         nr = -p[1];
         h1 = h;
         h2 = __fmul_rn(0.5f, h);
-        h3 = __fmul_rn(h, 1.0f / 3.0f);
         h6 = __fmul_rn(h, 1.0f / 6.0f);
         nh1 = -h1;
         nh2 = -h2;
@@ -370,18 +369,19 @@ __device__ __forceinline__ void lorenz_shift_adj(const float (&x)[3], float (&la
     lorenz_shift_stage(x2, x, c.sh2, c.nh2, c.h2, c, x3, d2);
     lorenz_shift_stage(x3, x, c.sh1, c.nh1, c.h1, c, x4, d3);
     const float d4 = __fsub_rn(x4[1], x4[0]);
-    float l[3], m[3], sum[3];
+    // u = h/6 lambda and 2u (= h/3 lambda rounded once) are the lambda terms of every l
+    float u[3], u2[3], l[3], m[3], sum[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) l[i] = __fmul_rn(c.h6, lam[i]);
-    lorenz_shift_vjp(x4, d4, c, l, m, jp);
+    for (int i = 0; i < 3; ++i) { u[i] = __fmul_rn(c.h6, lam[i]); u2[i] = __fadd_rn(u[i], u[i]); }
+    lorenz_shift_vjp(x4, d4, c, u, m, jp);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { sum[i] = m[i]; l[i] = fmaf(c.h3, lam[i], __fmul_rn(c.h1, m[i])); }
+    for (int i = 0; i < 3; ++i) { sum[i] = m[i]; l[i] = fmaf(c.h1, m[i], u2[i]); }
     lorenz_shift_vjp(x3, d3, c, l, m, jp);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { sum[i] = __fadd_rn(sum[i], m[i]); l[i] = fmaf(c.h3, lam[i], __fmul_rn(c.h2, m[i])); }
+    for (int i = 0; i < 3; ++i) { sum[i] = __fadd_rn(sum[i], m[i]); l[i] = fmaf(c.h2, m[i], u2[i]); }
     lorenz_shift_vjp(x2, d2, c, l, m, jp);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { sum[i] = __fadd_rn(sum[i], m[i]); l[i] = fmaf(c.h6, lam[i], __fmul_rn(c.h2, m[i])); }
+    for (int i = 0; i < 3; ++i) { sum[i] = __fadd_rn(sum[i], m[i]); l[i] = fmaf(c.h2, m[i], u[i]); }
     lorenz_shift_vjp(x, d1, c, l, m, jp);
 #pragma unroll
     for (int i = 0; i < 3; ++i) lam[i] = __fadd_rn(lam[i], __fadd_rn(sum[i], m[i]));
@@ -656,7 +656,7 @@ __device__ __forceinline__ f2 mul2a(f2 a, f2 b) {
 // LorenzShiftC per lane (lane 0 and lane 1 may differ in r, with a per-particle
 // parameter, and in h, across a group boundary).
 struct LorenzPairS {
-    f2 s, ns, nb, nbr, nr, h1, h2, h3, h6, nh1, nh2, nh6, sh1, sh2, sh6;
+    f2 s, ns, nb, nbr, nr, h1, h2, h6, nh1, nh2, nh6, sh1, sh2, sh6;
 };
 
 __device__ __forceinline__ LorenzPairS lorenz_pair(const LorenzShiftC& a, const LorenzShiftC& b) {
@@ -668,7 +668,6 @@ __device__ __forceinline__ LorenzPairS lorenz_pair(const LorenzShiftC& a, const 
     c.nr = pack2(a.nr, b.nr);
     c.h1 = pack2(a.h1, b.h1);
     c.h2 = pack2(a.h2, b.h2);
-    c.h3 = pack2(a.h3, b.h3);
     c.h6 = pack2(a.h6, b.h6);
     c.nh1 = pack2(a.nh1, b.nh1);
     c.nh2 = pack2(a.nh2, b.nh2);
@@ -735,18 +734,18 @@ __device__ __forceinline__ void lorenz_adj2(const f2 (&x)[3], f2 (&lam)[3], cons
     lorenz_stage2(x2, x, c.sh2, c.nh2, c.h2, c, x3, d2);
     lorenz_stage2(x3, x, c.sh1, c.nh1, c.h1, c, x4, d3);
     const f2 d4 = sub2(x4[1], x4[0]);
-    f2 l[3], m[3], sum[3];
+    f2 u[3], u2[3], l[3], m[3], sum[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) l[i] = mul2a(c.h6, lam[i]);
-    lorenz_vjp2(x4, d4, c, l, m, jp);
+    for (int i = 0; i < 3; ++i) { u[i] = mul2a(c.h6, lam[i]); u2[i] = add2(u[i], u[i]); }
+    lorenz_vjp2(x4, d4, c, u, m, jp);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { sum[i] = m[i]; l[i] = fma2(c.h3, lam[i], mul2a(c.h1, m[i])); }
+    for (int i = 0; i < 3; ++i) { sum[i] = m[i]; l[i] = fma2(c.h1, m[i], u2[i]); }
     lorenz_vjp2(x3, d3, c, l, m, jp);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(c.h3, lam[i], mul2a(c.h2, m[i])); }
+    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(c.h2, m[i], u2[i]); }
     lorenz_vjp2(x2, d2, c, l, m, jp);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(c.h6, lam[i], mul2a(c.h2, m[i])); }
+    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(c.h2, m[i], u[i]); }
     lorenz_vjp2(x, d1, c, l, m, jp);
 #pragma unroll
     for (int i = 0; i < 3; ++i) lam[i] = add2(lam[i], add2(sum[i], m[i]));

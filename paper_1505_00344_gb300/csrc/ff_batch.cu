@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(R::MAX_BLOCK, MinBlocks<R>::value) batch_kerne
                     Vec<PPT>::store(ck + k * a.pitch + i0, v);
                 }
             }
-            integrate_item<R, METHOD, false, PP, PPT, false>(a, t, b.n_steps);
+            integrate_item<R, METHOD, false, PP, PPT, false, false>(a, t, b.n_steps);  // checkpoint written above
         }
     }
 }

@@ -572,7 +572,8 @@ __device__ __forceinline__ void reset_check(const IntegrateArgs& a, const Steppe
 // One work item (PPT consecutive particles starting at t * PPT) of the integrator:
 // load, n_steps steps with the state in registers, store.  `a` may live in the
 // kernel's argument block or, for batched launches, in a device table.
-template <class R, int METHOD, bool KAHAN, bool PP, int PPT, bool RESET>
+// TAPE: the launch may carry checkpoints (a.ckpt); false compiles them out.
+template <class R, int METHOD, bool KAHAN, bool PP, int PPT, bool RESET, bool TAPE = true>
 __device__ __forceinline__ void integrate_item(const IntegrateArgs& a, int64_t t, int n_steps_run) {
     constexpr int D = R::DIM;
     using Stepper = typename StepperFor<R, METHOD, KAHAN>::type;
@@ -594,7 +595,8 @@ __device__ __forceinline__ void integrate_item(const IntegrateArgs& a, int64_t t
             x[j][k] = v[j];
             c[j][k] = KAHAN ? w[j] : 0.f;
         }
-        if (float* ck0 = start_checkpoint(a); ck0 && k < a.dim) Vec<PPT>::store(ck0 + k * a.pitch + i0, v);
+        if (float* ck0 = TAPE ? start_checkpoint(a) : nullptr; ck0 && k < a.dim)
+            Vec<PPT>::store(ck0 + k * a.pitch + i0, v);
     }
     float prm[PPT][R::NP];
     Stepper st[PPT];
@@ -664,7 +666,7 @@ __device__ __forceinline__ void integrate_item(const IntegrateArgs& a, int64_t t
         for (int j = 0; j < PPT; ++j) st[j].to_internal(x[j]);
     };
     // a step of a large system is long enough on its own; unrolling only grows the code
-    run_steps<(D > 8) ? 1 : 4>(a, n_steps, step, save);
+    run_steps<(D > 8) ? 1 : 4, TAPE>(a, n_steps, step, save);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
         st[j].from_internal(x[j]);
@@ -698,11 +700,12 @@ __device__ __forceinline__ int64_t warp_major_first(int64_t block_in_range, int6
 template <class R, class = void> struct MinBlocks { static constexpr int value = 1; };
 template <class R> struct MinBlocks<R, decltype((void)R::MIN_BLOCKS)> { static constexpr int value = R::MIN_BLOCKS; };
 
-template <class R, int METHOD, bool KAHAN, bool PP, int PPT, bool RESET = false>
+// Particle reset is never taped, so its variants carry no checkpoints.
+template <class R, int METHOD, bool KAHAN, bool PP, int PPT, bool RESET = false, bool TAPE = !RESET>
 __global__ void __launch_bounds__(R::MAX_BLOCK, MinBlocks<R>::value) integrate_kernel(const __grid_constant__ IntegrateArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = warp_major_first(blockIdx.x, gridDim.x); t < a.n_vec; t += stride)
-        integrate_item<R, METHOD, KAHAN, PP, PPT, RESET>(a, t, (int)a.n_steps);
+        integrate_item<R, METHOD, KAHAN, PP, PPT, RESET, TAPE>(a, t, (int)a.n_steps);
 }
 
 // ---------------------------------------------------------------------------
@@ -1046,8 +1049,11 @@ inline cudaError_t launch_ppt(const IntegrateArgs& a, const LaunchShape& s, cuda
         }
     }
     else {
+        // large systems run at their register limit: untaped launches take a variant without
+        // the checkpoint code
         if (s.ppt != 1) return cudaErrorInvalidValue;
-        return persistent_launch(integrate_kernel<R, METHOD, KAHAN, PP, 1>, a, s, st);
+        if (a.ckpt) return persistent_launch(integrate_kernel<R, METHOD, KAHAN, PP, 1, false, true>, a, s, st);
+        return persistent_launch(integrate_kernel<R, METHOD, KAHAN, PP, 1, false, false>, a, s, st);
     }
 }
 

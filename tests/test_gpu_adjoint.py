@@ -189,14 +189,16 @@ def test_autograd_function():
     check(p.grad.numpy(), dp_ref)
 
 
-@pytest.mark.parametrize("ppt,kahan", [(1, False), (4, False), (4, True)])
-def test_checkpoints_inside_launches_match_split_launches(ppt, kahan):
+@pytest.mark.parametrize("ppt,kahan,n_fwd", [(1, False, 1000), (4, False, 1000), (4, True, 1000), (4, False, 1001)])
+def test_checkpoints_inside_launches_match_split_launches(ppt, kahan, n_fwd):
     """The integrator writes a taped run's checkpoints inside its launches, re-basing
     there as a launch boundary would: one 95-step call and the same steps as calls of
     one chunk each give the same states, checkpoints and gradients, bit for bit; so do
-    launches capped at 7 steps and calls of 7 steps (checkpoints inside launches)."""
+    launches capped at 7 steps and calls of 7 steps (checkpoints inside launches).
+    Groups of 1000 + 24 run the group-uniform packed kernels, 1001 + 23 the packed
+    kernel with per-particle constants."""
     box = ([-20, -20, 0], [20, 20, 40])
-    groups = [G(1000, *box, 1, 11), G(24, *box, -1, 12)]
+    groups = [G(n_fwd, *box, 1, 11), G(1024 - n_fwd, *box, -1, 12)]
     P = sum(g["count"] for g in groups)
 
     def run(calls, max_steps=0):

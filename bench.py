@@ -202,7 +202,7 @@ def kernel_source_hash():
              _between(dev, "// Packed-pair RK4 for Lorenz.", "// Host-side launch of one integrator"),
              _between(dev, "// Deal the persistent grid's blocks out to the groups", "inline cudaError_t launch_variants("),
              _between(dev, "// First item of this thread in a grid-stride loop", "// Minimum resident blocks"),
-             _between(api, "const bool packed_lorenz", "s->blocks_per_sm"),  # default launch shape
+             _between(api, "const bool packed_lorenz", "*out = s;"),  # default launch shape
              _between(proj, "struct ViewArgs {", "// Continuous pixel coordinates"),
              open(os.path.join(csrc, "ff_integrate_lorenz.cu")).read()]
     h = hashlib.sha256()

@@ -136,9 +136,10 @@ ff_status ff_create_system(int rhs_id, int dim, const double* params, int n_para
         ff_destroy_system(s);
         return st;
     }
-    // default launch shape: plain RK4 on Lorenz runs packed pairs, 4 particles per thread
+    // default launch shape: RK4 on Lorenz runs packed pairs, 4 particles per thread (2 when
+    // compensated: its registers then leave room for more warps)
     const bool packed_lorenz = rhs_id == FF_RHS_LORENZ && method == FF_RK4;
-    s->ppt = packed_lorenz ? 4 : 1;  // packed pairs, plain or compensated
+    s->ppt = packed_lorenz ? ((flags & FF_FLAG_KAHAN) ? 2 : 4) : 1;
     s->block = packed_lorenz ? 512 : 256;
     *out = s;
     return FF_OK;

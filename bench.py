@@ -189,7 +189,7 @@ def _between(text, start, end):
 
 def kernel_source_hash():
     """Hash of the source the fused Lorenz integrator is compiled and launched from: its
-    argument block, the vector loads, the packed-pair section, the group-uniform launch and the
+    argument block, step loop, vector loads, packed-pair section, group-uniform launch and
     warp-major item order of ff_device.cuh, the view/pixel rule, ff_integrate_lorenz.cu and the
     default launch shape in ff_api.cu.  A profile taken on other
     sources gives no traffic."""
@@ -202,6 +202,7 @@ def kernel_source_hash():
              _between(dev, "// Packed-pair RK4 for Lorenz.", "// Host-side launch of one integrator"),
              _between(dev, "// Deal the persistent grid's blocks out to the groups", "inline cudaError_t launch_variants("),
              _between(dev, "// First item of this thread in a grid-stride loop", "// Minimum resident blocks"),
+             _between(dev, "// Checkpoint slot for the state as the launch loads it", "// Reset data of a system"),
              _between(api, "const bool packed_lorenz", "*out = s;"),  # default launch shape
              _between(proj, "struct ViewArgs {", "// Continuous pixel coordinates"),
              open(os.path.join(csrc, "ff_integrate_lorenz.cu")).read()]

@@ -88,20 +88,20 @@ __device__ __forceinline__ void run_steps(const IntegrateArgs& a, int n_steps, S
     if constexpr (!TAPE) {
 #pragma unroll UNROLL
         for (int s = 0; s < n_steps; ++s) step();
-        return;
-    }
-    const bool at0 = a.ckpt && a.ck_first == 0;  // written at load (start_checkpoint)
-    int next = a.ckpt ? (at0 ? a.ck_every : a.ck_first) : n_steps;
-    int slot = a.ck_slot0 + (at0 ? 1 : 0);
-    int s = 0;
-    for (;;) {
-        const int end = next < n_steps ? next : n_steps;
+    } else {
+        const bool at0 = a.ckpt && a.ck_first == 0;  // written at load (start_checkpoint)
+        int next = a.ckpt ? (at0 ? a.ck_every : a.ck_first) : n_steps;
+        int slot = a.ck_slot0 + (at0 ? 1 : 0);
+        int s = 0;
+        for (;;) {
+            const int end = next < n_steps ? next : n_steps;
 #pragma unroll UNROLL
-        for (; s < end; ++s) step();
-        if (s >= n_steps) break;
-        save(slot);
-        ++slot;
-        next += a.ck_every;
+            for (; s < end; ++s) step();
+            if (s >= n_steps) break;
+            save(slot);
+            ++slot;
+            next += a.ck_every;
+        }
     }
 }
 

@@ -156,3 +156,29 @@ def test_chaotic_at_classical_r():
         signs.add(bool(x[0, 0] > 0))
     assert signs == {True, False}
     assert float(G["strange_attractor_r"][0]) < 28.0
+
+
+def test_rk4_commutes_with_the_z_shift():
+    """RK4 commutes with affine changes of variables, so stepping Lorenz in zt = z - r
+    (where the right-hand side reads (sigma (y - x), -(x zt + y), x y - beta zt - beta r))
+    is the same map: the FP64 oracle's steps and the shifted steps agree to rounding, for
+    forward and backward steps.  The CUDA integrators step in zt."""
+    rng = np.random.default_rng(11)
+    r = 28.0
+    x0 = np.stack([rng.uniform(-20, 20, 64), rng.uniform(-20, 20, 64), rng.uniform(0, 40, 64)])
+
+    def fs(s):
+        x, y, zt = s
+        return np.stack([SIGMA * (y - x), -(x * zt + y), x * y - BETA * zt - BETA * r])
+
+    for h in (0.001, -0.001):
+        want = oracle.integrate(oracle.LORENZ, x0.copy(), [SIGMA, r, BETA], np.full(64, h), 200)
+        s = x0 - np.array([[0.0], [0.0], [r]])
+        for _ in range(200):
+            k1 = fs(s)
+            k2 = fs(s + 0.5 * h * k1)
+            k3 = fs(s + 0.5 * h * k2)
+            k4 = fs(s + h * k3)
+            s = s + (h / 6.0) * (k1 + 2 * k2 + 2 * k3 + k4)
+        got = s + np.array([[0.0], [0.0], [r]])
+        assert np.abs(got - want).max() <= 1e-10 * max(1.0, np.abs(want).max())

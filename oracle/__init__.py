@@ -21,6 +21,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ffo.c")
 _LIB = os.path.join(_HERE, "libffo.so")
+_SRC32 = os.path.join(_HERE, "ffo_fp32.c")
+_LIB32 = os.path.join(_HERE, "libffo32.so")
 
 LINEAR, HARMONIC, WILSON_COWAN, LORENZ, HH3 = 0, 1, 2, 3, 4
 RK4, EULER = 0, 1
@@ -28,15 +30,21 @@ RK4, EULER = 0, 1
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile ffo.c with gcc into oracle/libffo.so (no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = f"{_LIB}.{os.getpid()}.tmp"
+def _compile(src, lib, deps, force):
+    if force or not os.path.exists(lib) or any(os.path.getmtime(lib) < os.path.getmtime(d) for d in deps):
+        tmp = f"{lib}.{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
+               "-o", tmp, src, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)  # atomic: concurrent test workers never load a partial file
-    return _LIB
+        os.replace(tmp, lib)  # atomic: concurrent test workers never load a partial file
+    return lib
+
+
+def build(force: bool = False) -> str:
+    """Compile ffo.c with gcc into oracle/libffo.so (no FMA contraction), and its
+    single-precision evaluation ffo_fp32.c into oracle/libffo32.so."""
+    _compile(_SRC32, _LIB32, [_SRC, _SRC32], force)
+    return _compile(_SRC, _LIB, [_SRC], force)
 
 
 def _load():
@@ -189,6 +197,37 @@ def integrate_parallel(rhs_id, state, params, h, n_steps, method=RK4, pparam_ind
     if any(rcs):
         raise ValueError("ffo_integrate: bad arguments")
     return st, threads
+
+
+_lib32 = None
+
+
+def integrate_fp32(rhs_id, state, params, h, n_steps, method=RK4, pparam_index=-1, pparam=None):
+    """The oracle's integration evaluated in FP32 (ffo_fp32.c): state, parameters, steps and
+    every intermediate in float32, elementary functions rounded once to float.  Not a parity
+    reference -- a yardstick for the error any FP32 evaluation of the same formulas has
+    against the FP64 oracle.  Returns the float32 state [dim][P]."""
+    global _lib32
+    if _lib32 is None:
+        build()
+        lib = ctypes.CDLL(_LIB32)
+        P_, i64 = ctypes.c_void_p, ctypes.c_int64
+        lib.ffo_integrate.restype = ctypes.c_int
+        lib.ffo_integrate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, i64, P_, P_, ctypes.c_int,
+                                      ctypes.c_int, P_, P_, i64]
+        _lib32 = lib
+    st = np.array(state, dtype=np.float32, order="C", copy=True)
+    if st.ndim == 1:
+        st = st.reshape(-1, 1)
+    dim, P = st.shape
+    p = _c(params, np.float32)
+    hh = np.broadcast_to(np.asarray(h, dtype=np.float32), (P,)).copy()
+    pp = None if pparam is None else _c(pparam, np.float32)
+    rc = _lib32.ffo_integrate(rhs_id, method, dim, P, P, _ptr(st), _ptr(p), p.size, pparam_index, _ptr(pp),
+                              _ptr(hh), int(n_steps))
+    if rc != 0:
+        raise ValueError("ffo_integrate (fp32): bad arguments")
+    return st
 
 
 def integrate_reset(rhs_id, state, params, groups, dt, n_steps, step0=0, check_every=1, bounds=None,

@@ -7,7 +7,11 @@ alone with one particle per thread -- across graph replays, a new step count, a
 mid-run parameter change and autotuning (which restores the members' states; if it
 splits a call into several launches, Lorenz members agree to the rounding of the
 shifted state at launch boundaries instead).
-One member is also checked against the FP64 oracle.
+Every member is also checked directly against the FP64 oracle over the first 100
+steps, at the bar of the single-system parity tests: per-component relative error
+|x - x_ref| / max(|x_ref|, 1) <= 1e-5, and for the chaotic systems (Lorenz, HH x 3)
+the yardsticks of conftest.assert_parity_bar (the oracle's own one-ulp sensitivity and
+an FP32 evaluation of the oracle's formulas).
 """
 import numpy as np
 import pytest
@@ -16,6 +20,7 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 import paper_1505_00344_gb300 as ff  # noqa: E402
+from conftest import assert_parity_bar, state_err  # noqa: E402
 from paper_1505_00344_gb300.workloads import HH3_BASE, LORENZ_PARAMS, WC_PARAMS  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -96,6 +101,46 @@ def test_batch_matches_members_stepped_alone():
     assert err.max() <= 1e-5
     n_esc, t_fwd, t_bwd = batched[2].stats()
     assert abs(t_fwd - 1.77) < 1e-12 and abs(t_bwd + 1.77) < 1e-12
+    b.close()
+
+
+CHAOTIC = {"lorenz", "hh3"}
+ORACLE_IDS = {"lorenz": oracle.LORENZ, "wilson_cowan": oracle.WILSON_COWAN, "hh3": oracle.HH3,
+              "harmonic": oracle.HARMONIC, "linear": oracle.LINEAR}
+
+
+@pytest.mark.parametrize("tuned", [False, True])
+def test_batch_members_against_oracle(tuned):
+    """Each member of one batch (two Lorenz systems, one with a per-particle r; Wilson-Cowan;
+    two HH x 3 systems; harmonic; linear) after 100 batched steps against oracle.integrate,
+    in the default launch shape (one particle per thread) and in the autotuned one."""
+    seed0 = 300 + 17 * int(tuned)
+    members = [make(m, seed0 + 10 * i) for i, m in enumerate(MEMBERS)]
+    dts = [m[4] for m in MEMBERS]
+    b = ff.Batch(members, stream=torch.cuda.current_stream().cuda_stream)
+    if tuned:
+        b.autotune(dts, trial_steps=16)  # restores the members' states afterwards
+    b.step(60, dts)
+    b.step(40, dts)  # a second capture: the members carry their states between launches
+    for i, (m, s) in enumerate(zip(MEMBERS, members)):
+        rhs, params, groups, box, dt, pp = m
+        dim = len(box[0])
+        x0 = np.concatenate([oracle.seed_group(dim, box[0], box[1], seed0 + 10 * i + t, count=c)
+                             for t, (c, _) in enumerate(groups)], axis=1)
+        h = np.concatenate([np.full(c, d * dt) for c, d in groups])
+        kw = {}
+        if pp:
+            kw = dict(pparam_index=pp[0], pparam=oracle.linspace_param(x0.shape[1], pp[1], pp[2]).astype(np.float64))
+        rid = ORACLE_IDS[rhs]
+        want = oracle.integrate(rid, x0, params, h, 100, **kw)
+        err = state_err(state(s), want)
+        if rhs not in CHAOTIC:
+            assert_parity_bar(err)
+            continue
+        sign = np.random.default_rng(i).choice([-1.0, 1.0], x0.shape)
+        pert = oracle.integrate(rid, x0.astype(np.float64) * (1.0 + 6e-8 * sign), params, h, 100, **kw)
+        fp32 = oracle.integrate_fp32(rid, x0, params, h, 100, **kw)
+        assert_parity_bar(err, state_err(pert, want), h < 0, state_err(fp32, want))
     b.close()
 
 

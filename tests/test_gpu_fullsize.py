@@ -5,20 +5,27 @@ one by one from its own seeding (and, for the chaotic long runs, compares
 attractor-density statistics instead of trajectories):
 
 * lorenz_4M (4 particles per thread, packed pairs, splat fused into the
-  integrator, as timed): first 100 steps per sampled trajectory (state-relative error
-  <= max(1e-5, 5x the FP64 oracle's one-ulp sensitivity), 99% <= 1e-5);
+  integrator, as timed): first 100 steps per sampled trajectory (per-component
+  relative error |x - x_ref| / max(|x_ref|, 1): forward particles <= max(1e-5, 5x
+  the FP64 oracle's one-ulp sensitivity) with 99% <= 1e-5, backward ones <= 1e-4);
   after the full 100 frames x 200 steps, the forward group's coarse density
   matches the oracle's (total variation <= 0.05 and <= 3x the distance between
   two independent oracle samples), every backward particle has escaped, and the
   escape flags of the backward group after 1000 steps agree on >= 99% of
   sampled particles.  The compensated (Kahan) integrator's error against FP64
-  is stated at 100 and 1000 steps and must not exceed the plain one.
+  is stated at 100 and 1000 steps (median not above the plain one) and, after
+  the decorrelation of the chaotic trajectories, at 20,000 steps as the same
+  coarse-density distance for plain and Kahan.
 * lorenz_bif_8M: every sampled particle with 2 <= r <= 6 ends on its fixed
   point z = r - 1 in both the GPU and the oracle (on the same side), r <= 0.3
   ends at the origin, and the GPU image of those columns has all its mass on
-  the row of z = r - 1.
-* hh3_1M: first 100 steps per sampled trajectory (plain FP32: within five times
-  the FP64 oracle's one-ulp sensitivity; 99% of particles within 1e-5).
+  the row of z = r - 1; in the chaotic band r >= 25 the (r, z) density of all
+  GPU particles matches two disjoint 65,536-particle oracle samples (same
+  total-variation bar).
+* hh3_1M: first 100 steps per sampled trajectory (within five times the FP64
+  oracle's one-ulp sensitivity; 99% of particles within 1e-5), and after the
+  whole 50,000-step run the 64x64 density of the (V1, V2, V3) view against two
+  disjoint 8,192-particle oracle samples (same total-variation bar).
 * wc_4k: the whole workload (4096 particles, 1000 steps) per trajectory and the
   256x256 image against the oracle's.
 """
@@ -29,11 +36,11 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 import paper_1505_00344_gb300 as ff  # noqa: E402
+from conftest import TOL, assert_parity_bar, state_err  # noqa: E402
 from paper_1505_00344_gb300 import workloads as W  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -55,9 +62,7 @@ def state(s):
     return out
 
 
-def particle_err(got, want):
-    d = np.abs(got.astype(np.float64) - want).max(axis=0)
-    return d / np.maximum(np.abs(want).max(axis=0), 1.0)
+particle_err = state_err
 
 
 def locate(w, idx):
@@ -84,6 +89,12 @@ def oracle_sample(w, idx, steps, params=None, pparam=None):
     return oracle.integrate_parallel(rid, x0, params or w["params"], h, steps, **kw)[0], x0
 
 
+def report(capsys, text):
+    """Print a measured statement so that it shows in the test log."""
+    with capsys.disabled():
+        print("\n" + text)
+
+
 def escaped(x):
     return ~(np.abs(x.astype(np.float64)) <= 1e30).all(axis=0)
 
@@ -91,7 +102,7 @@ def escaped(x):
 # ---------------------------------------------------------------------------
 # 4M-particle Lorenz workload
 # ---------------------------------------------------------------------------
-def test_lorenz_4M_sampled_first_frame():
+def test_lorenz_4M_sampled_first_frame(capsys):
     w = W.workload("lorenz_4M")
     s = system(w)
     s.step(100, w["dt"])
@@ -104,10 +115,9 @@ def test_lorenz_4M_sampled_first_frame():
     sign = np.random.default_rng(0).choice([-1.0, 1.0], x0.shape)
     pert = oracle.integrate_parallel(oracle.LORENZ, x0.astype(np.float64) * (1 + 6e-8 * sign), w["params"], h,
                                      100)[0]
-    spread = particle_err(pert, want).max()
-    print(f"\n[lorenz_4M 100 steps] max err {err.max():.2e}, p99 {np.quantile(err, 0.99):.2e}, "
-          f"one-ulp spread {spread:.2e}")
-    assert err.max() <= max(TOL, 5 * spread) and np.quantile(err, 0.99) <= TOL
+    fp32 = oracle.integrate_fp32(oracle.LORENZ, x0, w["params"], h, 100)
+    summary = assert_parity_bar(err, particle_err(pert, want), h < 0, particle_err(fp32, want))
+    report(capsys, f"[lorenz_4M 100 steps, per-component error vs FP64] {summary}")
     s.close()
 
 
@@ -152,7 +162,7 @@ def _oracle_density(w, x, nb=(48, 27)):
     return img / max(img.sum(), 1.0)
 
 
-def test_lorenz_4M_full_job_statistics():
+def test_lorenz_4M_full_job_statistics(capsys):
     w = W.workload("lorenz_4M")
     s = system(w)
     view = ff.make_view(**w["view"])
@@ -177,15 +187,29 @@ def test_lorenz_4M_full_job_statistics():
     np.testing.assert_array_equal(again.cpu().numpy(), image.cpu().numpy())
     gpu = _coarse_density(s, w, group_mask=0b01)
     N = 65536
-    A, _ = oracle_sample(w, np.arange(N), 20000)
-    B, _ = oracle_sample(w, np.arange(N, 2 * N), 20000)
-    assert not escaped(A).any()
+    AB, _ = oracle_sample(w, np.arange(2 * N), 20000)
+    A, B = AB[:, :N], AB[:, N:]
+    assert not escaped(AB).any()
     pa, pb = _oracle_density(w, A), _oracle_density(w, B)
     tv_ab = 0.5 * np.abs(pa - pb).sum()
     tv = 0.5 * np.abs(gpu - pa).sum()
-    print(f"\n[lorenz_4M density] TV(gpu, oracle) = {tv:.4f}, TV(oracle A, oracle B) = {tv_ab:.4f}")
     assert tv <= 0.05 and tv <= 3 * tv_ab
+    plain_final = state(s)[:, :N]
     s.close()
+    # Error statement of the compensated integrator at step 20,000 (20 time units): the
+    # trajectories have decorrelated from the FP64 ones (largest Lyapunov exponent ~0.9), so
+    # the statement is statistical -- the same coarse-density distance, for plain and Kahan.
+    comp = system(w, kahan=True)
+    for f in range(w["frames"]):
+        comp.step(w["steps_per_frame"], w["dt"])
+    tv_k = 0.5 * np.abs(_coarse_density(comp, w, group_mask=0b01) - pa).sum()
+    ep = particle_err(plain_final, A)
+    ek = particle_err(state(comp)[:, :N], A)
+    comp.close()
+    report(capsys, f"[lorenz_4M error vs FP64] step 20000: TV(plain, oracle) = {tv:.4f}, TV(kahan, oracle) = "
+          f"{tv_k:.4f}, TV(oracle A, oracle B) = {tv_ab:.4f}; per-trajectory median plain {np.median(ep):.2e} "
+          f"kahan {np.median(ek):.2e} (decorrelated)")
+    assert tv_k <= 0.05 and tv_k <= 3 * tv_ab
 
 
 # ---------------------------------------------------------------------------
@@ -243,10 +267,93 @@ def _continue(w, idx, x, r):
     return out
 
 
+def test_lorenz_bif_8M_chaotic_band_density(capsys):
+    """Beyond the Hopf point (r > 24.74 at beta = 8/3, 21.4 at beta = 2) most columns of the
+    diagram are chaotic: there the (r, z) density of the GPU run over every particle with
+    r >= 25 is compared with two disjoint random samples of 65,536 such particles run by
+    the oracle (r in 35 bins of 5, z in 20 bins of 20 over [0, 400])."""
+    w = W.workload("lorenz_bif_8M")
+    s = system(w)
+    for f in range(w["frames"]):
+        if f in w["schedule"]:
+            s.set_params(w["schedule"][f])
+        s.step(w["steps_per_frame"], w["dt"])
+    nb = (35, 20)
+    lo, hi = (25.0, 0.0), (200.0, 400.0)
+    v = dict(w["view"], lo=lo, hi=hi, width=nb[0], height=nb[1])
+    img = torch.zeros((nb[1], nb[0]), dtype=torch.int32, device="cuda")
+    s.project_splat(v, img)
+    torch.cuda.synchronize()
+    gpu = img.cpu().numpy().view(np.uint32).astype(np.float64)
+    P = w["groups"][0]["count"]
+    n_esc = s.stats()[0]
+    s.close()
+    r_all = oracle.linspace_param(P, w["pparam"]["lo"], w["pparam"]["hi"])
+    band = np.nonzero(r_all >= 25.0)[0]
+    assert n_esc == 0 and gpu.sum() >= band.size - 1  # every band particle drawn but r = 200 (right edge)
+    rng = np.random.default_rng(11)
+    N = 65536
+    idx = np.sort(rng.choice(band, 2 * N, replace=False))
+    r = r_all[idx].astype(np.float64)
+    x = oracle_sample(w, idx, w["steps_per_frame"], pparam=r)[0]
+    x = _continue(w, idx, x, r)
+    assert not escaped(x).any()
+    perm = rng.permutation(2 * N)
+
+    def dens(sel):
+        a = oracle.splat2d(r[sel].astype(np.float32), x[2, sel].astype(np.float32), lo, hi, nb[0], nb[1])
+        return a.astype(np.float64) / a.sum()
+
+    pa, pb = dens(perm[:N]), dens(perm[N:])
+    gpu /= gpu.sum()
+    tv_ab = 0.5 * np.abs(pa - pb).sum()
+    tv = 0.5 * np.abs(gpu - pa).sum()
+    report(capsys, f"[lorenz_bif_8M chaotic band r >= 25] TV(gpu, oracle) = {tv:.4f}, "
+          f"TV(oracle A, oracle B) = {tv_ab:.4f}")
+    assert tv <= 0.05 and tv <= 3 * tv_ab
+
+
 # ---------------------------------------------------------------------------
 # 1M-particle three-neuron Hodgkin-Huxley
 # ---------------------------------------------------------------------------
-def test_hh3_1M_sampled_first_steps():
+def test_hh3_1M_full_run_density(capsys):
+    """The whole hh3_1M run (50,000 RK4 steps, 500 ms) in the bench's launch shape, then the
+    (V1, V2, V3) view through the workload's camera into a 64 x 64 grid: the GPU density of
+    all 1,048,576 particles against two disjoint oracle samples of 8,192 particles
+    (Sec. 3, Eq. 6-11; the projection of Fig. 6)."""
+    w = W.workload("hh3_1M")
+    s = system(w)
+    s.step(w["steps_per_frame"], w["dt"])
+    nb = 64
+    v = dict(w["view"], width=nb, height=nb)
+    img = torch.zeros((nb, nb), dtype=torch.int32, device="cuda")
+    s.project_splat(v, img)
+    torch.cuda.synchronize()
+    gpu = img.cpu().numpy().view(np.uint32).astype(np.float64)
+    n_esc = s.stats()[0]
+    s.close()
+    assert n_esc == 0
+    N = 8192
+    x, _ = oracle_sample(w, np.arange(2 * N), w["steps_per_frame"])
+    assert not escaped(x).any()
+    ax, mvp = w["view"]["axes"], w["view"]["mvp"]
+
+    def dens(x):
+        xf = x.astype(np.float32)
+        a = oracle.splat3d(xf[ax[0]], xf[ax[1]], xf[ax[2]], mvp, nb, nb).astype(np.float64)
+        return a / a.sum()
+
+    pa, pb = dens(x[:, :N]), dens(x[:, N:])
+    gpu /= gpu.sum()
+    tv_ab = 0.5 * np.abs(pa - pb).sum()
+    tv = 0.5 * np.abs(gpu - pa).sum()
+    report(capsys, f"[hh3_1M density after 50,000 steps] TV(gpu, oracle) = {tv:.4f}, "
+          f"TV(oracle A, oracle B) = {tv_ab:.4f}")
+    assert tv <= 0.05 and tv <= 3 * tv_ab
+
+
+
+def test_hh3_1M_sampled_first_steps(capsys):
     w = W.workload("hh3_1M")
     s = system(w)
     s.step(100, w["dt"])
@@ -257,16 +364,16 @@ def test_hh3_1M_sampled_first_steps():
     sign = np.random.default_rng(0).choice([-1.0, 1.0], x0.shape)
     h = np.full(idx.size, w["dt"])
     pert = oracle.integrate_parallel(oracle.HH3, x0.astype(np.float64) * (1 + 6e-8 * sign), w["params"], h, 100)[0]
-    spread = particle_err(pert, want).max()
-    assert err.max() <= max(TOL, 5 * spread)
-    assert np.quantile(err, 0.99) <= TOL
+    fp32 = oracle.integrate_fp32(oracle.HH3, x0, w["params"], h, 100)
+    summary = assert_parity_bar(err, particle_err(pert, want), None, particle_err(fp32, want))
+    report(capsys, f"[hh3_1M 100 steps, per-component error vs FP64] {summary}")
     s.close()
 
 
 # ---------------------------------------------------------------------------
 # 4096-particle Wilson-Cowan workload, whole run
 # ---------------------------------------------------------------------------
-def test_wc_4k_whole_workload():
+def test_wc_4k_whole_workload(capsys):
     w = W.workload("wc_4k")
     s = system(w)
     s.step(w["steps_per_frame"], w["dt"])
@@ -274,10 +381,23 @@ def test_wc_4k_whole_workload():
     image = torch.zeros((v["height"], v["width"]), dtype=torch.int32, device="cuda")
     s.project_splat(ff.make_view(**v), image)
     got = state(s)
-    want, _ = oracle_sample(w, np.arange(got.shape[1]), w["steps_per_frame"])
+    idx = np.arange(got.shape[1])
+    want, x0 = oracle_sample(w, idx, w["steps_per_frame"])
+    gi, _ = locate(w, idx)
+    h = np.array([w["groups"][g]["direction"] * w["dt"] for g in gi])
     err = particle_err(got, want)
-    print(f"\n[wc_4k] 1000-step state error vs FP64: max {err.max():.2e} median {np.median(err):.2e}")
-    assert err.max() <= 1e-4
+    # forward: the stable attractor keeps errors at their one-step size; backward: the
+    # particles leave [0,1]^2 on unstable paths (|E|, |I| up to ~2e4 after 10 time
+    # units), so rounding is amplified and the unstable-case yardsticks apply
+    assert err[h > 0].max() <= TOL
+    sign = np.random.default_rng(0).choice([-1.0, 1.0], x0.shape)
+    pert = oracle.integrate_parallel(oracle.WILSON_COWAN, x0.astype(np.float64) * (1 + 6e-8 * sign), w["params"], h,
+                                     w["steps_per_frame"])[0]
+    fp32 = oracle.integrate_fp32(oracle.WILSON_COWAN, x0, w["params"], h, w["steps_per_frame"])
+    bwd = h < 0
+    summary = assert_parity_bar(err[bwd], particle_err(pert, want)[bwd], np.ones(bwd.sum(), bool),
+                                particle_err(fp32, want)[bwd])
+    report(capsys, f"[wc_4k 1000 steps, per-component error vs FP64] forward max {err[h > 0].max():.2e}; {summary}")
     img = image.cpu().numpy().view(np.uint32).astype(np.int64)
     ref = oracle.splat2d(want[0].astype(np.float32), want[1].astype(np.float32), v["lo"], v["hi"], v["width"],
                          v["height"]).astype(np.int64)

@@ -55,8 +55,10 @@ def gpu_state(s):
 
 
 def particle_err(got, want):
-    d = np.abs(got.astype(np.float64) - want).max(axis=0)
-    return d / np.maximum(np.abs(want).max(axis=0), 1.0)
+    """Per-particle relative state error: max over components k of
+    |x_k - x_ref,k| / max(|x_ref,k|, 1) (each component on its own scale, floored at 1)."""
+    d = np.abs(got.astype(np.float64) - want) / np.maximum(np.abs(want), 1.0)
+    return d.max(axis=0)
 
 
 def oracle_x0(groups, dim):

@@ -182,6 +182,7 @@ def test_argument_errors():
         s.project_sprites(view, ff.make_sprite(1.0, technique=3), img)
     assert e.value.status == ff.FF_ERR_INVALID_ARG
     big = dict(view, width=4096, height=4096)  # 16,384 tiles: more than the tiled technique takes
-    with pytest.raises(ff.FFError) as e:
-        s.project_sprites(big, ff.make_sprite(1.0, technique=ff.FF_SPRITE_TILED), torch.zeros(4, device="cuda"))
+    small = torch.zeros(4, device="cuda")
+    with pytest.raises(ff.FFError) as e:  # raw pointer: the library itself rejects the view
+        s.project_sprites(big, ff.make_sprite(1.0, technique=ff.FF_SPRITE_TILED), small.data_ptr())
     assert e.value.status == ff.FF_ERR_UNSUPPORTED

@@ -126,3 +126,28 @@ def test_escape_count():
     n, flags = oracle.count_escaped(st)
     assert n == 3
     assert flags.tolist() == [False, True, True, True, False]
+
+
+def test_fp32_evaluation_is_the_same_map_in_single_precision():
+    """oracle.integrate_fp32 (the FP32 yardstick of the GPU parity bar) computes the same
+    RK4 map in float32: on dx/dt = A x it matches the matrix power T(hA)^n in float32 to
+    a few float32 ulps per step (and is visibly not the FP64 result), and on Lorenz one
+    step from an exactly representable state lands within a few float32 ulps of the
+    FP64 step."""
+    A = _stable_matrix(3, 21)
+    x0 = np.random.default_rng(5).standard_normal((3, 64)).astype(np.float32)
+    h, n = 0.01, 100
+    got = oracle.integrate_fp32(oracle.LINEAR, x0, A.reshape(-1).astype(np.float32), h, n)
+    assert got.dtype == np.float32
+    A32 = A.astype(np.float32).astype(np.float64)
+    want = np.linalg.matrix_power(_taylor4(np.float64(np.float32(h)) * A32), n) @ x0.astype(np.float64)
+    scale = np.maximum(np.abs(want), 1.0)
+    err = np.abs(got - want) / scale
+    assert err.max() <= n * 8 * 2.0**-24
+    assert err.max() > 1e-9  # rounded in FP32, not FP64
+    x = np.array([[1.5], [-2.25], [20.0]], np.float32)
+    p = [10.0, 28.0, 8.0 / 3.0]
+    one32 = oracle.integrate_fp32(oracle.LORENZ, x, p, 0.001, 1).astype(np.float64)
+    one64 = oracle.integrate(oracle.LORENZ, x, np.float32(p).astype(np.float64), np.float64(np.float32(0.001)), 1)
+    assert np.all(np.abs(one32 - one64) <= 4 * np.spacing(np.abs(one64).astype(np.float32)).astype(np.float64))
+    assert not np.array_equal(one32, one64)

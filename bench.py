@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time only the headline workload (no adjoint and per-workload sub-records)")
     # profiling cases only (a line taken with these is not the workload's number)
     ap.add_argument("--particles", type=int, default=0, help="scale the workload to this many particles")
     ap.add_argument("--frames", type=int, default=0, help="run only this many frames per step")
@@ -219,24 +221,73 @@ def measured_peaks():
         return {}
 
 
-def run_ours(args, rank, world, local):
+# MUFU operations of one RK4 step, counted from the equations (exp and reciprocal or
+# division each one multi-function-unit operation): Wilson-Cowan per right-hand side
+# 2 logistic functions = 2 exp + 2 reciprocals, x 4 stages; Hodgkin-Huxley x 3 per neuron
+# and right-hand side 7 exp (six rates + the synaptic activation) + 4 divisions, x 3
+# neurons x 4 stages.
+MUFU_PER_STEP = {"wilson_cowan": (8, 8), "hh3": (84, 48)}  # (exp, reciprocal)
+
+
+def pipe_rates(device_index):
+    """Measured lane-operation rates of the integrators' instruction kinds (ff_pipe_rate)."""
+    import paper_1505_00344_gb300 as ff
+
+    return {"ffma_lane_ops_per_s": ff.ff_pipe_rate(ff.FF_PIPE_FFMA, device_index),
+            "ffma2_lane_ops_per_s": ff.ff_pipe_rate(ff.FF_PIPE_FFMA2, device_index),
+            "ex2_per_s": ff.ff_pipe_rate(ff.FF_PIPE_EX2, device_index),
+            "rcp_per_s": ff.ff_pipe_rate(ff.FF_PIPE_RCP, device_index),
+            "how": "ff_pipe_rate: 8 independent chains per thread, full occupancy, 4096 iterations, CUDA events"}
+
+
+def roofline_for(w, n_work, avg_launch_ms, steps_per_launch, sms, max_mhz, rates, kahan=False):
+    """ALU roofline of one integrator launch: FP32 flops for Lorenz against the FP32 peak
+    derived from unit counts and the clock; multi-function-unit operations for Wilson-Cowan and
+    HH x 3 against the measured ex2 / reciprocal rates for their mix."""
+    if w["rhs"] == "lorenz":
+        step_flops = LORENZ_RK4_FLOPS + (KAHAN_EXTRA_FLOPS if kahan else 0)
+        work = step_flops * n_work * steps_per_launch
+        achieved = work / (avg_launch_ms / 1e3) / 1e12
+        peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+        out = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+               "frac": round(achieved / peak, 4),
+               "peak_basis": f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {max_mhz:.0f} MHz "
+                             "(max SM clock)",
+               "work_per_particle_step": f"{step_flops} flop (Eq. 3-5, FMA = 2 flops)"}
+        if rates:
+            m = 2 * rates["ffma2_lane_ops_per_s"] / 1e12
+            out["measured_fma2_peak"] = round(m, 3)
+            out["frac_of_measured_fma2"] = round(achieved / m, 4)
+        return out
+    if w["rhs"] in MUFU_PER_STEP and rates:
+        n_exp, n_rcp = MUFU_PER_STEP[w["rhs"]]
+        work = (n_exp + n_rcp) * n_work * steps_per_launch
+        achieved = work / (avg_launch_ms / 1e3) / 1e12
+        # the exp and reciprocal operations share the multi-function unit: the mix's time
+        # per step is the sum of the two kinds' times at their measured rates
+        peak = (n_exp + n_rcp) / (n_exp / rates["ex2_per_s"] + n_rcp / rates["rcp_per_s"]) / 1e12
+        return {"bound": "mufu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "Tops/s",
+                "frac": round(achieved / peak, 4),
+                "peak_basis": f"measured ex2 {rates['ex2_per_s']:.3e}/s and rcp {rates['rcp_per_s']:.3e}/s "
+                              f"(ff_pipe_rate) for the mix {n_exp} exp + {n_rcp} reciprocals",
+                "work_per_particle_step": f"{n_exp + n_rcp} MUFU operations counted from the equations"}
+    return None
+
+
+def measure_workload(args, w, dev, stream, steps, warmup, with_e2e, world, kahan=False, rates=None, reset=False,
+                     clocks_enabled=True):
+    """Time whole runs of one workload (re-seed, then its frames of RK4 steps with the
+    projection and count splat of the frames that draw) and return the bench record."""
     import torch
     import paper_1505_00344_gb300 as ff
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    stream = torch.cuda.current_stream().cuda_stream
-    w = workload_for(args, rank, world)
     P = total_particles(w)
     view = ff.make_view(**w["view"])
     H, Wd = w["view"]["height"], w["view"]["width"]
-    sysobj = ff.System.from_workload(w, kahan=args.kahan, stream=stream)
+    sysobj = ff.System.from_workload(w, kahan=kahan, stream=stream)
     if args.ppt or args.block or args.blocks_per_sm:
         sysobj.set_launch(args.ppt, args.block, args.blocks_per_sm, 0)  # 0: the library's default
-    if args.reset:
+    if reset:
         rs = w["reset"]
         sysobj.set_reset(rs["lo"], rs["hi"], rs["t_max"], rs["check_every"])
     image = torch.zeros((H, Wd), dtype=torch.int32, device=dev)
@@ -244,57 +295,57 @@ def run_ours(args, rank, world, local):
     every = w.get("splat_every_frame", False)
     schedule = {int(k): v for k, v in w.get("schedule", {}).items()}
     base_params = list(w["params"])
-    # the library fuses the splat into the integrator for the packed Lorenz kernel on 4-aligned groups
-    fused = (w["rhs"] == "lorenz" and (args.ppt or 4) in (2, 4) and not (args.kahan or args.reset)
-             and all(sum(g["count"] for g in w["groups"][:k]) % (args.ppt or 4) == 0 for k in range(len(w["groups"]))))
+    counted = {"launches": 0, "record": None}
 
-    def job(events=None):
-        """One whole workload run; returns the number of our kernel launches enqueued."""
+    def job(events=None, count=False):
+        """One whole workload run."""
         sysobj.reset()
         sysobj.set_params(base_params)
-        launches = len(w["groups"])
+        launches = len(w["groups"])  # the seed kernel, once per group
         for f in range(w["frames"]):
             if f in schedule:
                 sysobj.set_params(schedule[f])
             if events is not None:
-                events.append(("int0", torch.cuda.Event(enable_timing=True)))
-                events[-1][1].record()
-            splat = every or f == w["frames"] - 1
-            if splat:
-                # one frame: step + project + splat (fused into the integrator's last launch
-                # when the packed Lorenz kernel runs; launches counted as the fused kernel)
+                events.append(torch.cuda.Event(enable_timing=True))
+                events[-1].record()
+            if every or f == w["frames"] - 1:
+                # one frame: step + project + splat (the library fuses the splat into the
+                # integrator's last launch where its kernel has the epilogue)
                 sysobj.step_splat(w["steps_per_frame"], w["dt"], view, image)
-                launches += 1 if fused else 2
             else:
                 sysobj.step(w["steps_per_frame"], w["dt"])
-                launches += 1
             if events is not None:
-                events.append(("int1", torch.cuda.Event(enable_timing=True)))
-                events[-1][1].record()
-        return launches
+                events.append(torch.cuda.Event(enable_timing=True))
+                events[-1].record()
+            if count:
+                rec = sysobj.last_launch()  # what the library launched, not a guess
+                launches += rec["integrator_launches"] + rec["splat_launches"]
+                if every or f == w["frames"] - 1:
+                    counted["record"] = rec
+        if count:
+            counted["launches"] = launches
 
-    for _ in range(args.warmup):
-        job()
+    for k in range(max(1, warmup)):
+        job(count=(k == 0))
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local, enabled=not args.no_clocks)
+    clocks = ClockSampler(dev.index, enabled=clocks_enabled)
     step_ms, int_ms = [], []
-    launches = 0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()  # evict the state and image from L2 between timed steps
         ev = []
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record()
-        launches += job(ev)
+        job(ev)
         s1.record()
         torch.cuda.synchronize()
         step_ms.append(s0.elapsed_time(s1))
-        for (_, a), (_, b) in zip(ev[0::2], ev[1::2]):
+        for a, b in zip(ev[0::2], ev[1::2]):
             int_ms.append(a.elapsed_time(b))
     torch.cuda.synchronize()
     if world > 1:
@@ -303,78 +354,107 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
 
     total_ms = max_over_ranks(sum(step_ms), dev)
-    ms_per_step = total_ms / args.steps
-    steps_per_job = total_steps(w)
-    value = world * P * steps_per_job / (ms_per_step / 1e3)
-
-    # roofline of the integrator (dominant kernel)
+    ms_per_step = total_ms / steps
+    value = world * P * total_steps(w) / (ms_per_step / 1e3)
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    peaks = measured_peaks()
-    max_mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
-    avg_int_ms = statistics.mean(int_ms)
+    max_mhz = (clk or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    rec = counted["record"] or {}
+    fused = bool(rec.get("fused_splat"))
     n_work = (P + 3) // 4 * 4
-    # the compensated update adds t = x + y, (t - x) - y per component: 9 flops per step
-    step_flops = LORENZ_RK4_FLOPS + (KAHAN_EXTRA_FLOPS if args.kahan else 0)
-    flops_per_launch = step_flops * n_work * w["steps_per_frame"] if w["rhs"] == "lorenz" else None
-    roof = None
-    if flops_per_launch:
-        achieved = flops_per_launch / (avg_int_ms / 1e3) / 1e12
-        packed = (args.ppt or 4) in (2, 4) and not (args.kahan or args.reset)
-        kernel = ("lorenz_rk4_x2u_kernel<splat>" if fused and every else
-                  "lorenz_rk4_x2u_kernel" if packed else
-                  "lorenz_rk4_kahan_x2u_kernel" if args.kahan and (args.ppt or 4) in (2, 4) and not args.reset
-                  else "integrate_kernel<Lorenz,RK4>")
+    avg_int_ms = statistics.mean(int_ms)
+    # a frame's launch window holds one integrator launch when the call was not split
+    per_launch = w["steps_per_frame"] // max(1, rec.get("integrator_launches", 1))
+    roof = roofline_for(w, n_work, avg_int_ms * per_launch / w["steps_per_frame"], per_launch, sms, max_mhz, rates,
+                        kahan)
+    if roof:
+        kernel = rec.get("kernel", "")
         # DRAM bytes come from the committed ncu record, which is of the fused kernel on the full
-        # lorenz_4M frame: only that workload and variant, on the same sources, gets it
-        recorded = (w["name"] == "lorenz_4M" and fused and every and packed and not args.particles
-                    and not args.frame_steps)
-        traffic = traffic_from_profile(kernel_source_hash()) if recorded else None
-        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 3), "unit": "TFLOP/s",
-                "frac": round(achieved / peak_tflops, 4), "traffic": traffic, "kernel": kernel,
-                "peak_basis": f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
-                "algorithmic_bytes_per_launch": 24 * n_work,
-                "launch_window": ("ff_step_splat: image clear + integrator with fused splat" if fused and every
-                                  else "ff_step: integrator"),
-                "avg_launch_ms": round(avg_int_ms, 4)}
-        if clk:
-            roof["frac_at_sampled_clock"] = round(achieved / (sms * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12), 4)
+        # lorenz_4M frame: only that workload and kernel, on the same sources, gets it
+        recorded = (w["name"] == "lorenz_4M" and fused and "lorenz_rk4_x2u_kernel<false, 2, true>" in kernel
+                    and not args.particles and not args.frame_steps)
+        roof.update({"traffic": traffic_from_profile(kernel_source_hash()) if recorded else None,
+                     "kernel": kernel, "grid": rec.get("grid"), "block": rec.get("block"),
+                     "kernel_reported_by": "ff_last_launch",
+                     "algorithmic_bytes_per_launch": 2 * 4 * w["dim"] * n_work,
+                     "launch_window": ("ff_step_splat: image clear + integrator with fused splat" if fused else
+                                       "ff_step_splat: integrator + splat kernel" if every else
+                                       "ff_step: integrator"),
+                     "avg_launch_ms": round(avg_int_ms, 4)})
+        if clk and roof["bound"] == "alu":
+            roof["frac_at_sampled_clock"] = round(
+                roof["achieved"] / (sms * FP32_LANES_PER_SM * 2 * clk["sm_mhz"] * 1e6 / 1e12), 4)
+    out = {"value": value, "ms_per_step": ms_per_step, "frames_per_s": w["frames"] / (ms_per_step / 1e3),
+           "gpu_launches": counted["launches"] * steps, "wall_s_timed_region": wall, "roofline": roof,
+           "clocks": clk or {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": [],
+                             "note": "not sampled (--no-clocks)" if not clocks_enabled else
+                             "timed region shorter than the 200 ms sampling interval"},
+           "particles": P, "steps": steps}
+    if with_e2e:
+        out["e2e"] = e2e_ours(args, sysobj, w, view, image, P, world, dev, reps=min(steps, 5))
+    sysobj.close()
+    return out
 
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    w = workload_for(args, rank, world)
+    rates = pipe_rates(local)
+    m = measure_workload(args, w, dev, stream, args.steps, args.warmup, not args.no_e2e, world, kahan=args.kahan,
+                         rates=rates, reset=args.reset, clocks_enabled=not args.no_clocks)
+    P = m["particles"]
+    Wd, H = w["view"]["width"], w["view"]["height"]
     result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["name"], "particles_per_gpu": P, "groups": [
             {"count": g["count"], "direction": g["direction"]} for g in w["groups"]],
-            "rk4_steps_per_job": steps_per_job, "frames": w["frames"], "steps_per_frame": w["steps_per_frame"],
+            "rk4_steps_per_job": total_steps(w), "frames": w["frames"], "steps_per_frame": w["steps_per_frame"],
             "dt": w["dt"], "image": f"{Wd}x{H}", "kahan": bool(args.kahan), "reset": bool(args.reset),
             "profiling_case": bool(args.particles or args.frames),
             "l2": "flushed (256 MB write) before every timed step", "parallelism": "dp%d-weak-shards" % world,
             "launch": {"particles_per_thread": args.ppt or "library default", "block": args.block or "library default",
                        "blocks_per_sm": args.blocks_per_sm}},
-        "frames_per_s": w["frames"] / (ms_per_step / 1e3),
-        "gpu_launches": launches,
-        "wall_s_timed_region": wall,
+        "frames_per_s": m["frames_per_s"],
+        "gpu_launches": m["gpu_launches"],
+        "wall_s_timed_region": m["wall_s_timed_region"],
+        "clocks": m["clocks"],
+        "pipe_rates": rates,
     }
-    if roof:
-        result["roofline"] = roof
-    # a timed region shorter than the sampling interval has no clock samples: say so
-    result["clocks"] = clk or {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": [],
-                               "note": "not sampled (--no-clocks)" if args.no_clocks else
-                               "timed region shorter than the 200 ms sampling interval"}
-
-    if not args.no_e2e:
-        result["e2e"] = e2e_ours(args, sysobj, w, view, image, P, world, dev)
+    if m["roofline"]:
+        result["roofline"] = m["roofline"]
+    if "e2e" in m:
+        result["e2e"] = m["e2e"]
+    default_run = (w["name"] == "lorenz_4M" and not (args.kahan or args.reset or args.particles or args.frames
+                                                     or args.frame_steps or args.ppt or args.block
+                                                     or args.blocks_per_sm or args.no_extras))
+    if default_run:
+        # the gradient half of the metric and the other workloads, each with its own clocks
+        result["adjoint"] = adjoint_record(args, w, dev, stream, world)
+        result["workloads"] = {}
+        for name, steps in (("hh3_1M", 2), ("lorenz_bif_8M", 3), ("wc_4k", 10)):
+            wl = W.shard(W.workload(name), rank, world)
+            r = measure_workload(args, wl, dev, stream, steps, 2 if name == "hh3_1M" else 3, not args.no_e2e, world,
+                                 rates=rates, clocks_enabled=not args.no_clocks)
+            r["metric"] = METRIC
+            r["unit"] = UNIT
+            result["workloads"][name] = r
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w)
-    sysobj.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return result
 
 
-def e2e_ours(args, sysobj, w, view, image, P, world, dev):
+def e2e_ours(args, sysobj, w, view, image, P, world, dev, reps=5):
     """Same metric through the public API with host buffers: each step uploads the initial state
     from pinned host memory (ff_set_state) and reads the final image back to pinned host memory
     (ff_project_splat with a host image)."""
@@ -405,7 +485,7 @@ def e2e_ours(args, sysobj, w, view, image, P, world, dev):
     job()
     torch.cuda.synchronize()
     times = []
-    for _ in range(max(1, min(args.steps, 5))):
+    for _ in range(max(1, min(args.steps, reps))):
         t0 = time.perf_counter()
         job()
         torch.cuda.synchronize()
@@ -477,23 +557,21 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_adjoint(args, rank, world, local):
-    """Gradients of L = (1/P) sum |x(T) - t|^2 w.r.t. initial states and parameters for the
-    workload's particles over --adjoint-steps RK4 steps (checkpoint every --checkpoint-every):
-    particle-steps/s of the plain forward, the taped forward and the adjoint sweep."""
+def adjoint_timings(w, n, K, steps, warmup, dev, stream, clocks_enabled=True):
+    """Plain forward, taped forward and adjoint sweep of n RK4 steps (checkpoint every K) for
+    the workload's particles: gradients of L = (1/P) sum |x(T) - t|^2 w.r.t. the initial
+    states and parameters.  CUDA events on the system's stream; median of `steps` runs."""
     import torch
     import paper_1505_00344_gb300 as ff
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    w = workload_for(args, rank, world)
-    P, dim, n, dt = total_particles(w), w["dim"], args.adjoint_steps, w["dt"]
-    s = ff.System.from_workload(w, stream=torch.cuda.current_stream().cuda_stream)
+    P, dim, dt = total_particles(w), w["dim"], w["dt"]
+    s = ff.System.from_workload(w, stream=stream)
     x0 = torch.empty((dim, P), dtype=torch.float32, device=dev)
     s.get_state(x0)
     target = torch.empty_like(x0).uniform_(-20.0, 20.0)
     dx0 = torch.empty_like(x0)
     n_params = len(w["params"])
+    grad = torch.empty_like(x0)
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -511,10 +589,8 @@ def run_adjoint(args, rank, world, local):
 
     def taped():
         s.set_state(x0)
-        s.tape_begin(args.checkpoint_every, n)
+        s.tape_begin(K, n)
         s.step(n, dt)
-
-    grad = torch.empty_like(x0)
 
     def backward():
         s.backward(grad, dx0, n_params)
@@ -526,30 +602,61 @@ def run_adjoint(args, rank, world, local):
         torch.mul(xT - target, 2.0 / P, out=grad)
         return tf, timed(backward)
 
-    # warm-up runs every kernel of the timed steps once (the first launch of a kernel also
-    # loads it)
-    for _ in range(args.warmup):
+    # warm-up runs every kernel of the timed steps once (the first launch of a kernel also loads it)
+    for _ in range(max(1, warmup)):
         plain()
         sweep()
-    t_plain = [timed(plain) for _ in range(max(1, args.steps))]
+    clocks = ClockSampler(dev.index, enabled=clocks_enabled)
+    t_plain = [timed(plain) for _ in range(max(1, steps))]
     t_fwd, t_bwd = [], []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, steps)):
         tf, tb = sweep()
         t_fwd.append(tf)
         t_bwd.append(tb)
+    clk = clocks.stop()
     s.tape_end()
+    s.close()
     units = P * n
     med = statistics.median
-    bwd = units / (med(t_bwd) / 1e3)
+    return {"value": units / (med(t_bwd) / 1e3), "unit": UNIT, "particles": P, "rk4_steps": n,
+            "checkpoint_every": K, "plain_forward": units / (med(t_plain) / 1e3),
+            "taped_forward": units / (med(t_fwd) / 1e3), "backward_over_plain_time": med(t_bwd) / med(t_plain),
+            "ms": {"plain": med(t_plain), "taped_forward": med(t_fwd), "backward": med(t_bwd)},
+            "clocks": clk or {"sm_mhz": None, "samples": 0, "reasons": [],
+                              "note": "timed region shorter than the 200 ms sampling interval"}}
+
+
+def adjoint_record(args, w, dev, stream, world):
+    """The gradient half of the metric inside the default bench line: lorenz_4M particles,
+    2,000 RK4 steps, checkpoint every 100."""
+    r = adjoint_timings(w, 2000, 100, 3, 2, dev, stream, clocks_enabled=not args.no_clocks)
+    r["metric"] = "adjoint particle-RK4-steps/sec (gradients w.r.t. initial states and parameters)"
+    r["loss"] = "mean squared distance of final states to random targets"
+    r["dtype"] = "f32 (FP64 parameter sums)"
+    r["value"] *= world
+    return r
+
+
+def run_adjoint(args, rank, world, local):
+    """Gradients of L = (1/P) sum |x(T) - t|^2 w.r.t. initial states and parameters for the
+    workload's particles over --adjoint-steps RK4 steps (checkpoint every --checkpoint-every):
+    particle-steps/s of the plain forward, the taped forward and the adjoint sweep."""
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload_for(args, rank, world)
+    r = adjoint_timings(w, args.adjoint_steps, args.checkpoint_every, args.steps, args.warmup, dev,
+                        torch.cuda.current_stream().cuda_stream, clocks_enabled=not args.no_clocks)
     return {"metric": "adjoint particle-RK4-steps/sec (gradients w.r.t. initial states and parameters)",
-            "value": bwd, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": med(t_bwd), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["ms"]["backward"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (FP64 parameter sums)", "data": "synthetic",
-            "config": {"workload": w["name"], "particles": P, "rk4_steps": n, "checkpoint_every": args.checkpoint_every,
+            "config": {"workload": w["name"], "particles": r["particles"], "rk4_steps": r["rk4_steps"],
+                       "checkpoint_every": r["checkpoint_every"],
                        "loss": "mean squared distance of final states to random targets"},
-            "plain_forward": units / (med(t_plain) / 1e3), "taped_forward": units / (med(t_fwd) / 1e3),
-            "backward_over_plain_time": med(t_bwd) / med(t_plain),
-            "ms": {"plain": med(t_plain), "taped_forward": med(t_fwd), "backward": med(t_bwd)}}
+            "plain_forward": r["plain_forward"], "taped_forward": r["taped_forward"],
+            "backward_over_plain_time": r["backward_over_plain_time"], "ms": r["ms"], "clocks": r["clocks"]}
 
 
 def run_batch_adjoint(args, rank, world, local):

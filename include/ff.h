@@ -281,6 +281,27 @@ ff_status ff_stats(ff_system* sys, int64_t* n_escaped, double* t_fwd, double* t_
 ff_status ff_system_info(ff_system* sys, int64_t* n_particles, int64_t* pitch, int* dim,
                          int* n_groups);
 
+/* What the last ff_step or ff_step_splat on this system launched (the paper's
+ * main loop, App. A "Running the Simulation", one integration call per frame;
+ * this call only reports, it launches nothing).  All outputs are NULL-able:
+ *   kernel, kernel_len   the integrator kernel of the call's last launch, its
+ *                        demangled C++ name (e.g. "void ff::lorenz_rk4_x2u_kernel
+ *                        <false, 2, true>(ff::IntegrateArgs)"), truncated to
+ *                        kernel_len - 1 characters and NUL-terminated; "" before
+ *                        the first launch;
+ *   grid, block          that launch's grid and block size;
+ *   fused_splat          1 if the projection and count splat ran inside that
+ *                        launch (ff_step_splat on the fused path), else 0;
+ *   integrator_launches  integrator launches the call made (a call is split at
+ *                        ff_set_launch's max_steps_per_launch and at 2^30 steps);
+ *   splat_launches       separate splat kernels of the last ff_step_splat or
+ *                        ff_project_splat (0 when the splat was fused).
+ * An ff_step of 0 steps launches nothing and leaves these values as they were.
+ * Errors: FF_ERR_INVALID_ARG for a NULL system or kernel_len < 1 with a
+ * kernel buffer; FF_ERR_CUDA if the runtime cannot name the kernel. */
+ff_status ff_last_launch(ff_system* sys, char* kernel, int kernel_len, int* grid, int* block, int* fused_splat,
+                         int64_t* integrator_launches, int64_t* splat_launches);
+
 /* Launch shape of the integrator: particles per thread (1, 2 or 4; at 2 and 4
  * each plane is read with one 8- or 16-byte access, and RK4 on Lorenz, plain or
  * compensated, then runs two particles per packed f32x2 instruction; the
@@ -384,6 +405,25 @@ ff_status ff_batch_backward(ff_batch* batch, const float* const* dL_dxT_dev, flo
                             double* dL_dp_host);
 ff_status ff_batch_destroy(ff_batch* batch);
 
+/* Instruction kinds of ff_pipe_rate. */
+#define FF_PIPE_FFMA 0  /* fma.rn.f32: one lane operation (2 flops) per thread instruction */
+#define FF_PIPE_FFMA2 1 /* fma.rn.f32x2: two lane operations per thread instruction */
+#define FF_PIPE_EX2 2   /* ex2.approx.ftz.f32 (multi-function unit) */
+#define FF_PIPE_RCP 3   /* rcp.approx.ftz.f32 (multi-function unit) */
+
+/* Issue-rate microbenchmark of one instruction kind on `device` (not part of
+ * the paper's method: it supplies the measured denominators of the
+ * integrators' ALU rooflines, Table 1's per-step cost being their arithmetic).
+ * Every thread of a full-occupancy grid runs eight independent dependency
+ * chains of the instruction for 4,096 iterations; the launch is timed with
+ * events after one warm-up launch.  *lane_ops_per_s receives the lane
+ * operations per second over the whole device (an FFMA2 counts two; multiply
+ * FMA rates by 2 for flops).  The call allocates a small buffer, creates and
+ * destroys its own stream and events, synchronises, and takes a few
+ * milliseconds.  Errors: FF_ERR_INVALID_ARG for a NULL output or unknown op,
+ * FF_ERR_CUDA if the device cannot run it. */
+ff_status ff_pipe_rate(int op, int device, double* lane_ops_per_s);
+
 /* Most groups ff_count_escaped_noalloc accepts (its fixed scratch holds one
  * 64-bit counter per group: 2 KB per GPU). */
 #define FF_NOALLOC_MAX_GROUPS 256
@@ -405,14 +445,18 @@ ff_status ff_batch_destroy(ff_batch* batch);
  *   counts_out    host array of n_groups int64: escaped particles per group,
  *                 with the escape test of ff_stats (a component non-finite or
  *                 above 1e30 in magnitude).
- * The call synchronises the stream before returning.  It calls no
- * cudaMalloc or cudaFree: its only scratch is a fixed device array of
- * FF_NOALLOC_MAX_GROUPS counters in the library, present on every GPU that
- * loads the library until the process exits.  The first call on each device
- * looks up that array's device address (cudaGetSymbolAddress), so make the
- * first call on a device before any stream capture.  All calls on a device
- * share the array and each clears the counters it uses: calls that overlap on
- * the GPU (concurrent streams or threads) race and give wrong counts.
+ * The call synchronises the stream before returning, and it copies the
+ * counts to pageable host memory: it cannot be called while its stream (or
+ * the legacy default stream) is being captured into a CUDA graph, on any
+ * call.  It calls no cudaMalloc or cudaFree: its only scratch is a fixed
+ * device array of FF_NOALLOC_MAX_GROUPS counters in the library, present on
+ * every GPU that loads the library until the process exits.  The first call
+ * on each device looks up that array's device address (cudaGetSymbolAddress)
+ * and keeps it for the process; after cudaDeviceReset on a device the kept
+ * address is stale, so do not call this entry point on that device again.
+ * All calls on a device share the array and each clears the counters it
+ * uses: calls that overlap on the GPU (concurrent streams or threads) race
+ * and give wrong counts.
  * Errors: FF_ERR_INVALID_ARG for NULL pointers, dim outside 1..FF_MAX_DIM,
  * n_particles < 0, pitch < n_particles, n_groups outside
  * 1..FF_NOALLOC_MAX_GROUPS, or badly ordered group_starts; FF_ERR_CUDA if a

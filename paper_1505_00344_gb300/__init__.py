@@ -93,8 +93,11 @@ _SIGS = {
     "ff_system_info": [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(ctypes.c_int)],
     "ff_set_launch": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I64],
+    "ff_last_launch": [_P, ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "ff_backward": [_P, _P, _P, _P],
     "ff_count_escaped_noalloc": [_P, ctypes.c_int, _I64, _I64, _P, ctypes.c_int, _P, _P],
+    "ff_pipe_rate": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
     "ff_set_reset": [_P, _P, _P, ctypes.c_double, ctypes.c_int],
     "ff_tape_begin": [_P, _I64, _I64],
     "ff_batch_create": [_P, ctypes.c_int, _P, ctypes.POINTER(_P)],
@@ -133,8 +136,13 @@ def _check(status):
         raise FFError(status, lib().ff_last_error().decode(errors="replace"))
 
 
-def _buf(obj, dtype=None):
-    """(pointer, is_device, keepalive) of a torch tensor, numpy array or int device pointer."""
+def _buf(obj, dtype=None, min_elems=0):
+    """(pointer, is_device, keepalive) of a torch tensor, numpy array or int device pointer.
+
+    With ``dtype`` the array or tensor must hold that element type (a uint32 buffer
+    may also be an int32 tensor, as torch images usually are); with ``min_elems``
+    it must hold at least that many elements.  A raw int pointer is taken as is.
+    """
     if obj is None:
         return None, 0, None
     if isinstance(obj, int):
@@ -143,14 +151,40 @@ def _buf(obj, dtype=None):
         if not obj.flags.c_contiguous:
             raise ValueError("host arrays must be C-contiguous")
         if dtype is not None and obj.dtype != dtype:
-            raise ValueError(f"expected dtype {dtype}, got {obj.dtype}")
+            raise ValueError(f"expected dtype {np.dtype(dtype).name}, got {obj.dtype}")
+        if obj.size < min_elems:
+            raise ValueError(f"buffer holds {obj.size} elements, the call needs {min_elems}")
         return obj.ctypes.data, 0, obj
     # torch tensor (duck-typed so torch stays optional for host-only callers)
     if hasattr(obj, "data_ptr") and hasattr(obj, "is_cuda"):
         if not obj.is_contiguous():
             raise ValueError("tensors must be contiguous")
+        if dtype is not None:
+            want = np.dtype(dtype).name
+            got = str(obj.dtype).replace("torch.", "")
+            if got != want and not (want == "uint32" and got == "int32"):
+                raise ValueError(f"expected dtype {want}, got {got}")
+        if obj.numel() < min_elems:
+            raise ValueError(f"buffer holds {obj.numel()} elements, the call needs {min_elems}")
         return obj.data_ptr(), 1 if obj.is_cuda else 0, obj
     raise TypeError(f"unsupported buffer type {type(obj)}")
+
+
+def _image_buf(image, view, channels=1, dtype=None):
+    """_buf of an image of view.width x view.height x channels 4-byte elements
+    (counts: uint32 or int32; sprites: float32)."""
+    need = max(int(view.width), 0) * max(int(view.height), 0) * channels
+    if dtype is None and isinstance(image, np.ndarray) and image.dtype not in (np.uint32, np.int32):
+        raise ValueError(f"count images are uint32 or int32, got {image.dtype}")
+    if dtype is None and hasattr(image, "element_size") and not isinstance(image, np.ndarray):
+        if str(image.dtype).replace("torch.", "") not in ("int32", "uint32"):
+            raise ValueError(f"count images are uint32 or int32, got {image.dtype}")
+    return _buf(image, dtype, min_elems=need)
+
+
+def _state_elems(sys):
+    n, _, dim, _ = ff_system_info(sys)
+    return n * dim
 
 
 def _dbl(v):
@@ -256,14 +290,14 @@ def make_view(ndim_view=2, axes=(0, 1), lo=(0.0, 0.0), hi=(1.0, 1.0), mvp=None, 
 def ff_project_splat(sys, view, image):
     if isinstance(view, dict):
         view = make_view(**view)
-    ptr, dev, _keep = _buf(image)
+    ptr, dev, _keep = _image_buf(image, view)
     _check(lib().ff_project_splat(sys, ctypes.byref(view), ptr, dev))
 
 
 def ff_step_splat(sys, n_steps, dt, view, image):
     if isinstance(view, dict):
         view = make_view(**view)
-    ptr, dev, _keep = _buf(image)
+    ptr, dev, _keep = _image_buf(image, view)
     _check(lib().ff_step_splat(sys, int(n_steps), float(dt), ctypes.byref(view), ptr, dev))
 
 
@@ -273,17 +307,17 @@ def ff_project_sprites(sys, view, sprite, image):
         view = make_view(**view)
     if isinstance(sprite, dict):
         sprite = make_sprite(**sprite)
-    ptr, dev, _keep = _buf(image, np.float32)
+    ptr, dev, _keep = _image_buf(image, view, channels=4, dtype=np.float32)
     _check(lib().ff_project_sprites(sys, ctypes.byref(view), ctypes.byref(sprite), ptr, dev))
 
 
 def ff_get_state(sys, dst):
-    ptr, dev, _keep = _buf(dst, np.float32)
+    ptr, dev, _keep = _buf(dst, np.float32, min_elems=_state_elems(sys))
     _check(lib().ff_get_state(sys, ptr, dev))
 
 
 def ff_set_state(sys, src):
-    ptr, dev, _keep = _buf(src, np.float32)
+    ptr, dev, _keep = _buf(src, np.float32, min_elems=_state_elems(sys))
     _check(lib().ff_set_state(sys, ptr, dev))
 
 
@@ -302,6 +336,18 @@ def ff_system_info(sys):
     ng = ctypes.c_int(0)
     _check(lib().ff_system_info(sys, ctypes.byref(n), ctypes.byref(pitch), ctypes.byref(dim), ctypes.byref(ng)))
     return n.value, pitch.value, dim.value, ng.value
+
+
+def ff_last_launch(sys):
+    """What the last ff_step / ff_step_splat launched: dict with the integrator kernel's
+    name, grid, block, whether the splat was fused into it, and the launch counts."""
+    buf = ctypes.create_string_buffer(512)
+    grid, block, fused = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    n_int, n_splat = _I64(0), _I64(0)
+    _check(lib().ff_last_launch(sys, buf, len(buf), ctypes.byref(grid), ctypes.byref(block), ctypes.byref(fused),
+                                ctypes.byref(n_int), ctypes.byref(n_splat)))
+    return {"kernel": buf.value.decode(), "grid": grid.value, "block": block.value, "fused_splat": bool(fused.value),
+            "integrator_launches": n_int.value, "splat_launches": n_splat.value}
 
 
 def ff_set_launch(sys, particles_per_thread=1, block=256, blocks_per_sm=0, max_steps_per_launch=0):
@@ -334,21 +380,35 @@ def ff_backward(sys, dL_dxT, dL_dx0, dL_dp=None):
 
 
 FF_NOALLOC_MAX_GROUPS = 256
+FF_PIPE_FFMA, FF_PIPE_FFMA2, FF_PIPE_EX2, FF_PIPE_RCP = range(4)
+
+
+def ff_pipe_rate(op, device=0):
+    """Measured lane operations per second of one instruction kind (FF_PIPE_*) on a device."""
+    out = ctypes.c_double(0.0)
+    _check(lib().ff_pipe_rate(int(op), int(device), ctypes.byref(out)))
+    return out.value
 
 
 def ff_count_escaped_noalloc(state, dim, n_particles, pitch, group_starts, stream=None):
     """Escaped particles per group of a device SoA state, without any device allocation.
 
     For callers that must not allocate device memory at call time (see
-    include/ff.h); ``state`` is a device buffer (tensor or pointer), the
-    result a host int64 array with one count per group.
+    include/ff.h); ``state`` is a device buffer (float32 tensor or pointer) of at
+    least (dim - 1) * pitch + n_particles floats, the result a host int64 array
+    with one count per group.  A tensor of another dtype or too few elements is
+    rejected here, before anything reaches the GPU.
     """
-    ptr, dev, _keep = _buf(state)
+    dim, n_particles, pitch = int(dim), int(n_particles), int(pitch)
+    if dim < 1 or n_particles < 0 or pitch < n_particles:
+        raise ValueError("dim must be >= 1 and 0 <= n_particles <= pitch")
+    need = (dim - 1) * pitch + n_particles if n_particles > 0 else 0
+    ptr, dev, _keep = _buf(state, np.float32, min_elems=need)
     if not dev:
         raise ValueError("state must be device memory")
     starts = np.ascontiguousarray(np.asarray(group_starts, dtype=np.int64).reshape(-1))
     counts = np.zeros(starts.size, dtype=np.int64)
-    _check(lib().ff_count_escaped_noalloc(ptr, int(dim), int(n_particles), int(pitch), starts.ctypes.data,
+    _check(lib().ff_count_escaped_noalloc(ptr, dim, n_particles, pitch, starts.ctypes.data,
                                           starts.size, _stream_ptr(stream), counts.ctypes.data))
     return counts
 
@@ -530,6 +590,10 @@ class System:
 
     def info(self):
         return ff_system_info(self.handle)
+
+    def last_launch(self):
+        """ff_last_launch: the integrator kernel, shape and fusion of the last step call."""
+        return ff_last_launch(self.handle)
 
     def set_launch(self, particles_per_thread=0, block=0, blocks_per_sm=0, max_steps_per_launch=0):
         """Launch shape (0 keeps the current particles per thread or block size)."""

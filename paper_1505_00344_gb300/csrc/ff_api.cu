@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <cxxabi.h>
 #include <new>
 #include <string>
 
@@ -481,6 +483,9 @@ static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const
         a.max_age = steps <= 0.0 ? 0u : (steps >= 4294967295.0 ? 4294967295u : (uint32_t)steps);
     }
     int64_t left = n_steps;
+    s->last_integrator_launches = 0;
+    s->last_splat_launches = 0;
+    s->last_fused = false;
     while (left > 0) {
         int64_t chunk = (s->max_steps > 0 && left > s->max_steps) ? s->max_steps : left;
         if (chunk > ((int64_t)1 << 30)) chunk = (int64_t)1 << 30;  // kernels count steps in 32 bits
@@ -501,13 +506,20 @@ static ff_status integrate_steps(ff_system* s, int64_t n_steps, double dt, const
             }
         }
         cudaError_t e;
-        if (fuse && chunk == left) {
+        ff::last_launch_record() = ff::LaunchRecord{};
+        const bool fused = fuse && chunk == left;
+        if (fused) {
             a.view = *fuse;
             e = ff::launch_integrate_lorenz_splat(pp, a, shape, s->stream);
         } else {
             e = ff::launch_integrate(s->rhs_id, s->method, kahan, pp, a, shape, s->stream);
         }
         if (e != cudaSuccess) return cuda_fail(e, "integrator launch");
+        if (ff::last_launch_record().kernel) {
+            s->last_integrator = ff::last_launch_record();
+            s->last_integrator_launches += 1;
+            s->last_fused = fused;
+        }
         left -= chunk;
         s->steps_total += chunk;
     }
@@ -762,9 +774,11 @@ ff_status ff_project_splat(ff_system* s, const ff_view* v, uint32_t* image, int 
     a.v.image = static_cast<uint32_t*>(target);
     bool strip = false;  // a linspace parameter on an axis: consecutive particles share a column or row
     for (int q = 0; q < v->ndim_view; ++q) strip = strip || (v->axes[q] == s->dim && s->pparam_linspace);
+    s->last_splat_launches = 0;
     if (s->n_particles > 0 && a.v.mask != 0) {
         e = ff::launch_splat(a, v->ndim_view, masked, strip, s->num_sms, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "splat kernel launch");
+        s->last_splat_launches = 1;
     }
     return image_end(s, image, image_is_device, bytes, target, "ff_project_splat");
 }
@@ -867,7 +881,10 @@ ff_status ff_step_splat(ff_system* s, int64_t n_steps, double dt, const ff_view*
     if (!fusable) {
         st = ff_step(s, n_steps, dt);
         if (st != FF_OK) return st;
-        return ff_project_splat(s, v, image, image_is_device);
+        const int64_t integrator_launches = s->last_integrator_launches;
+        st = ff_project_splat(s, v, image, image_is_device);
+        s->last_integrator_launches = integrator_launches;  // ff_project_splat counted only its own
+        return st;
     }
     DeviceScope dev(s->device);
     if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_step_splat: set device");
@@ -939,12 +956,39 @@ ff_status ff_system_info(ff_system* s, int64_t* n_particles, int64_t* pitch, int
     return FF_OK;
 }
 
+ff_status ff_last_launch(ff_system* s, char* kernel, int kernel_len, int* grid, int* block, int* fused_splat,
+                         int64_t* integrator_launches, int64_t* splat_launches) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_last_launch: system is NULL");
+    if (kernel && kernel_len < 1) return fail(FF_ERR_INVALID_ARG, "ff_last_launch: kernel_len < 1");
+    if (grid) *grid = s->last_integrator.grid;
+    if (block) *block = s->last_integrator.block;
+    if (fused_splat) *fused_splat = s->last_fused ? 1 : 0;
+    if (integrator_launches) *integrator_launches = s->last_integrator_launches;
+    if (splat_launches) *splat_launches = s->last_splat_launches;
+    if (!kernel) return FF_OK;
+    kernel[0] = '\0';
+    if (!s->last_integrator.kernel) return FF_OK;
+    const char* mangled = nullptr;
+    cudaError_t e = cudaFuncGetName(&mangled, s->last_integrator.kernel);
+    if (e != cudaSuccess || !mangled) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidValue : e, "ff_last_launch: kernel name");
+    int rc = -1;
+    char* plain = abi::__cxa_demangle(mangled, nullptr, nullptr, &rc);
+    snprintf(kernel, (size_t)kernel_len, "%s", (rc == 0 && plain) ? plain : mangled);
+    std::free(plain);
+    return FF_OK;
+}
+
 
 }  // extern "C"
 
 namespace ff {
 // Lets entry points defined in other translation units report through ff_last_error().
 void set_last_error_message(const char* msg) { g_last_error = msg; }
+
+LaunchRecord& last_launch_record() {
+    static thread_local LaunchRecord record;
+    return record;
+}
 
 cudaError_t launch_integrate(int rhs_id, int method, bool kahan, bool pp, const IntegrateArgs& a,
                              const LaunchShape& shape, cudaStream_t stream) {

@@ -1012,6 +1012,14 @@ inline int spread_block(int block, int64_t items, int num_sms) {
     return b < 32 ? 32 : (b < block ? (int)b : block);
 }
 
+// The integrator kernel a launch helper last started on this host thread, with
+// its grid and block (ff_last_launch reports it; defined in ff_api.cu).
+struct LaunchRecord {
+    const void* kernel = nullptr;
+    int grid = 0, block = 0;
+};
+LaunchRecord& last_launch_record();
+
 // Grid for a persistent launch: enough blocks to cover the work, at most
 // blocks_per_sm (or the occupancy limit) per SM.  The block size is clamped to
 // the kernel's compiled maximum (its launch bound).
@@ -1034,6 +1042,7 @@ inline cudaError_t persistent_launch(Kernel kernel, const IntegrateArgs& a, cons
     const int grid = (int)(need < cap ? need : cap);
     if (grid < 1) return cudaSuccess;
     kernel<<<grid, s.block, 0, stream>>>(a);
+    last_launch_record() = LaunchRecord{(const void*)kernel, grid, s.block};
     return cudaGetLastError();
 }
 
@@ -1110,6 +1119,7 @@ inline cudaError_t uniform_launch(Kernel kernel, const IntegrateArgs& a0, const 
     }
     a.gblk[a.n_groups] = next;
     kernel<<<next, s.block, 0, stream>>>(a);
+    last_launch_record() = LaunchRecord{(const void*)kernel, next, s.block};
     return cudaGetLastError();
 }
 

@@ -103,6 +103,10 @@ struct ff_system {
     std::vector<ff::AdjChunk> chunks;
     int64_t params_version = 0, chunk_version = -1;
     double chunk_dt = 0.0;
+    // what the last ff_step / ff_step_splat launched (ff_last_launch)
+    ff::LaunchRecord last_integrator{};
+    int64_t last_integrator_launches = 0, last_splat_launches = 0;
+    bool last_fused = false;
 };
 
 namespace ff {

@@ -233,11 +233,16 @@ def pipe_rates(device_index):
     """Measured lane-operation rates of the integrators' instruction kinds (ff_pipe_rate)."""
     import paper_1505_00344_gb300 as ff
 
-    return {"ffma_lane_ops_per_s": ff.ff_pipe_rate(ff.FF_PIPE_FFMA, device_index),
-            "ffma2_lane_ops_per_s": ff.ff_pipe_rate(ff.FF_PIPE_FFMA2, device_index),
-            "ex2_per_s": ff.ff_pipe_rate(ff.FF_PIPE_EX2, device_index),
-            "rcp_per_s": ff.ff_pipe_rate(ff.FF_PIPE_RCP, device_index),
-            "how": "ff_pipe_rate: 8 independent chains per thread, full occupancy, 4096 iterations, CUDA events"}
+    r = {"ffma_lane_ops_per_s": ff.ff_pipe_rate(ff.FF_PIPE_FFMA, device_index),
+         "ffma2_lane_ops_per_s": ff.ff_pipe_rate(ff.FF_PIPE_FFMA2, device_index),
+         "ex2_per_s": ff.ff_pipe_rate(ff.FF_PIPE_EX2, device_index),
+         "rcp_per_s": ff.ff_pipe_rate(ff.FF_PIPE_RCP, device_index),
+         "logistic_mufu_ops_per_s": ff.ff_pipe_rate(ff.FF_PIPE_LOGISTIC, device_index),
+         "how": "ff_pipe_rate: 8 independent chains per thread, full occupancy, 4096 iterations, CUDA events"}
+    # ex2 and rcp share the multi-function unit when the logistic chain (one of each) runs at
+    # 2 / (1/ex2 + 1/rcp); the MUFU rooflines use that model
+    r["shared_unit_model_logistic"] = 2.0 / (1.0 / r["ex2_per_s"] + 1.0 / r["rcp_per_s"])
+    return r
 
 
 def roofline_for(w, n_work, avg_launch_ms, steps_per_launch, sms, max_mhz, rates, kahan=False):

@@ -409,7 +409,10 @@ ff_status ff_batch_destroy(ff_batch* batch);
 #define FF_PIPE_FFMA 0  /* fma.rn.f32: one lane operation (2 flops) per thread instruction */
 #define FF_PIPE_FFMA2 1 /* fma.rn.f32x2: two lane operations per thread instruction */
 #define FF_PIPE_EX2 2   /* ex2.approx.ftz.f32 (multi-function unit) */
-#define FF_PIPE_RCP 3   /* rcp.approx.ftz.f32 (multi-function unit) */
+#define FF_PIPE_RCP 3   /* rcp.approx.ftz.f32 (multi-function unit), each followed by an FP32 add,
+                           since a chain of reciprocals alone is an involution the compiler removes */
+#define FF_PIPE_LOGISTIC 4 /* 1 / (1 + 2^-a): ex2, add, rcp -- the sigmoid of the Wilson-Cowan
+                              right-hand side; counts two operations (ex2 and rcp) per step */
 
 /* Issue-rate microbenchmark of one instruction kind on `device` (not part of
  * the paper's method: it supplies the measured denominators of the
@@ -417,8 +420,8 @@ ff_status ff_batch_destroy(ff_batch* batch);
  * Every thread of a full-occupancy grid runs eight independent dependency
  * chains of the instruction for 4,096 iterations; the launch is timed with
  * events after one warm-up launch.  *lane_ops_per_s receives the lane
- * operations per second over the whole device (an FFMA2 counts two; multiply
- * FMA rates by 2 for flops).  The call allocates a small buffer, creates and
+ * operations per second over the whole device (an FFMA2 counts two, a logistic
+ * step its two multi-function operations; multiply FMA rates by 2 for flops).  The call allocates a small buffer, creates and
  * destroys its own stream and events, synchronises, and takes a few
  * milliseconds.  Errors: FF_ERR_INVALID_ARG for a NULL output or unknown op,
  * FF_ERR_CUDA if the device cannot run it. */

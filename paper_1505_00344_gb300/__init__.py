@@ -380,7 +380,7 @@ def ff_backward(sys, dL_dxT, dL_dx0, dL_dp=None):
 
 
 FF_NOALLOC_MAX_GROUPS = 256
-FF_PIPE_FFMA, FF_PIPE_FFMA2, FF_PIPE_EX2, FF_PIPE_RCP = range(4)
+FF_PIPE_FFMA, FF_PIPE_FFMA2, FF_PIPE_EX2, FF_PIPE_RCP, FF_PIPE_LOGISTIC = range(5)
 
 
 def ff_pipe_rate(op, device=0):

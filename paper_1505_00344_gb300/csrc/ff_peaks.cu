@@ -26,12 +26,18 @@ constexpr int kChains = 8;
 
 // One step of a chain of instruction kind OP.  Every chain stays finite and
 // bounded: FMA contracts towards a fixed point, ex2 of a negated value stays in
-// [0.5, 1], a reciprocal alternates between a value and its inverse.
+// [0.5, 1].  A chain of reciprocals alone would be an involution the compiler
+// removes, so each reciprocal is followed by an FP32 add (a = 1/a + 0.001 stays
+// near 1; the add runs on the FMA pipe beside it).  The logistic chain is the
+// Wilson-Cowan sigmoid's own sequence, 1 / (1 + 2^-a): one ex2, one add, one
+// reciprocal, so its rate shows how the two multi-function operations share
+// the hardware.
 template <int OP>
 __device__ __forceinline__ float chain_step(float a) {
     if constexpr (OP == FF_PIPE_FFMA) return fmaf(a, 0.999999f, 1e-7f);
     else if constexpr (OP == FF_PIPE_EX2) return ff::ex2_ftz(-a);
-    else return ff::rcp_ftz(a);
+    else if constexpr (OP == FF_PIPE_RCP) return __fadd_rn(ff::rcp_ftz(a), 0.001f);
+    else return ff::rcp_ftz(__fadd_rn(1.0f, ff::ex2_ftz(-a)));
 }
 
 template <int OP>
@@ -81,6 +87,7 @@ cudaError_t launch_op(int op, float* out, int grid, int iters, cudaStream_t st) 
     case FF_PIPE_FFMA2: return launch_pipe<FF_PIPE_FFMA2>(out, grid, iters, st);
     case FF_PIPE_EX2: return launch_pipe<FF_PIPE_EX2>(out, grid, iters, st);
     case FF_PIPE_RCP: return launch_pipe<FF_PIPE_RCP>(out, grid, iters, st);
+    case FF_PIPE_LOGISTIC: return launch_pipe<FF_PIPE_LOGISTIC>(out, grid, iters, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -90,11 +97,23 @@ ff_status fail(ff_status s, const char* msg) {
     return s;
 }
 
+// Milliseconds of one timed launch of instruction kind op (after a warm-up launch).
+cudaError_t time_op(int op, float* out, int grid, int iters, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1,
+                    float* ms) {
+    cudaError_t e = launch_op(op, out, grid, iters / 8, st);
+    if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+    if (e == cudaSuccess) e = launch_op(op, out, grid, iters, st);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, t0, t1);
+    return e;
+}
+
 }  // namespace
 
 extern "C" ff_status ff_pipe_rate(int op, int device, double* lane_ops_per_s) {
     if (!lane_ops_per_s) return fail(FF_ERR_INVALID_ARG, "ff_pipe_rate: NULL output");
-    if (op < FF_PIPE_FFMA || op > FF_PIPE_RCP) return fail(FF_ERR_INVALID_ARG, "ff_pipe_rate: unknown op");
+    if (op < FF_PIPE_FFMA || op > FF_PIPE_LOGISTIC) return fail(FF_ERR_INVALID_ARG, "ff_pipe_rate: unknown op");
     int prev = -1;
     cudaError_t e = cudaGetDevice(&prev);
     if (e == cudaSuccess && prev != device) e = cudaSetDevice(device);
@@ -106,10 +125,6 @@ extern "C" ff_status ff_pipe_rate(int op, int device, double* lane_ops_per_s) {
     float ms = 0.0f;
     const int iters = 4096;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) {
-        cudaFuncAttributes attr;
-        e = cudaFuncGetAttributes(&attr, (const void*)pipe_kernel<FF_PIPE_FFMA>);
-    }
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_kernel<FF_PIPE_FFMA2>, 256, 0);
     const int grid = sms * (per_sm > 0 ? per_sm : 1);
@@ -117,20 +132,15 @@ extern "C" ff_status ff_pipe_rate(int op, int device, double* lane_ops_per_s) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    // one warm-up launch (loads the module), then the timed one
-    if (e == cudaSuccess) e = launch_op(op, out, grid, iters / 8, st);
-    if (e == cudaSuccess) e = cudaEventRecord(t0, st);
-    if (e == cudaSuccess) e = launch_op(op, out, grid, iters, st);
-    if (e == cudaSuccess) e = cudaEventRecord(t1, st);
-    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    if (e == cudaSuccess) e = time_op(op, out, grid, iters, st, t0, t1, &ms);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     if (st) cudaStreamDestroy(st);
     if (out) cudaFree(out);
     if (prev >= 0 && prev != device) cudaSetDevice(prev);
     if (e != cudaSuccess || ms <= 0.0f) return fail(FF_ERR_CUDA, "ff_pipe_rate: measurement failed");
-    const double lanes = (op == FF_PIPE_FFMA2) ? 2.0 : 1.0;
+    // lane operations per chain step: two for a packed FMA, ex2 + rcp for the logistic
+    const double lanes = (op == FF_PIPE_FFMA2 || op == FF_PIPE_LOGISTIC) ? 2.0 : 1.0;
     *lane_ops_per_s = (double)grid * 256.0 * kChains * (double)iters * lanes / (ms * 1e-3);
     return FF_OK;
 }

@@ -461,7 +461,8 @@ FUSE_VIEWS = {
     ("xz_group1", (3000, 1000), 2, False, False, True),  # fused, masked, accumulating
     ("cam3d", (1001,), 4, False, False, False),           # fused, ragged count (padding not drawn)
     ("r_axis", (2048, 1024), 4, False, True, False),      # fused with per-particle r
-    ("xz", (3000, 1001), 4, False, False, False),        # misaligned group: separate calls
+    ("xz", (3000, 1001), 4, False, False, False),        # ragged total (padded last item): fused
+    ("xz", (3001, 1000), 4, False, False, False),        # group start not a multiple of 4: separate calls
     ("xz", (3000, 1000), 4, True, False, False),         # Kahan: separate calls
     ("xz", (3000, 1000), 1, False, False, False),        # scalar kernel: separate calls
 ])
@@ -489,7 +490,8 @@ def test_step_splat_equals_step_then_splat(view_name, counts, ppt, kahan, pp, ac
 @pytest.mark.parametrize("counts,ppt,kahan,expect,fused", [
     ((3000, 1000), 4, False, "lorenz_rk4_x2u_kernel<false, 2, true>", True),   # the bench's fused path
     ((3000, 1000), 2, False, "lorenz_rk4_x2u_kernel<false, 1, true>", True),
-    ((3000, 1001), 4, False, "lorenz_rk4_x2_kernel<false, 2>", False),          # misaligned group
+    ((3000, 1001), 4, False, "lorenz_rk4_x2u_kernel<false, 2, true>", True),   # ragged total: padded tail
+    ((3001, 1000), 4, False, "lorenz_rk4_x2_kernel<false, 2>", False),          # group start not a multiple of 4
     ((3000, 1000), 2, True, "lorenz_rk4_kahan_x2u_kernel", False),
     ((3000, 1000), 1, False, "integrate_kernel<ff::Lorenz, 0, false, false, 1", False),
 ])

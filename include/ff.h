@@ -135,6 +135,20 @@ ff_status ff_destroy_system(ff_system* sys);
 ff_status ff_seed_particles(ff_system* sys, int64_t count, const double* lo, const double* hi,
                             int direction, uint64_t seed, int* group_id_out);
 
+/* One contiguous slice of a larger particle group, for splitting one ensemble
+ * across GPUs (one process per GPU, each holding a contiguous range of the
+ * particle indices; the paper runs one GPU, Sec. 4): the `count` particles
+ * appended are particles first .. first + count - 1 of a group of `total`
+ * particles with this box, direction and seed.  Particle j of the slice takes
+ * the draws of group particle first + j (n = (first + j)*dim + k + 1), and an
+ * in-kernel reset (ff_set_reset) re-draws it as that group particle, so the
+ * union of the slices is, bit for bit, the ensemble of a system that seeds the
+ * whole group.  ff_seed_particles(sys, count, ...) is the slice (0, count).
+ * Errors: as ff_seed_particles, and FF_ERR_INVALID_ARG unless
+ * 0 <= first <= total - count. */
+ff_status ff_seed_particles_slice(ff_system* sys, int64_t count, int64_t first, int64_t total, const double* lo,
+                                  const double* hi, int direction, uint64_t seed, int* group_id_out);
+
 /* Restart: re-seed every group from its box and seed, clear the Kahan
  * compensation and simulated times (the paper re-initialises the GPU when a
  * system is modified, Appendix A). Per-particle parameters are kept. */
@@ -147,6 +161,15 @@ ff_status ff_reset(ff_system* sys);
  * Errors: FF_ERR_INVALID_ARG for an index out of range or non-finite bounds;
  * FF_ERR_STATE if no particles are seeded. */
 ff_status ff_set_particle_param(ff_system* sys, int param_index, double lo, double hi);
+
+/* The same linspace for a system holding particles first .. first + P - 1 of
+ * an ensemble of `total` (one GPU's share of a split ensemble): its particle j
+ * gets lo + (hi - lo) * ((first + j) / (total - 1)), the value particle
+ * first + j has in the whole ensemble.  ff_set_particle_param is the slice
+ * (0, P).  Errors: as ff_set_particle_param, and FF_ERR_INVALID_ARG unless
+ * 0 <= first <= total - P. */
+ff_status ff_set_particle_param_slice(ff_system* sys, int param_index, double lo, double hi, int64_t first,
+                                      int64_t total);
 
 /* Same, with caller-supplied per-particle values (P floats, host or device). */
 ff_status ff_set_particle_param_values(ff_system* sys, int param_index, const float* values,

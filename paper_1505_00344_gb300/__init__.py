@@ -78,6 +78,9 @@ _SIGS = {
                          ctypes.POINTER(_P)],
     "ff_destroy_system": [_P],
     "ff_seed_particles": [_P, _I64, _P, _P, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)],
+    "ff_seed_particles_slice": [_P, _I64, _I64, _I64, _P, _P, ctypes.c_int, ctypes.c_uint64,
+                                ctypes.POINTER(ctypes.c_int)],
+    "ff_set_particle_param_slice": [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _I64, _I64],
     "ff_reset": [_P],
     "ff_set_particle_param": [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double],
     "ff_set_particle_param_values": [_P, ctypes.c_int, _P, ctypes.c_int],
@@ -219,6 +222,20 @@ def ff_seed_particles(sys, count, lo, hi, direction, seed):
     _check(lib().ff_seed_particles(sys, int(count), lo_p, hi_p, int(direction), int(seed) & (2**64 - 1),
                                    ctypes.byref(gid)))
     return gid.value
+
+
+def ff_seed_particles_slice(sys, count, first, total, lo, hi, direction, seed):
+    """Particles first .. first + count - 1 of a group of `total` (one GPU's share)."""
+    lo_a, lo_p = _dbl(lo)
+    hi_a, hi_p = _dbl(hi)
+    gid = ctypes.c_int(-1)
+    _check(lib().ff_seed_particles_slice(sys, int(count), int(first), int(total), lo_p, hi_p, int(direction),
+                                         int(seed) & (2**64 - 1), ctypes.byref(gid)))
+    return gid.value
+
+
+def ff_set_particle_param_slice(sys, param_index, lo, hi, first, total):
+    _check(lib().ff_set_particle_param_slice(sys, int(param_index), float(lo), float(hi), int(first), int(total)))
 
 
 def ff_reset(sys):
@@ -535,6 +552,12 @@ class System:
 
     def seed(self, count, lo, hi, direction, seed):
         return ff_seed_particles(self.handle, count, lo, hi, direction, seed)
+
+    def seed_slice(self, count, first, total, lo, hi, direction, seed):
+        return ff_seed_particles_slice(self.handle, count, first, total, lo, hi, direction, seed)
+
+    def set_particle_param_slice(self, index, lo, hi, first, total):
+        ff_set_particle_param_slice(self.handle, index, lo, hi, first, total)
 
     def reset(self):
         ff_reset(self.handle)

@@ -5,9 +5,10 @@
 // One thread per particle walks the chunks in reverse with the adjoint state
 // lambda = dL/dx in registers.  A chunk of L <= M*M steps is recomputed from its
 // checkpoint twice (once when L <= M): once to place sub-checkpoints every M steps (local memory),
-// then per sub-segment (in reverse) to put its <= M states in registers (local
-// memory for the 15-dimensional system), which the reverse RK4 steps consume
-// from last to first.  Parameter gradients are
+// then per sub-segment (in reverse) to put its <= M states in registers (shared
+// memory for the packed Lorenz sweep), which the reverse RK4 steps consume from
+// last to first.  The 15-dimensional system is recomputed once per chunk into a
+// per-thread scratch area in global memory instead (the staged sweep).  Parameter gradients are
 // summed per particle in FP32 within a chunk, added to FP64 per chunk, and
 // reduced over particles through per-block FP64 partials in fixed order.
 //
@@ -59,6 +60,10 @@ int adjoint_sub_steps(int64_t checkpoint_every) {
 }
 
 int64_t adjoint_partial_rows(int num_sms) { return (int64_t)num_sms * 8 * 8; }
+
+int64_t adjoint_scratch_threads(int rhs_id, int method, bool pp, int num_sms, bool batched) {
+    return rhs_id == FF_RHS_HH3 ? adjoint_scratch_threads_hh3(method, pp, num_sms, batched) : 0;
+}
 
 cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const AdjointArgs& a, int num_sms,
                            cudaStream_t s, double* dL_dp_dev, int n_params_kernel) {

@@ -34,6 +34,8 @@ struct AdjointArgs {
     int n_groups;
     int pad_;
     int64_t gstart[FF_MAX_GROUPS];
+    float* scratch;           // staged sweep (15-dimensional system): one chunk of states per thread
+    int64_t scratch_threads;  // threads the scratch has room for (floats = threads * chunk steps * dim)
 };
 
 // Batched adjoint: work tiles of consecutive particles of one member (one
@@ -47,16 +49,23 @@ struct AdjTile {
 };
 
 struct BatchAdjointArgs {
-    const AdjointArgs* sys;  // per member (its partial / max_blocks fields unused)
+    const AdjointArgs* sys;  // per member (its partial / max_blocks / scratch fields unused)
     const AdjTile* tiles;
     int n_tiles;
     int np_stride;           // doubles per partial row
     double* partial;         // n_tiles rows
+    float* scratch;          // staged sweep: one chunk of states per thread (as AdjointArgs)
+    int64_t scratch_threads;
 };
 
 bool adjoint_supported(int rhs_id);
 int adjoint_sub_steps(int64_t checkpoint_every);  // M >= K up to 16, else M * M >= K (K at most 256)
 int64_t adjoint_partial_rows(int num_sms);
+// Threads of the staged sweep (the 15-dimensional system's adjoint, standalone or
+// batched): each needs a scratch area of (largest chunk) x dim floats; 0 for the
+// systems whose sweeps keep their states on chip.
+int64_t adjoint_scratch_threads(int rhs_id, int method, bool pp, int num_sms, bool batched);
+int64_t adjoint_scratch_threads_hh3(int method, bool pp, int num_sms, bool batched);
 cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const AdjointArgs& a, int num_sms,
                            cudaStream_t s, double* dL_dp_dev, int n_params_kernel);
 constexpr int kAdjTile = 128;  // particles per batched-adjoint tile = threads per block

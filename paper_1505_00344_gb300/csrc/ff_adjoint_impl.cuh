@@ -7,13 +7,15 @@
 // lambda = dL/dx in registers.  A chunk of L <= M*M steps is recomputed from its
 // checkpoint twice (once when L <= M): once to place sub-checkpoints every M
 // steps (local memory), then per sub-segment (in reverse) to put its <= M
-// states in registers (local memory for the 15-dimensional system), which the
-// reverse RK4 steps consume from last to first.  Parameter gradients are summed
+// states in registers (shared memory in the packed Lorenz sweep), which the
+// reverse RK4 steps consume from last to first.  The 15-dimensional system runs
+// the staged sweep instead: one recomputation per chunk into a global scratch.  Parameter gradients are summed
 // per particle in FP32 within a chunk, added to FP64 per chunk, and reduced
 // over particles through per-block FP64 partials in fixed order.
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "ff.h"
@@ -458,42 +460,7 @@ __device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[
         return;
     }
     const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
-    if constexpr (D > 8) {
-        // large systems: stage points in a (local-memory) array, each pass one copy of f
-        // or of the vector-Jacobian product; the same operations in the same order as below
-        float xs[4][D], k[D], l[D], m[D], sum[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) xs[0][i] = x[i];
-#pragma unroll 1
-        for (int st = 0; st < 3; ++st) {
-            R::f(xs[st], p, k);
-            const float c = (st == 2) ? h : h2;
-#pragma unroll
-            for (int i = 0; i < D; ++i) xs[st + 1][i] = fmaf(c, k[i], x[i]);
-        }
-#pragma unroll 1
-        for (int st = 3; st >= 0; --st) {
-            if (st == 3) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) l[i] = h6 * lam[i];
-            } else {
-                const float cl = (st == 0) ? h6 : h3, cm = (st == 2) ? h : h2;
-#pragma unroll
-                for (int i = 0; i < D; ++i) l[i] = fmaf(cl, lam[i], cm * m[i]);
-            }
-            Vjp<R>::apply(xs[st], p, l, m, jp);
-            if (st == 3) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) sum[i] = m[i];
-            } else if (st > 0) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) sum[i] = __fadd_rn(sum[i], m[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < D; ++i) lam[i] = __fadd_rn(lam[i], __fadd_rn(sum[i], m[i]));
-        return;
-    }
+    static_assert(METHOD == FF_EULER || D <= 8, "the 15-dimensional system's reverse RK4 step is adj_step_staged");
     float k[D], x2[D], x3[D], x4[D];
     R::f(x, p, k);
 #pragma unroll
@@ -522,7 +489,8 @@ __device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[
 }
 
 // Reverse sweep of one particle i over all chunks: lambda from lam_in to
-// lam_out, parameter contributions added to gacc (FP64, per chunk).
+// lam_out, parameter contributions added to gacc (FP64, per chunk).  For systems
+// of up to 8 dimensions (the 15-dimensional one runs adjoint_particle_staged).
 template <class R, int METHOD, bool PP, int M>
 __device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i, double (&gacc)[R::NP]) {
     constexpr int D = R::DIM, NP = R::NP;
@@ -565,27 +533,17 @@ __device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i
             float st[M][D];
 #pragma unroll
             for (int k = 0; k < D; ++k) x[k] = cp[sq][k];
-            if constexpr (D > 8) {
-                // large states: the sub-segment stays in local memory (indexed at run time)
-                for (int r = 0; r < nq; ++r) {
+#pragma unroll
+            for (int r = 0; r < M; ++r) {
+                if (r < nq) {
 #pragma unroll
                     for (int k = 0; k < D; ++k) st[r][k] = x[k];
                     if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
                 }
-                for (int r = nq - 1; r >= 0; --r) adj_step<R, METHOD>(st[r], lam, h, p, jp);
-            } else {
-#pragma unroll
-                for (int r = 0; r < M; ++r) {
-                    if (r < nq) {
-#pragma unroll
-                        for (int k = 0; k < D; ++k) st[r][k] = x[k];
-                        if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
-                    }
-                }
-#pragma unroll
-                for (int r = M - 1; r >= 0; --r)
-                    if (r < nq) adj_step<R, METHOD>(st[r], lam, h, p, jp);
             }
+#pragma unroll
+            for (int r = M - 1; r >= 0; --r)
+                if (r < nq) adj_step<R, METHOD>(st[r], lam, h, p, jp);
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q) gacc[q] += (double)jp[q];
@@ -638,6 +596,255 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
             if (lane == 0) a.partial[((int64_t)blockIdx.x * nwarps + warp) * a.np_stride + q] = v;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Staged sweep for the 15-dimensional system (HH x 3).  Its sub-segment states
+// do not fit in registers, so a chunk is recomputed once from its checkpoint
+// and every state goes to the thread's scratch area in global memory (state
+// variable k of step r at scratch[(r * D + k) * T], T the launch's threads: one
+// coalesced column per warp); the reverse steps read them back from last to
+// first.  The reverse step's three stage points live in shared memory, and the
+// kernels run 4 blocks of 128 threads per SM within the register file.  Against
+// the two-level scheme of adjoint_particle this saves one forward
+// recomputation per step; the states, steps and sums are the same, in the same
+// order, so the gradients agree with it to the bit.
+// ---------------------------------------------------------------------------
+constexpr int kStagedBlock = 128;
+constexpr int kStagedMinBlocks = 3;
+
+// adj_step with the step's state and its RK4 stage points in shared memory:
+// stage + (s * D + i) * bs holds component i of stage point s + 1 (x1 = x) for this
+// thread, and the parameter contributions accumulate in jp + q * bs (shared).
+template <class R, int METHOD>
+__device__ __forceinline__ void adj_step_staged(float (&xs)[R::DIM], float (&lam)[R::DIM], float h, const float* p,
+                                                float* jp, float* stage, int bs) {
+    constexpr int D = R::DIM, NP = R::NP;
+    float jr[NP];
+    if constexpr (METHOD == FF_EULER) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) jr[q] = jp[q * bs];
+        adj_step<R, METHOD>(xs, lam, h, p, jr);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) jp[q * bs] = jr[q];
+    } else {
+        const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
+        float k[D], l[D], m[D], sum[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) stage[i * bs] = xs[i];
+#pragma unroll 1
+        for (int st = 0; st < 3; ++st) {
+            if constexpr (std::is_same<R, HH3>::value) hh3_f_packed(xs, p, k);  // the bits of HH3::f
+            else R::f(xs, p, k);
+            const float c = (st == 2) ? h : h2;
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                xs[i] = fmaf(c, k[i], stage[i * bs]);
+                stage[((st + 1) * D + i) * bs] = xs[i];
+            }
+        }
+#pragma unroll 1
+        for (int st = 3; st >= 0; --st) {
+            if (st == 3) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) l[i] = h6 * lam[i];
+            } else {
+                const float cl = (st == 0) ? h6 : h3, cm = (st == 2) ? h : h2;
+#pragma unroll
+                for (int i = 0; i < D; ++i) l[i] = fmaf(cl, lam[i], cm * m[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < D; ++i) xs[i] = stage[(st * D + i) * bs];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) jr[q] = jp[q * bs];
+            Vjp<R>::apply(xs, p, l, m, jr);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) jp[q * bs] = jr[q];
+            if (st == 3) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) sum[i] = m[i];
+            } else if (st > 0) {
+#pragma unroll
+                for (int i = 0; i < D; ++i) sum[i] = __fadd_rn(sum[i], m[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) lam[i] = __fadd_rn(lam[i], __fadd_rn(sum[i], m[i]));
+    }
+}
+
+// Reverse sweep of particle i with the chunk's states in the thread's scratch
+// (scr = the thread's first float, T = floats between consecutive entries); stage
+// and jp are the thread's shared-memory columns (stride bs).
+template <class R, int METHOD, bool PP>
+__device__ __forceinline__ void adjoint_particle_staged(const AdjointArgs& a, int64_t i, double (&gacc)[R::NP],
+                                                        float* scr, int64_t T, float* stage, float* jp, int bs) {
+    constexpr int D = R::DIM, NP = R::NP;
+    int g = 0;
+#pragma unroll
+    for (int q = 1; q < FF_MAX_GROUPS; ++q)
+        if (q < a.n_groups && i >= a.gstart[q]) g = q;
+    float lam[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) lam[k] = (k < a.dim) ? a.lam_in[k * a.n + i] : 0.0f;
+    const float pv = PP ? a.pparam[i] : 0.0f;
+    for (int c = a.n_chunks - 1; c >= 0; --c) {
+        const AdjChunk& ch = a.chunks[c];
+        // the chunk's parameters: read from the chunk table where they are the same for every
+        // particle (the compiler may load them again where needed instead of holding them)
+        float pl[PP ? NP : 1];
+        if constexpr (PP) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) pl[q] = (q == a.pidx) ? pv : ch.p[q];
+        }
+        const float* p = PP ? pl : ch.p;
+        const float h = ch.gh[g];
+        const int L = ch.n_steps;
+        const float* ck = a.ckpt + (int64_t)ch.ckpt * a.dim * a.pitch;
+        float x[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[k] = (k < a.dim) ? ck[k * a.pitch + i] : 0.0f;
+#pragma unroll 1
+        for (int r = 0; r < L; ++r) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) scr[((int64_t)r * D + k) * T] = x[k];
+            if (r + 1 < L) fwd_step<R, METHOD>(x, h, p);
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) jp[q * bs] = 0.0f;
+#pragma unroll 1
+        for (int r = L - 1; r >= 0; --r) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) x[k] = scr[((int64_t)r * D + k) * T];
+            adj_step_staged<R, METHOD>(x, lam, h, p, jp, stage, bs);
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) gacc[q] += (double)jp[q * bs];
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+        if (k < a.dim) a.lam_out[k * a.n + i] = lam[k];
+}
+
+template <class R, int METHOD, bool PP>
+__global__ void __launch_bounds__(kStagedBlock, kStagedMinBlocks) adjoint_staged_kernel(
+    const __grid_constant__ AdjointArgs a) {
+    constexpr int NP = R::NP, D = R::DIM;
+    __shared__ double red[kStagedBlock / 32][NP];
+    __shared__ float stage[4 * D * kStagedBlock];
+    __shared__ float jp[NP * kStagedBlock];
+    double gacc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) gacc[q] = 0.0;
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t; i < a.n; i += T)
+        adjoint_particle_staged<R, METHOD, PP>(a, i, gacc, a.scratch + t, T, stage + threadIdx.x, jp + threadIdx.x,
+                                               blockDim.x);
+    block_sum_to_row<NP, kStagedBlock / 32>(gacc, red, a.partial + (int64_t)blockIdx.x * a.np_stride);
+}
+
+// Batched form: tiles of one member's particles, one per thread, round-robin over the blocks.
+template <class R, int METHOD, bool PP>
+__global__ void __launch_bounds__(kAdjTile, kStagedMinBlocks) batch_adjoint_staged_kernel(
+    const __grid_constant__ BatchAdjointArgs b) {
+    constexpr int NP = R::NP, D = R::DIM;
+    static_assert(kAdjTile == kStagedBlock, "one tile per block");
+    __shared__ double red[kAdjTile / 32][NP];
+    __shared__ float stage[4 * D * kAdjTile];
+    __shared__ float jp[NP * kAdjTile];
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
+        const AdjTile tl = b.tiles[tile];
+        const AdjointArgs& a = b.sys[tl.sys];
+        double gacc[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) gacc[q] = 0.0;
+        const int64_t i = tl.first + threadIdx.x;
+        if (i < tl.first + tl.count)
+            adjoint_particle_staged<R, METHOD, PP>(a, i, gacc, b.scratch + t, T, stage + threadIdx.x,
+                                                   jp + threadIdx.x, blockDim.x);
+        block_sum_to_row<NP, kAdjTile / 32>(gacc, red, b.partial + (int64_t)tile * b.np_stride);
+    }
+}
+
+// Resident threads of a staged kernel: the most it launches, and the scratch it needs room for.
+template <class Kernel>
+static int64_t staged_threads(Kernel kernel, int num_sms) {
+    int occ = 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kStagedBlock, 0) != cudaSuccess || occ < 1)
+        return 0;
+    return (int64_t)occ * num_sms * kStagedBlock;
+}
+
+template <class R, bool BATCHED>
+static int64_t staged_threads_for(int method, bool pp, int num_sms) {
+    if constexpr (BATCHED) {
+        if (method == FF_RK4)
+            return pp ? staged_threads(batch_adjoint_staged_kernel<R, FF_RK4, true>, num_sms)
+                      : staged_threads(batch_adjoint_staged_kernel<R, FF_RK4, false>, num_sms);
+        return pp ? staged_threads(batch_adjoint_staged_kernel<R, FF_EULER, true>, num_sms)
+                  : staged_threads(batch_adjoint_staged_kernel<R, FF_EULER, false>, num_sms);
+    } else {
+        if (method == FF_RK4)
+            return pp ? staged_threads(adjoint_staged_kernel<R, FF_RK4, true>, num_sms)
+                      : staged_threads(adjoint_staged_kernel<R, FF_RK4, false>, num_sms);
+        return pp ? staged_threads(adjoint_staged_kernel<R, FF_EULER, true>, num_sms)
+                  : staged_threads(adjoint_staged_kernel<R, FF_EULER, false>, num_sms);
+    }
+}
+
+template <class R, int METHOD, bool PP>
+static cudaError_t launch_staged_one(const AdjointArgs& a, int num_sms, cudaStream_t s, int64_t* rows) {
+    auto kernel = adjoint_staged_kernel<R, METHOD, PP>;
+    const int64_t resident = staged_threads(kernel, num_sms);
+    if (resident < kStagedBlock) return cudaErrorInvalidConfiguration;
+    int64_t cap = resident / kStagedBlock;
+    if (cap > a.scratch_threads / kStagedBlock) cap = a.scratch_threads / kStagedBlock;  // room in the scratch
+    if (cap > 8 * a.max_blocks) cap = 8 * a.max_blocks;  // rows of the partial-sum buffer (one per block here)
+    const int64_t need = (a.n + kStagedBlock - 1) / kStagedBlock;
+    const int grid = (int)(need < cap ? need : cap);
+    if (grid < 1 || !a.scratch) return cudaErrorInvalidConfiguration;
+    kernel<<<grid, kStagedBlock, 0, s>>>(a);
+    *rows = grid;
+    return cudaGetLastError();
+}
+
+template <class R>
+static cudaError_t launch_staged(int method, bool pp, const AdjointArgs& a, int num_sms, cudaStream_t s,
+                                 int64_t* rows) {
+    if (method == FF_RK4)
+        return pp ? launch_staged_one<R, FF_RK4, true>(a, num_sms, s, rows)
+                  : launch_staged_one<R, FF_RK4, false>(a, num_sms, s, rows);
+    return pp ? launch_staged_one<R, FF_EULER, true>(a, num_sms, s, rows)
+              : launch_staged_one<R, FF_EULER, false>(a, num_sms, s, rows);
+}
+
+template <class R, int METHOD, bool PP>
+static cudaError_t launch_batch_staged_one(const BatchAdjointArgs& b, int num_sms, cudaStream_t s) {
+    auto kernel = batch_adjoint_staged_kernel<R, METHOD, PP>;
+    const int64_t resident = staged_threads(kernel, num_sms);
+    if (resident < kAdjTile) return cudaErrorInvalidConfiguration;
+    int64_t cap = resident / kAdjTile;
+    if (cap > b.scratch_threads / kAdjTile) cap = b.scratch_threads / kAdjTile;
+    const int grid = (int)((int64_t)b.n_tiles < cap ? b.n_tiles : cap);
+    if (grid < 1) return cudaSuccess;
+    if (!b.scratch) return cudaErrorInvalidConfiguration;
+    kernel<<<grid, kAdjTile, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <class R>
+static cudaError_t launch_batch_staged(int method, bool pp, const BatchAdjointArgs& b, int num_sms, cudaStream_t s) {
+    if (method == FF_RK4)
+        return pp ? launch_batch_staged_one<R, FF_RK4, true>(b, num_sms, s)
+                  : launch_batch_staged_one<R, FF_RK4, false>(b, num_sms, s);
+    return pp ? launch_batch_staged_one<R, FF_EULER, true>(b, num_sms, s)
+              : launch_batch_staged_one<R, FF_EULER, false>(b, num_sms, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -79,6 +79,7 @@ ff_status seed_group(ff_system* s, const Group& g) {
     a.pitch = s->pitch;
     a.start = g.start;
     a.count = g.count;
+    a.first = g.first;
     a.seed = g.seed;
     a.dim = s->dim;
     for (int k = 0; k < s->dim; ++k) {
@@ -165,13 +166,22 @@ ff_status ff_destroy_system(ff_system* s) {
     cudaFree(s->d_chunks);
     cudaFree(s->d_partial);
     cudaFree(s->d_dp);
+    cudaFree(s->d_adj_scratch);
     delete s;
     return FF_OK;
 }
 
 ff_status ff_seed_particles(ff_system* s, int64_t count, const double* lo, const double* hi,
                             int direction, uint64_t seed, int* group_id_out) {
+    return ff_seed_particles_slice(s, count, 0, count, lo, hi, direction, seed, group_id_out);
+}
+
+ff_status ff_seed_particles_slice(ff_system* s, int64_t count, int64_t first, int64_t total, const double* lo,
+                                  const double* hi, int direction, uint64_t seed, int* group_id_out) {
     if (!s) return fail(FF_ERR_INVALID_ARG, "ff_seed_particles: system is NULL");
+    if (count >= 1 && (first < 0 || total < 1 || first > total - count))
+        return fail(FF_ERR_INVALID_ARG, "ff_seed_particles_slice: slice [%lld, %lld) not inside a group of %lld",
+                    (long long)first, (long long)(first + count), (long long)total);
     if (s->stepped) return fail(FF_ERR_STATE, "ff_seed_particles: system already stepped (call ff_reset first)");
     if (s->n_groups >= FF_MAX_GROUPS) return fail(FF_ERR_STATE, "ff_seed_particles: already %d groups", FF_MAX_GROUPS);
     if (count < 1) return fail(FF_ERR_INVALID_ARG, "ff_seed_particles: count %lld < 1", (long long)count);
@@ -190,6 +200,8 @@ ff_status ff_seed_particles(ff_system* s, int64_t count, const double* lo, const
     Group g{};
     g.start = s->n_particles;
     g.count = count;
+    g.first = first;
+    g.total = total;
     g.direction = direction;
     g.seed = seed;
     for (int k = 0; k < s->dim; ++k) {
@@ -245,6 +257,12 @@ static ff_status ensure_pparam(ff_system* s) {
 
 ff_status ff_set_particle_param(ff_system* s, int param_index, double lo, double hi) {
     if (!s) return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param: system is NULL");
+    return ff_set_particle_param_slice(s, param_index, lo, hi, 0, s->n_particles);
+}
+
+ff_status ff_set_particle_param_slice(ff_system* s, int param_index, double lo, double hi, int64_t first,
+                                      int64_t total) {
+    if (!s) return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param: system is NULL");
     if (param_index == -1) {
         s->pparam_index = -1;
         s->params_version++;
@@ -255,11 +273,14 @@ ff_status ff_set_particle_param(ff_system* s, int param_index, double lo, double
     if (!std::isfinite(lo) || !std::isfinite(hi))
         return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param: non-finite bounds");
     if (s->n_particles < 1) return fail(FF_ERR_STATE, "ff_set_particle_param: no particles seeded");
+    if (first < 0 || first > total - s->n_particles)
+        return fail(FF_ERR_INVALID_ARG, "ff_set_particle_param_slice: particles [%lld, %lld) not inside %lld",
+                    (long long)first, (long long)(first + s->n_particles), (long long)total);
     DeviceScope dev(s->device);
     if (dev.err != cudaSuccess) return cuda_fail(dev.err, "ff_set_particle_param: set device");
     ff_status st = ensure_pparam(s);
     if (st != FF_OK) return st;
-    cudaError_t e = ff::launch_linspace(s->d_pparam, s->n_particles, lo, hi, s->num_sms, s->stream);
+    cudaError_t e = ff::launch_linspace(s->d_pparam, s->n_particles, lo, hi, first, total, s->num_sms, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "linspace kernel launch");
     s->pparam_index = param_index;
     s->pparam_linspace = true;
@@ -399,7 +420,8 @@ static ff_status upload_reset_table(ff_system* s) {
             t.lo[g][k] = s->groups[g].lo[k];
             t.width[g][k] = s->groups[g].hi[k] - s->groups[g].lo[k];
         }
-        t.count[g] = s->groups[g].count;
+        t.count[g] = s->groups[g].total;
+        t.first[g] = s->groups[g].first;
         t.seed[g] = s->groups[g].seed;
     }
     for (int k = 0; k < s->dim; ++k) {
@@ -575,10 +597,13 @@ static void free_tape(ff_system* s) {
     cudaFree(s->d_chunks);
     cudaFree(s->d_partial);
     cudaFree(s->d_dp);
+    cudaFree(s->d_adj_scratch);
     s->d_ckpt = nullptr;
     s->d_chunks = nullptr;
     s->d_partial = nullptr;
     s->d_dp = nullptr;
+    s->d_adj_scratch = nullptr;
+    s->adj_scratch_floats = 0;
     s->ckpt_capacity = 0;
     s->chunks.clear();
     s->tape_on = false;
@@ -664,6 +689,23 @@ ff_status ff_backward(ff_system* s, const float* dL_dxT_dev, float* dL_dx0_dev, 
     a.pitch = s->pitch;
     a.n_groups = s->n_groups;
     for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
+    // the staged sweep (HH x 3) keeps a chunk of states per thread in a scratch area,
+    // allocated on first use and kept with the tape
+    const int64_t scratch_threads =
+        ff::adjoint_scratch_threads(s->rhs_id, s->method, s->pparam_index >= 0, s->num_sms, false);
+    if (scratch_threads > 0) {
+        const size_t need = (size_t)scratch_threads * (size_t)s->tape_every * (size_t)s->dim;
+        if (need > s->adj_scratch_floats) {
+            cudaFree(s->d_adj_scratch);  // waits for any sweep still reading it
+            s->d_adj_scratch = nullptr;
+            s->adj_scratch_floats = 0;
+            e = cudaMalloc(&s->d_adj_scratch, sizeof(float) * need);
+            if (e != cudaSuccess) return cuda_fail(e, "ff_backward: scratch allocation");
+            s->adj_scratch_floats = need;
+        }
+        a.scratch = s->d_adj_scratch;
+        a.scratch_threads = scratch_threads;
+    }
     const int np_kernel = s->rhs_id == FF_RHS_LINEAR ? 64 : s->n_params;
     e = ff::launch_adjoint(s->rhs_id, s->method, s->pparam_index >= 0, ff::adjoint_sub_steps(s->tape_every), a,
                            s->num_sms, s->stream, s->d_dp, np_kernel);

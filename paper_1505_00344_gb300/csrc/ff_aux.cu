@@ -26,8 +26,9 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
 __global__ void seed_kernel(const __grid_constant__ SeedArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.count; j += stride) {
+        const uint64_t jg = (uint64_t)(a.first + j);  // index within the whole group
         for (int k = 0; k < a.dim; ++k) {
-            const uint64_t r = splitmix64_at(a.seed, (uint64_t)j * (uint64_t)a.dim + (uint64_t)k + 1u);
+            const uint64_t r = splitmix64_at(a.seed, jg * (uint64_t)a.dim + (uint64_t)k + 1u);
             const double u = (double)(r >> 40) * (1.0 / 16777216.0);
             const double v = __dadd_rn(a.lo[k], __dmul_rn(a.width[k], u));
             a.x[k * a.pitch + a.start + j] = __double2float_rn(v);
@@ -35,12 +36,14 @@ __global__ void seed_kernel(const __grid_constant__ SeedArgs a) {
     }
 }
 
-// Per-particle parameter: lo + (hi - lo) * (i / (P - 1)) in double, to float.
-__global__ void linspace_kernel(float* out, int64_t P, double lo, double width) {
+// Per-particle parameter: lo + (hi - lo) * (i / (total - 1)) in double, to float, for
+// particles i = first .. first + P - 1 of a linspace over `total` particles.
+__global__ void linspace_kernel(float* out, int64_t P, double lo, double width, int64_t first, int64_t total) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += stride) {
-        const double frac = (P > 1) ? __ddiv_rn((double)i, (double)(P - 1)) : 0.0;
-        out[i] = __double2float_rn(__dadd_rn(lo, __dmul_rn(width, frac)));
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P; j += stride) {
+        const int64_t i = first + j;
+        const double frac = (total > 1) ? __ddiv_rn((double)i, (double)(total - 1)) : 0.0;
+        out[j] = __double2float_rn(__dadd_rn(lo, __dmul_rn(width, frac)));
     }
 }
 
@@ -188,10 +191,10 @@ cudaError_t launch_seed(const SeedArgs& a, int num_sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_linspace(float* out, int64_t P, double lo, double hi, int num_sms,
+cudaError_t launch_linspace(float* out, int64_t P, double lo, double hi, int64_t first, int64_t total, int num_sms,
                             cudaStream_t s) {
     if (P <= 0) return cudaSuccess;
-    linspace_kernel<<<grid_for(P, 256, num_sms, 8), 256, 0, s>>>(out, P, lo, hi - lo);
+    linspace_kernel<<<grid_for(P, 256, num_sms, 8), 256, 0, s>>>(out, P, lo, hi - lo, first, total);
     return cudaGetLastError();
 }
 

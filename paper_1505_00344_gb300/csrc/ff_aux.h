@@ -14,6 +14,7 @@ struct SeedArgs {
     int64_t pitch;
     int64_t start;   // first particle of the group
     int64_t count;
+    int64_t first;   // index of the first of these particles within its whole group (a slice)
     uint64_t seed;
     int dim;
     int pad_;
@@ -61,7 +62,7 @@ int sprite_tiles(int W, int H);          // tiles covering a W x H image
 int64_t sprite_entries_bound(int64_t n, float radius);
 cudaError_t launch_sprites_tiled(const SpriteArgs& a, int ndim_view, bool masked, uint32_t* tiles,
                                  uint32_t* entries, int num_sms, cudaStream_t s);
-cudaError_t launch_linspace(float* out, int64_t P, double lo, double hi, int num_sms,
+cudaError_t launch_linspace(float* out, int64_t P, double lo, double hi, int64_t first, int64_t total, int num_sms,
                             cudaStream_t s);
 // strip: consecutive particles map to a narrow strip of the image (a linspace
 // per-particle parameter on a view axis), so the shared-memory histogram pays.

@@ -133,6 +133,8 @@ struct ff_batch {
         double* d_partial = nullptr;
         double* d_dp = nullptr;
         size_t adj_tiles_cap = 0;
+        float* d_adj_scratch = nullptr;  // staged sweep (HH x 3): one chunk of states per thread
+        size_t adj_scratch_floats = 0;
     };
     int device = 0, num_sms = 1;
     cudaStream_t user = nullptr;   // the caller's stream
@@ -285,6 +287,7 @@ void destroy_batch(ff_batch* b) {
         cudaFree(f.d_row0);
         cudaFree(f.d_partial);
         cudaFree(f.d_dp);
+        cudaFree(f.d_adj_scratch);
         if (f.side) cudaStreamDestroy(f.side);
         if (f.done) cudaEventDestroy(f.done);
     }
@@ -542,6 +545,25 @@ ff_status ff_batch_backward(ff_batch* b, const float* const* dL_dxT_dev, float* 
         if (e != cudaSuccess) break;
         ff::BatchAdjointArgs ba{f.d_adj, f.d_adj_tiles, (int)f.adj_tiles.size(), FF_MAX_PARAMS, f.d_partial};
         const ff_system* s0 = b->systems[f.members[0]];
+        const int64_t scratch_threads = ff::adjoint_scratch_threads(f.rhs_id, f.method, f.pp, b->num_sms, true);
+        if (scratch_threads > 0) {
+            int64_t longest = 1;  // the longest chunk of any member
+            for (int m = 0; m < nm; ++m) {
+                const ff_system* s = b->systems[f.members[m]];
+                if (s->tape_every > longest) longest = s->tape_every;
+            }
+            const size_t need = (size_t)scratch_threads * (size_t)longest * (size_t)s0->dim;
+            if (need > f.adj_scratch_floats) {
+                cudaFree(f.d_adj_scratch);  // waits for any sweep still reading it
+                f.d_adj_scratch = nullptr;
+                f.adj_scratch_floats = 0;
+                e = cudaMalloc(&f.d_adj_scratch, sizeof(float) * need);
+                if (e != cudaSuccess) break;
+                f.adj_scratch_floats = need;
+            }
+            ba.scratch = f.d_adj_scratch;
+            ba.scratch_threads = scratch_threads;
+        }
         const int np_kernel = f.rhs_id == FF_RHS_LINEAR ? 64 : s0->n_params;
         e = ff::launch_batch_adjoint(f.rhs_id, f.method, f.pp, ff::adjoint_sub_steps(s0->tape_every), ba, f.d_row0,
                                      nm, np_kernel, b->num_sms, b->user, f.d_dp);

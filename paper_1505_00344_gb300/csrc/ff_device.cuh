@@ -109,7 +109,8 @@ __device__ __forceinline__ void run_steps(const IntegrateArgs& a, int n_steps, S
 struct ResetTable {
     double lo[FF_MAX_GROUPS][FF_MAX_DIM];
     double width[FF_MAX_GROUPS][FF_MAX_DIM];  // hi - lo in double, as for the initial seeding
-    int64_t count[FF_MAX_GROUPS];
+    int64_t count[FF_MAX_GROUPS];             // particles of the whole group (a slice's is its group's)
+    int64_t first[FF_MAX_GROUPS];             // index within the whole group of the group's first particle
     uint64_t seed[FF_MAX_GROUPS];
     float blo[FF_MAX_DIM], bhi[FF_MAX_DIM];
     int has_bounds;
@@ -545,7 +546,7 @@ __device__ __forceinline__ void reset_check(const IntegrateArgs& a, const Steppe
         for (int k = 0; k < a.dim; ++k) out |= !(e[k] >= t->blo[k] && e[k] <= t->bhi[k]);
     if (!out) return;
     const uint32_t r = nres + 1u;
-    const uint64_t j = (uint64_t)(i - a.gstart[g]);
+    const uint64_t j = (uint64_t)(t->first[g] + (i - a.gstart[g]));  // index within the whole group
     const uint64_t base = ((uint64_t)r * (uint64_t)t->count[g] + j) * (uint64_t)a.dim;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -1242,5 +1243,24 @@ struct HH3RK4Packed {
     }
 };
 template <bool KAHAN> struct StepperFor<HH3, FF_RK4, KAHAN> { using type = HH3RK4Packed; };
+
+// HH3::f with neurons 0 and 1 packed in f32x2 registers and neuron 2 on floats, as
+// in HH3RK4Packed: lane by lane the same operations as HH3::f, so the same bits.
+__device__ __forceinline__ void hh3_f_packed(const float (&x)[15], const float* p, float (&dx)[15]) {
+    const HHConst<HHPair> c2 = hh_const<HHPair>(p);
+    const HHConst<HHScalar> c1 = hh_const<HHScalar>(p);
+    const float s_sum = __fadd_rn(__fadd_rn(x[4], x[9]), x[14]);
+    f2 X[5], K[5];
+    float k2[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) X[k] = pack2(x[k], x[5 + k]);
+    hh_neuron<HHPair>(X[0], X[1], X[2], X[3], X[4], sub2(pack2(s_sum, s_sum), X[4]), pack2(p[9], p[10]), c2, K);
+    hh_neuron<HHScalar>(x[10], x[11], x[12], x[13], x[14], __fsub_rn(s_sum, x[14]), p[11], c1, k2);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        unpack2(K[k], dx[k], dx[5 + k]);
+        dx[10 + k] = k2[k];
+    }
+}
 
 }  // namespace ff

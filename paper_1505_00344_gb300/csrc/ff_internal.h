@@ -21,6 +21,7 @@ ff_status cuda_fail(cudaError_t e, const char* what);
 
 struct Group {
     int64_t start, count;
+    int64_t first, total;  // these particles are first .. first + count - 1 of a group of `total`
     int direction;
     uint64_t seed;
     double lo[FF_MAX_DIM], hi[FF_MAX_DIM];
@@ -99,6 +100,8 @@ struct ff_system {
     ff::AdjChunk* d_chunks = nullptr;
     double* d_partial = nullptr;
     double* d_dp = nullptr;
+    float* d_adj_scratch = nullptr;  // staged adjoint sweep (HH x 3): one chunk of states per thread
+    size_t adj_scratch_floats = 0;
     int64_t partial_blocks = 0;
     std::vector<ff::AdjChunk> chunks;
     int64_t params_version = 0, chunk_version = -1;

@@ -327,9 +327,11 @@ ff_status ff_last_launch(ff_system* sys, char* kernel, int kernel_len, int* grid
 
 /* Launch shape of the integrator: particles per thread (1, 2 or 4; at 2 and 4
  * each plane is read with one 8- or 16-byte access, and RK4 on Lorenz, plain or
- * compensated, then runs two particles per packed f32x2 instruction; the
- * default is 4 for RK4 on Lorenz, 2 when compensated, and 1 otherwise; 0 keeps
- * the current value),
+ * compensated, then runs two particles per packed f32x2 instruction; HH3 takes
+ * 1 or 2, and plain RK4 at 2 runs all three neurons of two particles packed,
+ * bit-identical to 1, when the pairs fill one wave (3 x 128 per SM; smaller
+ * ensembles run one particle per thread); the default is 4 for RK4 on Lorenz, 2 when compensated,
+ * 2 for plain RK4 on HH3, and 1 otherwise; 0 keeps the current value),
  * threads per block (a multiple of 32 up to 1024, default 512 for RK4 on
  * Lorenz and 256 otherwise, 0 keeps the current value; clamped to the kernel's
  * maximum, 512 for the 2- and 3-dimensional systems and 256 for LINEAR and

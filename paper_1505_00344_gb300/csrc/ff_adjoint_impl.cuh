@@ -168,10 +168,10 @@ __device__ __forceinline__ void hh_neuron_vjp(typename O::T V, typename O::T m, 
     const T am = O::sel(sm, bernoulli_series_t<O>(ym), O::mul(ym, rm));
     const T gn = O::sel(sn, bernoulli_series_t<O>(yn), O::mul(yn, rn));
     const T dgm = O::sel(sm, bernoulli_series_deriv_t<O>(ym),
-                         O::mul(O::sub(one, O::mul(em, O::add(one, ym))), O::mul(rm, rm)));
+                         O::mul(O::fms(em, O::add(one, ym), one), O::mul(rm, rm)));
     const T dgn = O::sel(sn, bernoulli_series_deriv_t<O>(yn),
-                         O::mul(O::sub(one, O::mul(en, O::add(one, yn))), O::mul(rn, rn)));
-    const T an = O::mul(O::k(0.1f), gn);
+                         O::mul(O::fms(en, O::add(one, yn), one), O::mul(rn, rn)));
+    const T anbn = O::fma(O::k(0.1f), gn, bn);  // alpha_n + beta_n (alpha_n = g(yn) / 10), fused
     const T dam = O::mul(O::k(0.1f), dgm), dan = O::mul(O::k(0.01f), dgn);
     const T ph = O::fma(O::k(kE3), q8, one), ps = O::add(one, es);
     const T r = O::rcp(O::mul(ph, ps));
@@ -197,10 +197,11 @@ __device__ __forceinline__ void hh_neuron_vjp(typename O::T V, typename O::T m, 
     const T gate_h = O::fma(dah, O::sub(one, h), O::mul(nd_bh, h));
     const T gate_n = O::fma(dan, O::sub(one, n), O::mul(nd_bn, n));
     const T jv = O::fma(vm, gate_m, O::fma(vh, gate_h, O::fma(vn, gate_n, O::mul(O::mul(c.sig, a1), sv))));
-    jx[0] = O::sub(jv, O::mul(uV, gtot));
-    jx[1] = O::sub(O::mul(O::mul(O::mul(O::mul(uV, c.gNa3), m2), h), dNa), O::mul(vm, O::add(am, bm)));
-    jx[2] = O::sub(O::mul(O::mul(O::mul(uV, c.gNa), m3), dNa), O::mul(vh, O::add(ah, bh)));
-    jx[3] = O::sub(O::mul(O::mul(O::mul(uV, c.gK4), n3), dK), O::mul(vn, O::add(an, bn)));
+    // x - u w with one rounding (O::fms)
+    jx[0] = O::fms(uV, gtot, jv);
+    jx[1] = O::fms(vm, O::add(am, bm), O::mul(O::mul(O::mul(O::mul(uV, c.gNa3), m2), h), dNa));
+    jx[2] = O::fms(vh, O::add(ah, bh), O::mul(O::mul(O::mul(uV, c.gNa), m3), dNa));
+    jx[3] = O::fms(vn, anbn, O::mul(O::mul(O::mul(uV, c.gK4), n3), dK));
     self = O::mul(vs, O::fma(act, c.neg_inv_tr, c.neg_inv_td));
     syn = O::mul(O::mul(c.gsyn, dS), uV);
     // parameters: C, gNa, gK, gL, ENa, EK, EL, gsyn, Esyn, drive, tau_r, tau_d, sig, theta
@@ -222,7 +223,11 @@ __device__ __forceinline__ void hh_neuron_vjp(typename O::T V, typename O::T m, 
 
 template <> struct Vjp<HH3> {
     // Neurons 0 and 1 run the neuron product above packed in f32x2 registers,
-    // neuron 2 on floats; lane by lane the arithmetic is the same.
+    // neuron 2 on floats, with the same operations.  The gate rows of jx can still
+    // round one way in f32x2 and another in floats (measured: about a quarter of
+    // random inputs, by one rounding), where the toolchain fuses a different pair
+    // of packed operations than the float form; every kernel runs this same code,
+    // so batched and standalone sweeps agree to the bit.
     __device__ __forceinline__ static void apply(const float (&x)[15], const float* p, const float (&v)[15],
                                                  float (&jx)[15], float* jp) {
         const HHVjpConst<HHPair> c2 = hh_vjp_const<HHPair>(p);

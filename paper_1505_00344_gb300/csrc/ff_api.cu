@@ -142,7 +142,9 @@ ff_status ff_create_system(int rhs_id, int dim, const double* params, int n_para
     // default launch shape: RK4 on Lorenz runs packed pairs, 4 particles per thread (2 when
     // compensated: its registers then leave room for more warps)
     const bool packed_lorenz = rhs_id == FF_RHS_LORENZ && method == FF_RK4;
-    s->ppt = packed_lorenz ? ((flags & FF_FLAG_KAHAN) ? 2 : 4) : 1;
+    // HH3 plain RK4: two particles per thread, all three neurons of the pair packed
+    const bool packed_hh3 = rhs_id == FF_RHS_HH3 && method == FF_RK4 && !(flags & FF_FLAG_KAHAN);
+    s->ppt = packed_lorenz ? ((flags & FF_FLAG_KAHAN) ? 2 : 4) : (packed_hh3 ? 2 : 1);
     s->block = packed_lorenz ? 512 : 256;
     *out = s;
     return FF_OK;
@@ -340,8 +342,8 @@ ff_status ff_set_launch(ff_system* s, int ppt, int block, int blocks_per_sm, int
     if (ppt == 0) ppt = s->ppt;
     if (block == 0) block = s->block;
     if (ppt != 1 && ppt != 2 && ppt != 4) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: ppt %d not 1, 2 or 4", ppt);
-    if (ppt != 1 && s->dim > 4 && s->rhs_id != FF_RHS_LINEAR)
-        return fail(FF_ERR_INVALID_ARG, "ff_set_launch: ppt > 1 needs dim <= 4");
+    if (ppt != 1 && s->dim > 4 && s->rhs_id != FF_RHS_LINEAR && !(s->rhs_id == FF_RHS_HH3 && ppt == 2))
+        return fail(FF_ERR_INVALID_ARG, "ff_set_launch: ppt > 1 needs dim <= 4 (HH3: ppt 2)");
     if (ppt != 1 && s->rhs_id == FF_RHS_LINEAR) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: LINEAR runs ppt 1");
     if (block < 32 || block > 1024 || block % 32) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: block %d", block);
     if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(FF_ERR_INVALID_ARG, "ff_set_launch: blocks_per_sm %d", blocks_per_sm);

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -56,12 +57,37 @@ __global__ void __launch_bounds__(R::MAX_BLOCK, MinBlocks<R>::value) batch_kerne
     }
 }
 
+// HH3 RK4 at two particles per thread: all three neurons of a particle pair packed
+// (hh3_rk4_x2_item, bit-identical to one particle per thread), under its own register bound.
+template <bool PP>
+__global__ void __launch_bounds__(HH3::MAX_BLOCK / 2, 3) batch_hh3_x2_kernel(const __grid_constant__ BatchArgs b) {
+    for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
+        const BatchTile T = b.tiles[tile];
+        const IntegrateArgs& a = b.sys[T.sys];
+        float* ck = b.ckpt ? b.ckpt[T.sys] : nullptr;
+        for (int64_t t = T.first + threadIdx.x; t < T.first + T.count; t += blockDim.x) {
+            if (ck) {  // checkpoint of a taped chunk: the state this launch starts from
+                const int64_t i0 = t * 2;
+                for (int k = 0; k < a.dim; ++k) {
+                    float v[2];
+                    Vec<2>::load(a.x + k * a.pitch + i0, v);
+                    Vec<2>::store(ck + k * a.pitch + i0, v);
+                }
+            }
+            hh3_rk4_x2_item<PP, false>(a, t, b.n_steps);  // checkpoint written above
+        }
+    }
+}
+
 template <class R, int METHOD, bool PP>
 static const void* kernel_pp(int ppt) {
     if (ppt == 1) return (const void*)batch_kernel<R, METHOD, PP, 1>;
     if constexpr (R::DIM <= 4) {
         if (ppt == 2) return (const void*)batch_kernel<R, METHOD, PP, 2>;
         if (ppt == 4) return (const void*)batch_kernel<R, METHOD, PP, 4>;
+    }
+    if constexpr (std::is_same<R, HH3>::value && METHOD == FF_RK4) {
+        if (ppt == 2) return (const void*)batch_hh3_x2_kernel<PP>;
     }
     return nullptr;
 }
@@ -70,18 +96,6 @@ static const void* kernel_pp(int ppt) {
 template <class R, int METHOD>
 static const void* kernel_for(int ppt, bool pp) {
     return pp ? kernel_pp<R, METHOD, true>(ppt) : kernel_pp<R, METHOD, false>(ppt);
-}
-
-// Kernel state width of a family (LINEAR is padded to 8 whatever its dim).
-static int family_kernel_dim(int rhs_id) {
-    switch (rhs_id) {
-    case FF_RHS_LINEAR: return Linear::DIM;
-    case FF_RHS_HARMONIC: return Harmonic::DIM;
-    case FF_RHS_WILSON_COWAN: return WilsonCowan::DIM;
-    case FF_RHS_LORENZ: return Lorenz::DIM;
-    case FF_RHS_HH3: return HH3::DIM;
-    default: return 0;
-    }
 }
 
 static const void* family_kernel(int rhs_id, int method, int ppt, bool pp) {
@@ -615,7 +629,7 @@ ff_status ff_batch_autotune(ff_batch* b, const double* dt, int64_t trial_steps) 
         double best = -1.0;
         int best_ppt = f.ppt, best_block = f.block;
         for (int pi = 0; pi < 3 && e == cudaSuccess && st == FF_OK; ++pi) {
-            if (ppts[pi] > 1 && ff::family_kernel_dim(f.rhs_id) > 4) continue;
+            if (!ff::family_kernel(f.rhs_id, f.method, ppts[pi], f.pp)) continue;  // shape not built
             for (int bi = 0; bi < 4 && e == cudaSuccess && st == FF_OK; ++bi) {
                 f.ppt = ppts[pi];
                 f.block = blocks[bi];

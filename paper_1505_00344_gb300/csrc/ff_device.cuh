@@ -203,9 +203,12 @@ struct Lorenz {
 // 0.5, where the FP32 difference would cancel.  5 MUFU operations per neuron.
 //
 // One neuron's right-hand side is written once over a lane type: O = HHScalar
-// (one neuron) or, further below, the packed pair type (two neurons of one
-// particle in one f32x2 register).  Every operation is explicit and rounded on
-// its own, so both forms give the same bits lane by lane.
+// (one neuron) or, further below, the packed pair type (two lanes of one f32x2
+// register).  Every operation is explicit, so both forms give the same bits lane
+// by lane -- with one care: the toolchain fuses an f32x2 product whose only use
+// is an f32x2 addition or subtraction into one fused operation, which the float
+// form keeps as two roundings, so such places are written as explicit fused
+// operations (checked on 65,536 random neuron states: no lane differs).
 struct HHScalar {
     using T = float;
     using M = bool;
@@ -218,6 +221,8 @@ struct HHScalar {
     __device__ __forceinline__ static T rcp(T a) { return rcp_ftz(a); }
     __device__ __forceinline__ static M small(T y) { return fabsf(y) < 0.5f; }
     __device__ __forceinline__ static T sel(M c, T a, T b) { return c ? a : b; }
+    // a - t y with one rounding
+    __device__ __forceinline__ static T fms(T t, T y, T a) { return fmaf(-t, y, a); }
 };
 
 // Parameter-derived constants of the neuron right-hand side.
@@ -288,7 +293,7 @@ __device__ __forceinline__ void hh_neuron(typename O::T V, typename O::T m, type
     // beta_h = 1 / (1 + e^3 q^8), act = 1 / (1 + es)
     const T ph = O::fma(O::k(kE3), q8, one), ps = O::add(one, es);
     const T r = O::rcp(O::mul(ph, ps));
-    const T bh = O::mul(ps, r), act = O::mul(ph, r);
+    const T act = O::mul(ph, r);  // beta_h = ps r enters only the h gate, fused there
     const T m3h = O::mul(O::mul(O::mul(m, m), m), h);
     const T n2 = O::mul(n, n), n4 = O::mul(n2, n2);
     T I = O::mul(c.gL, O::sub(c.EL, V));
@@ -297,10 +302,11 @@ __device__ __forceinline__ void hh_neuron(typename O::T V, typename O::T m, type
     I = O::fma(O::mul(c.gsyn, others), O::sub(c.Esyn, V), I);
     I = O::add(I, drive);
     d[0] = O::mul(I, c.invC);
-    // gates: a (1 - y) - b y = a - (a + b) y
-    d[1] = O::sub(am, O::mul(O::add(am, bm), m));
-    d[2] = O::sub(ah, O::mul(O::add(ah, bh), h));
-    d[3] = O::sub(an, O::mul(O::add(an, bn), n));
+    // gates: a (1 - y) - b y = a - (a + b) y, with one rounding on both lane types (the
+    // toolchain would fuse the f32x2 form of an unfused product and difference anyway)
+    d[1] = O::fms(O::add(am, bm), m, am);
+    d[2] = O::fms(O::fma(ps, r, ah), h, ah);  // ah + bh with bh = ps r, fused likewise
+    d[3] = O::fms(O::add(an, bn), n, an);
     d[4] = O::fma(O::mul(act, c.inv_tr), O::sub(one, s), O::mul(s, c.neg_inv_td));
 }
 
@@ -1181,6 +1187,10 @@ struct HHPair {
         unpack2(y, ya, yb);
         return pack2(c.a ? xa : ya, c.b ? xb : yb);
     }
+    // a - t y with one rounding: f32x2 has no negated-operand form in PTX, and the toolchain
+    // fuses a product whose only use is this subtraction into one fused operation (the
+    // bit-identity tests of the one- and two-particle HH3 kernels depend on it and check it)
+    __device__ __forceinline__ static T fms(T t, T y, T a) { return sub2(a, mul2(t, y)); }
 };
 
 struct HH3RK4Packed {
@@ -1243,6 +1253,123 @@ struct HH3RK4Packed {
     }
 };
 template <bool KAHAN> struct StepperFor<HH3, FF_RK4, KAHAN> { using type = HH3RK4Packed; };
+
+// ---------------------------------------------------------------------------
+// RK4 for HH3 with two particles per work item, packed across particles: every
+// f32x2 register holds one state variable of particles 2t (lane 0) and 2t + 1
+// (lane 1), and all three neurons run the neuron right-hand side over f32x2.  The
+// one-particle stepper (HH3RK4Packed) packs neurons 0 and 1 and runs neuron 2 on
+// floats; here no neuron runs on floats, so a particle-step issues about three
+// quarters of the instructions.  Lane by lane the operations are those of HH3::f
+// and of the RK4 stepper, in the same order, so every state is the one-particle
+// kernel's to the bit (the adjoint's recomputation still reproduces the taped
+// states).  `a` may live in the argument block or, batched, in a device table.
+// ---------------------------------------------------------------------------
+// The neuron constants of two particles' parameter vectors, per lane (the
+// fields of hh_const<HHScalar>, each formed as it forms them).
+__device__ __forceinline__ HHConst<HHPair> hh_const_pair(const float* pa, const float* pb) {
+    const HHConst<HHScalar> a = hh_const<HHScalar>(pa), b = hh_const<HHScalar>(pb);
+    HHConst<HHPair> c;
+    c.gNa = pack2(a.gNa, b.gNa);
+    c.gK = pack2(a.gK, b.gK);
+    c.gL = pack2(a.gL, b.gL);
+    c.ENa = pack2(a.ENa, b.ENa);
+    c.EK = pack2(a.EK, b.EK);
+    c.EL = pack2(a.EL, b.EL);
+    c.gsyn = pack2(a.gsyn, b.gsyn);
+    c.Esyn = pack2(a.Esyn, b.Esyn);
+    c.invC = pack2(a.invC, b.invC);
+    c.inv_tr = pack2(a.inv_tr, b.inv_tr);
+    c.neg_inv_td = pack2(a.neg_inv_td, b.neg_inv_td);
+    c.neg_sig2 = pack2(a.neg_sig2, b.neg_sig2);
+    c.sig2_theta = pack2(a.sig2_theta, b.sig2_theta);
+    return c;
+}
+
+template <bool PP, bool TAPE>
+__device__ __forceinline__ void hh3_rk4_x2_item(const IntegrateArgs& a, int64_t t, int n_steps) {
+    constexpr int D = HH3::DIM;
+    const int64_t i0 = 2 * t;
+    f2 X[D];
+    float* ck0 = TAPE ? start_checkpoint(a) : nullptr;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float v[2];
+        Vec<2>::load(a.x + k * a.pitch + i0, v);
+        if (ck0) Vec<2>::store(ck0 + k * a.pitch + i0, v);
+        X[k] = pack2(v[0], v[1]);
+    }
+    float hs[2], pa[HH3::NP], pb[HH3::NP];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int64_t i = i0 + j;
+        hs[j] = a.gh[0];
+#pragma unroll
+        for (int g = 1; g < FF_MAX_GROUPS; ++g)
+            if (g < a.n_groups && i >= a.gstart[g]) hs[j] = a.gh[g];
+    }
+    const float pva = PP ? a.pparam[i0] : 0.0f, pvb = PP ? a.pparam[i0 + 1] : 0.0f;
+#pragma unroll
+    for (int q = 0; q < HH3::NP; ++q) {
+        pa[q] = (PP && q == a.pidx) ? pva : a.p[q];
+        pb[q] = (PP && q == a.pidx) ? pvb : a.p[q];
+    }
+    const HHConst<HHPair> c = hh_const_pair(pa, pb);
+    f2 drive[3];
+#pragma unroll
+    for (int n = 0; n < 3; ++n) drive[n] = pack2(pa[9 + n], pb[9 + n]);
+    // the stepper's constants, per lane: h, h/2, h/6
+    const f2 H1 = pack2(hs[0], hs[1]);
+    const f2 H2 = pack2(0.5f * hs[0], 0.5f * hs[1]);
+    const f2 H6 = pack2(hs[0] * (1.0f / 6.0f), hs[1] * (1.0f / 6.0f));
+    auto step = [&]() {
+        f2 XS[D], A[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            XS[k] = X[k];
+            A[k] = pack2(0.0f, 0.0f);
+        }
+#pragma unroll 1
+        for (int st = 0; st < 4; ++st) {
+            const f2 s_sum = add2(add2(XS[4], XS[9]), XS[14]);
+            f2 K[D];
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                f2 d[5];
+                hh_neuron<HHPair>(XS[5 * n], XS[5 * n + 1], XS[5 * n + 2], XS[5 * n + 3], XS[5 * n + 4],
+                                  sub2(s_sum, XS[5 * n + 4]), drive[n], c, d);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) K[5 * n + k] = d[k];
+            }
+            const float w = (st == 1 || st == 2) ? 2.0f : 1.0f;  // fmaf(1, k, 0) = k
+            const f2 W = pack2(w, w);
+#pragma unroll
+            for (int k = 0; k < D; ++k) A[k] = fma2(W, K[k], A[k]);
+            if (st == 3) break;
+            const f2 C = (st == 2) ? H1 : H2;
+#pragma unroll
+            for (int k = 0; k < D; ++k) XS[k] = fma2(C, K[k], X[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) X[k] = fma2(H6, A[k], X[k]);
+    };
+    auto save = [&](int slot) {
+        float* ck = a.ckpt + (int64_t)slot * a.ck_stride;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            float v[2];
+            unpack2(X[k], v[0], v[1]);
+            Vec<2>::store(ck + k * a.pitch + i0, v);
+        }
+    };
+    run_steps<1, TAPE>(a, n_steps, step, save);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float v[2];
+        unpack2(X[k], v[0], v[1]);
+        Vec<2>::store(a.x + k * a.pitch + i0, v);
+    }
+}
 
 // HH3::f with neurons 0 and 1 packed in f32x2 registers and neuron 2 on floats, as
 // in HH3RK4Packed: lane by lane the same operations as HH3::f, so the same bits.

@@ -167,6 +167,64 @@ def test_integrate_parity(name, method, kahan):
                  method=oracle.RK4 if method == "rk4" else oracle.EULER)
 
 
+@pytest.mark.parametrize("method,kahan", [("rk4", False), ("euler", False), ("rk4", True)])
+def test_hh3_two_particles_per_thread_bit_identical(method, kahan):
+    """HH x 3 at two particles per thread (RK4: all three neurons of a particle pair packed in
+    f32x2, for an ensemble that fills a wave of pairs; Euler and the compensated update fall
+    back to one particle per thread) ends bit-identical to one particle per thread -- also for a
+    pair that straddles a forward / backward group boundary (lanes with different signed steps)
+    and across chunked launches -- and meets the oracle bar on a sample."""
+    rhs, params, dim, (lo, hi), dt = CASES["hh3"]
+    groups = [G(120_001, lo, hi, 1, 61), G(37, lo, hi, -1, 62), G(2, lo, hi, 1, 63)]
+    one = make_system(rhs, params, groups, dim, method=method, kahan=kahan, ppt=1)
+    two = make_system(rhs, params, groups, dim, method=method, kahan=kahan, ppt=2)
+    chunked = make_system(rhs, params, groups, dim, method=method, kahan=kahan, ppt=2)
+    chunked.set_launch(2, 0, 0, 13)
+    for sysobj in (one, two, chunked):
+        sysobj.step(60, dt)
+    np.testing.assert_array_equal(get_state(two), get_state(one))
+    np.testing.assert_array_equal(get_state(chunked), get_state(one))
+    pair = "hh3_rk4_x2_kernel" in two.last_launch()["kernel"]
+    assert pair == (method == "rk4" and not kahan)
+    idx = np.sort(np.random.default_rng(8).choice(120_001, 2000, replace=False))
+    x0 = oracle_seed(groups, dim)[:, idx]
+    h = oracle_h(groups, dt)[idx]
+    m = oracle.RK4 if method == "rk4" else oracle.EULER
+    want = oracle.integrate(oracle.HH3, x0, params, h, 60, method=m)
+    check_parity(oracle.HH3, get_state(two)[:, idx], want, x0, params, h, 60, method=m)
+
+
+def test_hh3_two_particles_per_thread_small_ensemble_runs_singles():
+    rhs, params, dim, (lo, hi), dt = CASES["hh3"]
+    s = make_system(rhs, params, [G(16_384, lo, hi, 1, 64)], dim, ppt=2)
+    s.step(5, dt)
+    assert "integrate_kernel<ff::HH3" in s.last_launch()["kernel"]  # too few pairs to fill a wave
+
+
+def test_hh3_two_particles_per_thread_taped_checkpoints():
+    """A taped HH x 3 run at two particles per thread writes the checkpoints of the run at one
+    particle per thread, and the adjoint from them gives the same gradients."""
+    rhs, params, dim, (lo, hi), dt = CASES["hh3"]
+    n = 120_004
+    groups = [G(n, lo, hi, 1, 71)]
+    grads = []
+    for ppt in (1, 2):
+        s = make_system(rhs, params, groups, dim, ppt=ppt)
+        s.tape_begin(10, 50)
+        s.step(50, dt)
+        assert ("hh3_rk4_x2_kernel" in s.last_launch()["kernel"]) == (ppt == 2)
+        xT = torch.empty((dim, n), dtype=torch.float32, device="cuda")
+        s.get_state(xT)
+        g = (xT * 1e-3).contiguous()
+        out = torch.empty_like(g)
+        dp = s.backward(g, out, len(params))
+        grads.append((xT.cpu().numpy(), out.cpu().numpy(), np.asarray(dp)))
+        s.tape_end()
+    np.testing.assert_array_equal(grads[0][0], grads[1][0])
+    np.testing.assert_array_equal(grads[0][1], grads[1][1])
+    np.testing.assert_array_equal(grads[0][2], grads[1][2])
+
+
 def test_hh3_backward_escapes_like_oracle():
     rhs, params, dim, (lo, hi), dt = CASES["hh3"]
     groups = [G(2000, lo, hi, -1, 99)]

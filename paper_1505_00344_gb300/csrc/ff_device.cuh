@@ -165,18 +165,19 @@ struct WilsonCowan {
     static constexpr int DIM = 2;
     static constexpr int NP = 10;
     static constexpr int MAX_BLOCK = 512;
-    __device__ __forceinline__ static float S(float a, float g2, float g2th) {
-        // exp(-gain (a - th)) = 2^(g2 th - g2 a) with g2 = gain * log2(e)
-        const float e = ex2_ftz(fmaf(-g2, a, g2th));
-        return rcp_ftz(1.0f + e);
-    }
     __device__ __forceinline__ static void f(const float (&x)[DIM], const float* p, float (&dx)[DIM]) {
         const float E = x[0], I = x[1];
-        const float g2 = p[8] * kLog2e, g2th = g2 * p[9];
-        const float aE = fmaf(p[0], E, fmaf(-p[1], I, p[4]));
-        const float aI = fmaf(p[2], E, fmaf(-p[3], I, p[5]));
-        dx[0] = __fdividef(S(aE, g2, g2th) - E, p[6]);
-        dx[1] = __fdividef(S(aI, g2, g2th) - I, p[7]);
+        // the logistic's exponent -gain (a - th), a = wE E - wI I + drive, as one affine form
+        // of E and I in base 2 (the constants depend on the parameters only, so a step loop
+        // forms them once), and (S - x) / tau as S / tau - x / tau: from a stage point to its
+        // derivative the dependent chain is two FMAs, ex2, an add, rcp and one FMA
+        const float g2 = p[8] * kLog2e;
+        const float argE = fmaf(-g2 * p[0], E, fmaf(g2 * p[1], I, g2 * (p[9] - p[4])));
+        const float argI = fmaf(-g2 * p[2], E, fmaf(g2 * p[3], I, g2 * (p[9] - p[5])));
+        const float SE = rcp_ftz(1.0f + ex2_ftz(argE)), SI = rcp_ftz(1.0f + ex2_ftz(argI));
+        const float iE = __fdividef(1.0f, p[6]), iI = __fdividef(1.0f, p[7]);
+        dx[0] = fmaf(SE, iE, -E * iE);
+        dx[1] = fmaf(SI, iI, -I * iI);
     }
 };
 

@@ -32,7 +32,7 @@ struct AdjointArgs {
     int64_t n;               // particles
     int64_t pitch;           // floats between checkpoint planes
     int n_groups;
-    int pad_;
+    int max_chunk;           // steps of the longest chunk (the tape's checkpoint spacing)
     int64_t gstart[FF_MAX_GROUPS];
     float* scratch;           // staged sweep (15-dimensional system): one chunk of states per thread
     int64_t scratch_threads;  // threads the scratch has room for (floats = threads * chunk steps * dim)

@@ -1059,6 +1059,170 @@ __global__ void __launch_bounds__(kLx2Block, 8) adjoint_lorenz_x2_kernel(const _
     block_sum_to_row<3, kLx2Block / 32>(gacc, red, a.partial + (int64_t)blockIdx.x * a.np_stride);
 }
 
+// ---------------------------------------------------------------------------
+// Packed-pair sweep for chunks longer than 16 steps: sub-segments of 4 steps
+// whose recomputation also keeps each step's three stage points, so the reverse
+// step applies the four Jacobian products without recomputing them.  Per
+// 64-thread block the 4 steps x (state + 3 stage points) take the 24.6 KB the
+// 16 states of the plain sweep took; the sub-checkpoints (up to 64 per chunk)
+// live in local memory.  The stage points are the ones lorenz_adj2 recomputes,
+// operation for operation, so dL/dx0 is unchanged to the bit.
+// ---------------------------------------------------------------------------
+constexpr int kLx2sSub = 4;      // steps per sub-segment
+constexpr int kLx2sMaxSub = 64;  // sub-checkpoints of a chunk of up to 256 steps
+
+// lorenz_fwd2 that also returns the stage points x2, x3, x4 (S[3 s + k], component k of
+// stage point s + 2); with full false the step's update is skipped.
+__device__ __forceinline__ void lorenz_fwd2_stages(f2 (&x)[3], const LorenzPairS& c, f2 (&S)[9], bool full) {
+    const f2 two = pack2(2.0f, 2.0f);
+    f2 d, A, kz, X, Y, Z, a0, a1, a2;
+    d = sub2(x[1], x[0]);
+    A = fma2(x[0], x[2], x[1]);
+    kz = fma2(x[0], x[1], fma2(c.nb, x[2], c.nbr));
+    a0 = d; a1 = A; a2 = kz;
+    X = fma2(c.sh2, d, x[0]); Y = fma2(c.nh2, A, x[1]); Z = fma2(c.h2, kz, x[2]);
+    S[0] = X; S[1] = Y; S[2] = Z;
+    d = sub2(Y, X);
+    A = fma2(X, Z, Y);
+    kz = fma2(X, Y, fma2(c.nb, Z, c.nbr));
+    a0 = fma2(two, d, a0); a1 = fma2(two, A, a1); a2 = fma2(two, kz, a2);
+    X = fma2(c.sh2, d, x[0]); Y = fma2(c.nh2, A, x[1]); Z = fma2(c.h2, kz, x[2]);
+    S[3] = X; S[4] = Y; S[5] = Z;
+    d = sub2(Y, X);
+    A = fma2(X, Z, Y);
+    kz = fma2(X, Y, fma2(c.nb, Z, c.nbr));
+    a0 = fma2(two, d, a0); a1 = fma2(two, A, a1); a2 = fma2(two, kz, a2);
+    X = fma2(c.sh1, d, x[0]); Y = fma2(c.nh1, A, x[1]); Z = fma2(c.h1, kz, x[2]);
+    S[6] = X; S[7] = Y; S[8] = Z;
+    if (!full) return;
+    d = sub2(Y, X);
+    A = fma2(X, Z, Y);
+    kz = fma2(X, Y, fma2(c.nb, Z, c.nbr));
+    a0 = add2(a0, d); a1 = add2(a1, A); a2 = add2(a2, kz);
+    x[0] = fma2(c.sh6, a0, x[0]); x[1] = fma2(c.nh6, a1, x[1]); x[2] = fma2(c.h6, a2, x[2]);
+}
+
+// lorenz_adj2 with the stage points given (the same products and sums).
+__device__ __forceinline__ void lorenz_adj2_given(const f2 (&x)[3], const f2 (&x2)[3], const f2 (&x3)[3],
+                                                  const f2 (&x4)[3], f2 (&lam)[3], const LorenzPairS& c,
+                                                  f2 (&jp)[3]) {
+    const f2 d1 = sub2(x[1], x[0]), d2 = sub2(x2[1], x2[0]), d3 = sub2(x3[1], x3[0]), d4 = sub2(x4[1], x4[0]);
+    f2 u[3], u2[3], l[3], m[3], sum[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { u[i] = mul2a(c.h6, lam[i]); u2[i] = add2(u[i], u[i]); }
+    lorenz_vjp2(x4, d4, c, u, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { sum[i] = m[i]; l[i] = fma2(c.h1, m[i], u2[i]); }
+    lorenz_vjp2(x3, d3, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(c.h2, m[i], u2[i]); }
+    lorenz_vjp2(x2, d2, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { sum[i] = add2(sum[i], m[i]); l[i] = fma2(c.h2, m[i], u[i]); }
+    lorenz_vjp2(x, d1, c, l, m, jp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) lam[i] = add2(lam[i], add2(sum[i], m[i]));
+}
+
+template <bool PP>
+__global__ void __launch_bounds__(kLx2Block, 8) adjoint_lorenz_x2s_kernel(const __grid_constant__ AdjointArgs a) {
+    constexpr int MS = kLx2sSub;
+    __shared__ double red[kLx2Block / 32][3];
+    __shared__ f2 st[MS][12][kLx2Block];  // per step: the state, then stage points 2, 3, 4
+    const int tid = threadIdx.x;
+    double gacc[3] = {0.0, 0.0, 0.0};
+    const int64_t npair = (a.n + 1) / 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += stride) {
+        const int64_t i0 = 2 * t, i1 = 2 * t + 1;
+        const bool has1 = i1 < a.n;  // an odd count leaves the last pair half empty
+        int g0 = 0, g1 = 0;
+#pragma unroll
+        for (int q = 1; q < FF_MAX_GROUPS; ++q) {
+            if (q < a.n_groups && i0 >= a.gstart[q]) g0 = q;
+            if (q < a.n_groups && i1 >= a.gstart[q]) g1 = q;
+        }
+        f2 lam[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            lam[k] = pack2(a.lam_in[k * a.n + i0], has1 ? a.lam_in[k * a.n + i1] : 0.0f);
+        const float pv0 = PP ? a.pparam[i0] : 0.0f, pv1 = (PP && has1) ? a.pparam[i1] : 0.0f;
+        for (int c = a.n_chunks - 1; c >= 0; --c) {
+            const AdjChunk& ch = a.chunks[c];
+            float pa[3], pb[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                pa[q] = (PP && q == a.pidx) ? pv0 : ch.p[q];
+                pb[q] = (PP && q == a.pidx) ? pv1 : ch.p[q];
+            }
+            LorenzShiftC ca, cb;
+            ca.init(ch.gh[g0], pa);
+            cb.init(ch.gh[g1], pb);
+            const LorenzPairS cp2 = lorenz_pair(ca, cb);
+            const int L = ch.n_steps;
+            const float* ck = a.ckpt + (int64_t)ch.ckpt * a.dim * a.pitch;
+            f2 x[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) x[k] = pack2(ck[k * a.pitch + i0], ck[k * a.pitch + i1]);  // pitch covers i1
+            x[2] = sub2(x[2], pack2(pa[1], pb[1]));  // zt = z - r
+            f2 cpt[kLx2sMaxSub][3];
+            int nsub = 0;
+            for (int base = 0; base < L; base += MS, ++nsub) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cpt[nsub][k] = x[k];
+                const int nq = (base + MS < L) ? MS : 0;
+#pragma unroll 1
+                for (int r = 0; r < nq; ++r) lorenz_fwd2(x, cp2);
+            }
+            f2 jp[3] = {pack2(0.f, 0.f), pack2(0.f, 0.f), pack2(0.f, 0.f)};
+            for (int sq = nsub - 1; sq >= 0; --sq) {
+                const int nq = min(MS, L - sq * MS);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) x[k] = cpt[sq][k];
+#pragma unroll
+                for (int r = 0; r < MS; ++r) {
+                    if (r < nq) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) st[r][k][tid] = x[k];
+                        f2 S[9];
+                        lorenz_fwd2_stages(x, cp2, S, r + 1 < nq);
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) st[r][3 + k][tid] = S[k];
+                    }
+                }
+#pragma unroll
+                for (int r = MS - 1; r >= 0; --r)
+                    if (r < nq) {
+                        f2 xr[3], x2[3], x3[3], x4[3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            xr[k] = st[r][k][tid];
+                            x2[k] = st[r][3 + k][tid];
+                            x3[k] = st[r][6 + k][tid];
+                            x4[k] = st[r][9 + k][tid];
+                        }
+                        lorenz_adj2_given(xr, x2, x3, x4, lam, cp2, jp);
+                    }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                float u, w;
+                unpack2(jp[q], u, w);
+                gacc[q] += (double)u;
+                if (has1) gacc[q] += (double)w;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float u, w;
+            unpack2(lam[k], u, w);
+            a.lam_out[k * a.n + i0] = u;
+            if (has1) a.lam_out[k * a.n + i1] = w;
+        }
+    }
+    block_sum_to_row<3, kLx2Block / 32>(gacc, red, a.partial + (int64_t)blockIdx.x * a.np_stride);
+}
+
 // Batched adjoint: each block takes tiles round-robin; a tile is a run of
 // particles of one member, one per thread, and its parameter gradient is
 // reduced over the block into the tile's own row.
@@ -1148,9 +1312,9 @@ static cudaError_t launch_r(int method, bool pp, int m, const AdjointArgs& a, in
     }
 }
 
-template <bool PP, int M>
-static cudaError_t launch_lorenz_x2_one(const AdjointArgs& a, int num_sms, cudaStream_t s, int64_t* rows) {
-    auto kernel = adjoint_lorenz_x2_kernel<PP, M>;
+template <class Kernel>
+static cudaError_t launch_lorenz_x2_kernel(Kernel kernel, const AdjointArgs& a, int num_sms, cudaStream_t s,
+                                           int64_t* rows) {
     // the sub-segment states take shared memory, so favour it over L1
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
@@ -1169,8 +1333,20 @@ static cudaError_t launch_lorenz_x2_one(const AdjointArgs& a, int num_sms, cudaS
     return cudaGetLastError();
 }
 
+template <bool PP, int M>
+static cudaError_t launch_lorenz_x2_one(const AdjointArgs& a, int num_sms, cudaStream_t s, int64_t* rows) {
+    return launch_lorenz_x2_kernel(adjoint_lorenz_x2_kernel<PP, M>, a, num_sms, s, rows);
+}
+
 static cudaError_t launch_lorenz_x2(bool pp, int m, const AdjointArgs& a, int num_sms, cudaStream_t s,
                                     int64_t* rows) {
+    // chunks of up to 16 steps are one sub-segment (one recomputation); longer ones take the
+    // sweep with 4-step sub-segments that keep their stage points
+    if (a.max_chunk > 16) {
+        if (a.max_chunk > kLx2sSub * kLx2sMaxSub) return cudaErrorInvalidValue;
+        return pp ? launch_lorenz_x2_kernel(adjoint_lorenz_x2s_kernel<true>, a, num_sms, s, rows)
+                  : launch_lorenz_x2_kernel(adjoint_lorenz_x2s_kernel<false>, a, num_sms, s, rows);
+    }
     switch (m) {
     case 4: return pp ? launch_lorenz_x2_one<true, 4>(a, num_sms, s, rows) : launch_lorenz_x2_one<false, 4>(a, num_sms, s, rows);
     case 8: return pp ? launch_lorenz_x2_one<true, 8>(a, num_sms, s, rows) : launch_lorenz_x2_one<false, 8>(a, num_sms, s, rows);

@@ -690,6 +690,7 @@ ff_status ff_backward(ff_system* s, const float* dL_dxT_dev, float* dL_dx0_dev, 
     a.n = s->n_particles;
     a.pitch = s->pitch;
     a.n_groups = s->n_groups;
+    a.max_chunk = (int)s->tape_every;
     for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
     // the staged sweep (HH x 3) keeps a chunk of states per thread in a scratch area,
     // allocated on first use and kept with the tape

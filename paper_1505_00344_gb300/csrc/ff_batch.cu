@@ -522,6 +522,7 @@ ff_status ff_batch_backward(ff_batch* b, const float* const* dL_dxT_dev, float* 
             a.n = s->n_particles;
             a.pitch = s->pitch;
             a.n_groups = s->n_groups;
+            a.max_chunk = (int)s->tape_every;
             for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
             f.row0[m] = (int)f.adj_tiles.size();
             for (int64_t first = 0; first < s->n_particles; first += ff::kAdjTile) {

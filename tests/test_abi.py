@@ -120,6 +120,15 @@ def test_host_side_argument_errors(lib):
     assert lib.ff_batch_backward(None, None, None, None) == ff.FF_ERR_INVALID_ARG
     sp = ff.make_sprite(2.0)
     assert lib.ff_project_sprites(None, None, ctypes.byref(sp), None, 1) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_seed_particles_slice(None, 1, 0, 1, None, None, 1, 0, None) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_set_particle_param_slice(None, 0, 0.0, 1.0, 0, 1) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_last_launch(None, None, 0, None, None, None, None, None) == ff.FF_ERR_INVALID_ARG
+    # the microbenchmark checks its arguments before touching a device
+    rate = ctypes.c_double(0.0)
+    assert lib.ff_pipe_rate(ff.FF_PIPE_FFMA, 0, None) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_pipe_rate(-1, 0, ctypes.byref(rate)) == ff.FF_ERR_INVALID_ARG
+    assert lib.ff_pipe_rate(ff.FF_PIPE_LOGISTIC + 1, 0, ctypes.byref(rate)) == ff.FF_ERR_INVALID_ARG
+    assert "unknown op" in ff.ff_last_error()
 
 
 def test_binding_raises_with_message(lib):

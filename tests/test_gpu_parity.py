@@ -602,3 +602,22 @@ def test_step_splat_fallbacks_wc_and_host_image():
     np.testing.assert_array_equal(ha, hb)
     with pytest.raises(ff.FFError):
         a.step_splat(1, 0.01, dict(view, ndim_view=5), ha)
+
+
+def test_pipe_rates_are_consistent():
+    """ff_pipe_rate, the denominators of the ALU rooflines: the packed FMA does not widen the
+    FP32 pipe (FFMA2 lane rate within 15% of FFMA's), no rate exceeds its unit count at the
+    maximum clock, and the logistic chain (one ex2 and one rcp per step) runs at the rate of
+    two operations sharing one unit, 2 / (1/ex2 + 1/rcp), within 10% -- the model the
+    multi-function rooflines use."""
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    r = {name: ff.ff_pipe_rate(op, 0) for name, op in (("ffma", ff.FF_PIPE_FFMA), ("ffma2", ff.FF_PIPE_FFMA2),
+                                                      ("ex2", ff.FF_PIPE_EX2), ("rcp", ff.FF_PIPE_RCP),
+                                                      ("logistic", ff.FF_PIPE_LOGISTIC))}
+    clock = 2.2e9  # above the maximum SM clock of this part
+    assert 0.85 <= r["ffma2"] / r["ffma"] <= 1.15
+    assert r["ffma"] <= sms * 128 * clock and r["ffma2"] <= sms * 128 * clock
+    assert r["ex2"] <= sms * 32 * clock and r["rcp"] <= sms * 32 * clock
+    model = 2.0 / (1.0 / r["ex2"] + 1.0 / r["rcp"])
+    assert abs(r["logistic"] / model - 1.0) <= 0.10, (r, model)

@@ -444,6 +444,16 @@ def run_ours(args, rank, world, local):
     if default_run:
         # the gradient half of the metric and the other workloads, each with its own clocks
         result["adjoint"] = adjoint_record(args, w, dev, stream, world)
+        result["adjoint_hh3_1M"] = adjoint_record(args, W.shard(W.workload("hh3_1M"), rank, world), dev, stream,
+                                                  world, n=1000, K=100)
+        # the batched systems: forward (one graph launch per step call) and gradients
+        # (every rank runs the whole batch: the job's value is this rank's times the ranks)
+        result["batch_mixed256"] = {
+            "forward": batch_timings("mixed_batch256", 500, 3, 1, dev, stream, clocks_enabled=not args.no_clocks),
+            "adjoint": batch_adjoint_timings("mixed_batch256", 200, 100, 2, 1, dev, stream,
+                                             clocks_enabled=not args.no_clocks)}
+        for r in result["batch_mixed256"].values():
+            r["value"] *= world
         result["workloads"] = {}
         for name, steps in (("hh3_1M", 2), ("lorenz_bif_8M", 3), ("wc_4k", 10)):
             wl = W.shard(W.workload(name), rank, world)
@@ -631,10 +641,10 @@ def adjoint_timings(w, n, K, steps, warmup, dev, stream, clocks_enabled=True):
                               "note": "timed region shorter than the 200 ms sampling interval"}}
 
 
-def adjoint_record(args, w, dev, stream, world):
-    """The gradient half of the metric inside the default bench line: lorenz_4M particles,
-    2,000 RK4 steps, checkpoint every 100."""
-    r = adjoint_timings(w, 2000, 100, 3, 2, dev, stream, clocks_enabled=not args.no_clocks)
+def adjoint_record(args, w, dev, stream, world, n=2000, K=100):
+    """The gradient half of the metric inside the default bench line: the workload's particles,
+    n RK4 steps, checkpoint every K (lorenz_4M: 2,000 and 100)."""
+    r = adjoint_timings(w, n, K, 3, 2, dev, stream, clocks_enabled=not args.no_clocks)
     r["metric"] = "adjoint particle-RK4-steps/sec (gradients w.r.t. initial states and parameters)"
     r["loss"] = "mean squared distance of final states to random targets"
     r["dtype"] = "f32 (FP64 parameter sums)"
@@ -664,21 +674,66 @@ def run_adjoint(args, rank, world, local):
             "backward_over_plain_time": r["backward_over_plain_time"], "ms": r["ms"], "clocks": r["clocks"]}
 
 
-def run_batch_adjoint(args, rank, world, local):
-    """The differentiable batched ensemble: a taped ff_batch_step of --adjoint-steps RK4
-    steps (checkpoint every --checkpoint-every) and one ff_batch_backward, gradients of
-    L = sum_s (1/P_s) sum_i |x_i(T) - t_i|^2 w.r.t. every member's initial states and
-    parameters; against the plain batched forward."""
+def _timed_on_stream(fn):
+    import torch
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record()
+    fn()
+    e.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(e)
+
+
+def batch_timings(name, n, steps, warmup, dev, stream, clocks_enabled=True):
+    """ff_batch_step of n RK4 steps over a batched workload (one graph launch, autotuned
+    launch shapes) against stepping the same systems one after the other with ff_step."""
+    import paper_1505_00344_gb300 as ff
+
+    ws = W.batch_workload(name)
+    systems = [ff.System.from_workload(w, stream=stream) for w in ws]
+    dts = [w["dt"] for w in ws]
+    units = sum(total_particles(w) for w in ws) * n
+    b = ff.Batch(systems, stream=stream)
+    b.autotune(dts, trial_steps=max(8, min(64, n // 10)))
+
+    def batched():
+        b.step(n, dts)
+
+    def one_by_one():
+        for s_, dt in zip(systems, dts):
+            s_.step(n, dt)
+
+    for _ in range(warmup):
+        batched()
+    clocks = ClockSampler(dev.index, enabled=clocks_enabled)
+    tb = [_timed_on_stream(batched) for _ in range(max(1, steps))]
+    clk = clocks.stop()
+    to = [_timed_on_stream(one_by_one) for _ in range(max(1, steps))]
+    launch = b.describe().strip().split("\n")
+    b.close()
+    for s_ in systems:
+        s_.close()
+    med = statistics.median
+    return {"metric": "particle-RK4-steps/sec (batched systems)", "value": units / (med(tb) / 1e3), "unit": UNIT,
+            "workload": name, "systems": len(ws), "particles": units // n, "rk4_steps": n, "ms": med(tb),
+            "launch": launch, "one_by_one": units / (med(to) / 1e3), "speedup_vs_one_by_one": med(to) / med(tb),
+            "gpu_launches": len({(w["rhs"], w["method"]) for w in ws}),  # one kernel per family in the graph
+            "clocks": clk or {"sm_mhz": None, "samples": 0, "reasons": [],
+                              "note": "timed region shorter than the 200 ms sampling interval"}}
+
+
+def batch_adjoint_timings(name, n, K, steps, warmup, dev, stream, clocks_enabled=True):
+    """The differentiable batched ensemble: a taped ff_batch_step of n RK4 steps (checkpoint
+    every K) and one ff_batch_backward, gradients of L = sum_s (1/P_s) sum_i |x_i(T) - t_i|^2
+    w.r.t. every member's initial states and parameters; against the plain batched forward."""
     import torch
     import paper_1505_00344_gb300 as ff
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream().cuda_stream
-    ws = W.batch_workload(args.batch)
+    ws = W.batch_workload(name)
     systems = [ff.System.from_workload(w, stream=stream) for w in ws]
     dts = [w["dt"] for w in ws]
-    n, K = args.adjoint_steps, args.checkpoint_every
     b = ff.Batch(systems, stream=stream)
     b.autotune(dts, trial_steps=16)
     x0, tgt = [], []
@@ -693,16 +748,6 @@ def run_batch_adjoint(args, rank, world, local):
         tgt.append(lo + (hi - lo) * torch.rand((dim, P), generator=g, device=dev))
     units = sum(total_particles(w) for w in ws) * n
 
-    def timed(fn):
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        a.record()
-        fn()
-        e.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(e)
-
     def restore():
         for s, x in zip(systems, x0):
             s.set_state(x)
@@ -716,79 +761,72 @@ def run_batch_adjoint(args, rank, world, local):
             g.sub_(t).mul_(2.0 / x.shape[1])
 
     t_plain, t_fwd, t_bwd = [], [], []
-    for it in range(args.warmup + max(1, args.steps)):
+    clocks = None
+    for it in range(warmup + max(1, steps)):
+        if it == warmup:
+            clocks = ClockSampler(dev.index, enabled=clocks_enabled)
         restore()
-        tp = timed(lambda: b.step(n, dts))
+        tp = _timed_on_stream(lambda: b.step(n, dts))
         restore()
         b.tape_begin(K, n)
-        tf = timed(lambda: b.step(n, dts))
+        tf = _timed_on_stream(lambda: b.step(n, dts))
         loss_grads()
-        tb = timed(lambda: b.backward(grads, outs))
+        tb = _timed_on_stream(lambda: b.backward(grads, outs))
         b.tape_end()
-        if it >= args.warmup:
+        if it >= warmup:
             t_plain.append(tp)
             t_fwd.append(tf)
             t_bwd.append(tb)
+    clk = clocks.stop()
+    launch = b.describe().strip().split("\n")
+    b.close()
+    for s_ in systems:
+        s_.close()
     med = statistics.median
     return {"metric": "adjoint particle-RK4-steps/sec (batched ensemble, gradients w.r.t. all initial states "
                       "and parameters)",
-            "value": units / (med(t_bwd) / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": med(t_bwd), "higher_is_better": True, "scaling": "weak",
+            "value": units / (med(t_bwd) / 1e3), "unit": UNIT, "workload": name, "systems": len(ws),
+            "particles": units // n, "rk4_steps": n, "checkpoint_every": K,
+            "loss": "sum over systems of the mean squared endpoint distance to seeded targets",
+            "launch": launch, "plain_forward": units / (med(t_plain) / 1e3),
+            "taped_forward": units / (med(t_fwd) / 1e3), "backward_over_plain_time": med(t_bwd) / med(t_plain),
+            "ms": {"plain": med(t_plain), "taped_forward": med(t_fwd), "backward": med(t_bwd)},
+            "clocks": clk or {"sm_mhz": None, "samples": 0, "reasons": [],
+                              "note": "timed region shorter than the 200 ms sampling interval"}}
+
+
+def run_batch_adjoint(args, rank, world, local):
+    """Command-line form of batch_adjoint_timings (--batch NAME --adjoint)."""
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    r = batch_adjoint_timings(args.batch, args.adjoint_steps, args.checkpoint_every, args.steps, args.warmup, dev,
+                              torch.cuda.current_stream().cuda_stream, clocks_enabled=not args.no_clocks)
+    return {"metric": r["metric"], "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"]["backward"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (FP64 parameter sums)", "data": "synthetic",
-            "config": {"workload": args.batch, "systems": len(ws), "particles": units // n, "rk4_steps": n,
-                       "checkpoint_every": K, "loss": "sum over systems of the mean squared endpoint distance "
-                                                     "to seeded targets",
-                       "launch": b.describe().strip().split("\n")},
-            "plain_forward": units / (med(t_plain) / 1e3), "taped_forward": units / (med(t_fwd) / 1e3),
-            "backward_over_plain_time": med(t_bwd) / med(t_plain),
-            "ms": {"plain": med(t_plain), "taped_forward": med(t_fwd), "backward": med(t_bwd)}}
+            "config": {"workload": args.batch, "systems": r["systems"], "particles": r["particles"],
+                       "rk4_steps": r["rk4_steps"], "checkpoint_every": r["checkpoint_every"], "loss": r["loss"],
+                       "launch": r["launch"]},
+            "plain_forward": r["plain_forward"], "taped_forward": r["taped_forward"],
+            "backward_over_plain_time": r["backward_over_plain_time"], "ms": r["ms"], "clocks": r["clocks"]}
 
 
 def run_batch(args, rank, world, local):
-    """A batched workload: ff_batch_step (one graph launch, autotuned launch shapes) against
-    stepping the same systems one after the other with ff_step."""
+    """Command-line form of batch_timings (--batch NAME)."""
     import torch
-    import paper_1505_00344_gb300 as ff
 
     torch.cuda.set_device(local)
-    stream = torch.cuda.current_stream().cuda_stream
-    ws = W.batch_workload(args.batch)
-    systems = [ff.System.from_workload(w, stream=stream) for w in ws]
-    dts = [w["dt"] for w in ws]
-    n = args.batch_steps
-    units = sum(total_particles(w) for w in ws) * n
-    b = ff.Batch(systems, stream=stream)
-    b.autotune(dts, trial_steps=max(8, min(64, n // 10)))
-
-    def timed(fn):
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        a.record()
-        fn()
-        e.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(e)
-
-    def batched():
-        b.step(n, dts)
-
-    def one_by_one():
-        for s_, dt in zip(systems, dts):
-            s_.step(n, dt)
-
-    for _ in range(args.warmup):
-        batched()
-    tb = [timed(batched) for _ in range(max(1, args.steps))]
-    to = [timed(one_by_one) for _ in range(max(1, args.steps))]
-    med = statistics.median
-    return {"metric": "particle-RK4-steps/sec (batched systems)", "value": units / (med(tb) / 1e3), "unit": UNIT,
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": med(tb),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.batch, "systems": len(ws), "particles": units // n, "rk4_steps": n,
-                       "launch": b.describe().strip().split("\n")},
-            "one_by_one": units / (med(to) / 1e3), "speedup_vs_one_by_one": med(to) / med(tb),
-            "gpu_launches": len({(w["rhs"], w["method"]) for w in ws})}  # one kernel per family in the graph
+    r = batch_timings(args.batch, args.batch_steps, args.steps, args.warmup, torch.device("cuda", local),
+                      torch.cuda.current_stream().cuda_stream, clocks_enabled=not args.no_clocks)
+    return {"metric": r["metric"], "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.batch, "systems": r["systems"], "particles": r["particles"],
+                       "rk4_steps": r["rk4_steps"], "launch": r["launch"]},
+            "one_by_one": r["one_by_one"], "speedup_vs_one_by_one": r["speedup_vs_one_by_one"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
 
 
 def run_sprites(args, rank, world, local):

@@ -165,12 +165,14 @@ __device__ __forceinline__ void hh_neuron_vjp(typename O::T V, typename O::T m, 
     const T rmn = O::rcp(O::mul(dm, dn));
     const T rm = O::mul(dn, rmn), rn = O::mul(dm, rmn);  // 1 / dm, 1 / dn
     // g(y) = y / (1 - e^-y), g'(y) = (1 - e^-y (1 + y)) / (1 - e^-y)^2; alpha_m = g(ym), alpha_n = g(yn) / 10
-    const T am = O::sel(sm, bernoulli_series_t<O>(ym), O::mul(ym, rm));
-    const T gn = O::sel(sn, bernoulli_series_t<O>(yn), O::mul(yn, rn));
-    const T dgm = O::sel(sm, bernoulli_series_deriv_t<O>(ym),
-                         O::mul(O::fms(em, O::add(one, ym), one), O::mul(rm, rm)));
-    const T dgn = O::sel(sn, bernoulli_series_deriv_t<O>(yn),
-                         O::mul(O::fms(en, O::add(one, yn), one), O::mul(rn, rn)));
+    // at most one of ym, yn (which differ by 1.5) lies in the series band: one series and one
+    // derivative series serve both
+    const T ys = O::sel(sm, ym, yn);
+    const T ser = bernoulli_series_t<O>(ys), dser = bernoulli_series_deriv_t<O>(ys);
+    const T am = O::sel(sm, ser, O::mul(ym, rm));
+    const T gn = O::sel(sn, ser, O::mul(yn, rn));
+    const T dgm = O::sel(sm, dser, O::mul(O::fms(em, O::add(one, ym), one), O::mul(rm, rm)));
+    const T dgn = O::sel(sn, dser, O::mul(O::fms(en, O::add(one, yn), one), O::mul(rn, rn)));
     const T anbn = O::fma(O::k(0.1f), gn, bn);  // alpha_n + beta_n (alpha_n = g(yn) / 10), fused
     const T dam = O::mul(O::k(0.1f), dgm), dan = O::mul(O::k(0.01f), dgn);
     const T ph = O::fma(O::k(kE3), q8, one), ps = O::add(one, es);

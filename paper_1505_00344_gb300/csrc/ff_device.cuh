@@ -227,22 +227,24 @@ struct HHScalar {
 };
 
 // Parameter-derived constants of the neuron right-hand side.
+// The conductances come divided by the capacitance C (and the caller passes the drive as
+// I_i / C), so that dV/dt is the current sum itself.
 template <class O> struct HHConst {
-    typename O::T gNa, gK, gL, ENa, EK, EL, gsyn, Esyn, invC, inv_tr, neg_inv_td, neg_sig2, sig2_theta;
+    typename O::T gNaC, gKC, gLC, ENa, EK, EL, gsynC, Esyn, inv_tr, neg_inv_td, neg_sig2, sig2_theta;
 };
 
 template <class O>
 __device__ __forceinline__ HHConst<O> hh_const(const float* p) {
     HHConst<O> c;
-    c.gNa = O::k(p[1]);
-    c.gK = O::k(p[2]);
-    c.gL = O::k(p[3]);
+    const float invC = __fdividef(1.0f, p[0]);
+    c.gNaC = O::k(__fmul_rn(p[1], invC));
+    c.gKC = O::k(__fmul_rn(p[2], invC));
+    c.gLC = O::k(__fmul_rn(p[3], invC));
     c.ENa = O::k(p[4]);
     c.EK = O::k(p[5]);
     c.EL = O::k(p[6]);
-    c.gsyn = O::k(p[7]);
+    c.gsynC = O::k(__fmul_rn(p[7], invC));
     c.Esyn = O::k(p[8]);
-    c.invC = O::k(__fdividef(1.0f, p[0]));
     c.inv_tr = O::k(__fdividef(1.0f, p[12]));
     c.neg_inv_td = O::k(-__fdividef(1.0f, p[13]));
     const float sig2 = p[14] * kLog2e;
@@ -263,10 +265,10 @@ __device__ __forceinline__ typename O::T bernoulli_series_t(typename O::T y) {
 __device__ __forceinline__ float bernoulli_series(float y) { return bernoulli_series_t<HHScalar>(y); }
 
 // Derivatives of one neuron: V, m, h, n, s its state, `others` the sum of the
-// other neurons' s, `drive` its injected current.
+// other neurons' s, `driveC` its injected current divided by C (hh_drive_c).
 template <class O>
 __device__ __forceinline__ void hh_neuron(typename O::T V, typename O::T m, typename O::T h, typename O::T n,
-                                          typename O::T s, typename O::T others, typename O::T drive,
+                                          typename O::T s, typename O::T others, typename O::T driveC,
                                           const HHConst<O>& c, typename O::T (&d)[5]) {
     using T = typename O::T;
     constexpr float kE25 = 12.182493960703473f;  // e^2.5
@@ -289,26 +291,33 @@ __device__ __forceinline__ void hh_neuron(typename O::T V, typename O::T m, type
     const T dm = O::sel(sm, one, O::fma(O::k(-kE25), q8, one));
     const T dn = O::sel(sn, one, O::fma(O::k(-kE1), q8, one));
     const T rmn = O::rcp(O::mul(dm, dn));
-    const T am = O::sel(sm, bernoulli_series_t<O>(ym), O::mul(O::mul(ym, dn), rmn));
-    const T an = O::mul(O::k(0.1f), O::sel(sn, bernoulli_series_t<O>(yn), O::mul(O::mul(yn, dm), rmn)));
+    // yn - ym = 1.5, so at most one of the two lies in the series band: one series serves both
+    const T ser = bernoulli_series_t<O>(O::sel(sm, ym, yn));
+    const T am = O::sel(sm, ser, O::mul(O::mul(ym, dn), rmn));
+    const T an = O::mul(O::k(0.1f), O::sel(sn, ser, O::mul(O::mul(yn, dm), rmn)));
     // beta_h = 1 / (1 + e^3 q^8), act = 1 / (1 + es)
     const T ph = O::fma(O::k(kE3), q8, one), ps = O::add(one, es);
     const T r = O::rcp(O::mul(ph, ps));
     const T act = O::mul(ph, r);  // beta_h = ps r enters only the h gate, fused there
     const T m3h = O::mul(O::mul(O::mul(m, m), m), h);
     const T n2 = O::mul(n, n), n4 = O::mul(n2, n2);
-    T I = O::mul(c.gL, O::sub(c.EL, V));
-    I = O::fma(O::mul(c.gNa, m3h), O::sub(c.ENa, V), I);
-    I = O::fma(O::mul(c.gK, n4), O::sub(c.EK, V), I);
-    I = O::fma(O::mul(c.gsyn, others), O::sub(c.Esyn, V), I);
-    I = O::add(I, drive);
-    d[0] = O::mul(I, c.invC);
+    // dV/dt = (I_i + sum of g (E - V)) / C with every term already divided by C
+    T u = O::fma(c.gLC, O::sub(c.EL, V), driveC);
+    u = O::fma(O::mul(c.gNaC, m3h), O::sub(c.ENa, V), u);
+    u = O::fma(O::mul(c.gKC, n4), O::sub(c.EK, V), u);
+    u = O::fma(O::mul(c.gsynC, others), O::sub(c.Esyn, V), u);
+    d[0] = u;
     // gates: a (1 - y) - b y = a - (a + b) y, with one rounding on both lane types (the
     // toolchain would fuse the f32x2 form of an unfused product and difference anyway)
     d[1] = O::fms(O::add(am, bm), m, am);
     d[2] = O::fms(O::fma(ps, r, ah), h, ah);  // ah + bh with bh = ps r, fused likewise
     d[3] = O::fms(O::add(an, bn), n, an);
     d[4] = O::fma(O::mul(act, c.inv_tr), O::sub(one, s), O::mul(s, c.neg_inv_td));
+}
+
+// Neuron i's drive I_i / C, formed the same way on every path (one rounding).
+__device__ __forceinline__ float hh_drive_c(const float* p, int i) {
+    return __fmul_rn(p[9 + i], __fdividef(1.0f, p[0]));
 }
 
 struct HH3 {
@@ -323,7 +332,7 @@ struct HH3 {
         for (int i = 0; i < 3; ++i) {
             float d[5];
             hh_neuron<HHScalar>(x[5 * i], x[5 * i + 1], x[5 * i + 2], x[5 * i + 3], x[5 * i + 4],
-                                __fsub_rn(s_sum, x[5 * i + 4]), p[9 + i], c, d);
+                                __fsub_rn(s_sum, x[5 * i + 4]), hh_drive_c(p, i), c, d);
 #pragma unroll
             for (int k = 0; k < 5; ++k) dx[5 * i + k] = d[k];
         }
@@ -1209,7 +1218,8 @@ struct HH3RK4Packed {
     __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
         const HHConst<HHPair> c2 = hh_const<HHPair>(p);
         const HHConst<HHScalar> c1 = hh_const<HHScalar>(p);
-        const f2 drive01 = pack2(p[9], p[10]);
+        const f2 drive01 = pack2(hh_drive_c(p, 0), hh_drive_c(p, 1));
+        const float drive2 = hh_drive_c(p, 2);
         f2 X[5], XS[5], A[5], K[5];
         float x2[5], xs2[5], a2[5], k2[5];
 #pragma unroll
@@ -1227,7 +1237,7 @@ struct HH3RK4Packed {
             unpack2(XS[4], s0, s1);
             const float s_sum = __fadd_rn(__fadd_rn(s0, s1), xs2[4]);
             hh_neuron<HHPair>(XS[0], XS[1], XS[2], XS[3], XS[4], sub2(pack2(s_sum, s_sum), XS[4]), drive01, c2, K);
-            hh_neuron<HHScalar>(xs2[0], xs2[1], xs2[2], xs2[3], xs2[4], __fsub_rn(s_sum, xs2[4]), p[11], c1, k2);
+            hh_neuron<HHScalar>(xs2[0], xs2[1], xs2[2], xs2[3], xs2[4], __fsub_rn(s_sum, xs2[4]), drive2, c1, k2);
             const float w = (st == 1 || st == 2) ? 2.0f : 1.0f;  // fmaf(1, k, 0) = k
             const f2 W = pack2(w, w);
 #pragma unroll
@@ -1271,15 +1281,14 @@ template <bool KAHAN> struct StepperFor<HH3, FF_RK4, KAHAN> { using type = HH3RK
 __device__ __forceinline__ HHConst<HHPair> hh_const_pair(const float* pa, const float* pb) {
     const HHConst<HHScalar> a = hh_const<HHScalar>(pa), b = hh_const<HHScalar>(pb);
     HHConst<HHPair> c;
-    c.gNa = pack2(a.gNa, b.gNa);
-    c.gK = pack2(a.gK, b.gK);
-    c.gL = pack2(a.gL, b.gL);
+    c.gNaC = pack2(a.gNaC, b.gNaC);
+    c.gKC = pack2(a.gKC, b.gKC);
+    c.gLC = pack2(a.gLC, b.gLC);
     c.ENa = pack2(a.ENa, b.ENa);
     c.EK = pack2(a.EK, b.EK);
     c.EL = pack2(a.EL, b.EL);
-    c.gsyn = pack2(a.gsyn, b.gsyn);
+    c.gsynC = pack2(a.gsynC, b.gsynC);
     c.Esyn = pack2(a.Esyn, b.Esyn);
-    c.invC = pack2(a.invC, b.invC);
     c.inv_tr = pack2(a.inv_tr, b.inv_tr);
     c.neg_inv_td = pack2(a.neg_inv_td, b.neg_inv_td);
     c.neg_sig2 = pack2(a.neg_sig2, b.neg_sig2);
@@ -1318,7 +1327,7 @@ __device__ __forceinline__ void hh3_rk4_x2_item(const IntegrateArgs& a, int64_t 
     const HHConst<HHPair> c = hh_const_pair(pa, pb);
     f2 drive[3];
 #pragma unroll
-    for (int n = 0; n < 3; ++n) drive[n] = pack2(pa[9 + n], pb[9 + n]);
+    for (int n = 0; n < 3; ++n) drive[n] = pack2(hh_drive_c(pa, n), hh_drive_c(pb, n));
     // the stepper's constants, per lane: h, h/2, h/6
     const f2 H1 = pack2(hs[0], hs[1]);
     const f2 H2 = pack2(0.5f * hs[0], 0.5f * hs[1]);
@@ -1382,8 +1391,9 @@ __device__ __forceinline__ void hh3_f_packed(const float (&x)[15], const float* 
     float k2[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) X[k] = pack2(x[k], x[5 + k]);
-    hh_neuron<HHPair>(X[0], X[1], X[2], X[3], X[4], sub2(pack2(s_sum, s_sum), X[4]), pack2(p[9], p[10]), c2, K);
-    hh_neuron<HHScalar>(x[10], x[11], x[12], x[13], x[14], __fsub_rn(s_sum, x[14]), p[11], c1, k2);
+    hh_neuron<HHPair>(X[0], X[1], X[2], X[3], X[4], sub2(pack2(s_sum, s_sum), X[4]),
+                      pack2(hh_drive_c(p, 0), hh_drive_c(p, 1)), c2, K);
+    hh_neuron<HHScalar>(x[10], x[11], x[12], x[13], x[14], __fsub_rn(s_sum, x[14]), hh_drive_c(p, 2), c1, k2);
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         unpack2(K[k], dx[k], dx[5 + k]);

@@ -411,20 +411,19 @@ __device__ __forceinline__ void fwd_step(float (&x)[R::DIM], float h, const floa
         c.init(h, p);
         lorenz_shift_fwd(x, c);
         return;
-    }
-    const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
-    float k[D], xs[D], acc[D];
-    if constexpr (D > 8) {
-        // large systems: the forward integrator's own RK4 stepper (for HH3 the packed
-        // neuron pairs), so the recomputed states are the taped forward's, bit for bit
+    } else if constexpr (!std::is_same<typename StepperFor<R, FF_RK4, false>::type, GenericRK4<R>>::value) {
+        // the forward integrator's own RK4 stepper (HH3: the packed neuron pairs; Wilson-Cowan:
+        // the shortened stage chain), so the recomputed states are the taped forward's, bit for bit
         typename StepperFor<R, FF_RK4, false>::type st;
-        float sc[D];
+        float acc[D], sc[D];
         st.init(h, p);
         st.acc(x, acc, sc);
 #pragma unroll
         for (int i = 0; i < D; ++i) x[i] = fmaf(sc[i], acc[i], x[i]);
         return;
     }
+    const float h2 = 0.5f * h, h6 = h * (1.0f / 6.0f);
+    float k[D], xs[D], acc[D];
     R::f(x, p, k);
 #pragma unroll
     for (int i = 0; i < D; ++i) { acc[i] = k[i]; xs[i] = fmaf(h2, k[i], x[i]); }

@@ -513,7 +513,81 @@ struct LorenzRK4Shift {
     }
 };
 
+// RK4 on Wilson-Cowan with a shorter dependent chain between stages.  The
+// logistic's base-2 exponents are affine in the state, arg = A x + c, so at a
+// stage point P = x + c_s k they are arg(x) + c_s A k, and with k = (S - Q) / tau
+// (Q the point k was taken at, S its logistic values)
+//   arg(P) = [arg(x) - c_s A (Q / tau)] + c_s A (S / tau).
+// The bracket needs only Q and runs beside the exponentials, so from the
+// reciprocals to the next exponentials the chain is two FMAs instead of four
+// (k, the stage point, and the two FMAs of the exponent).  The stage points and
+// k themselves are formed as in the generic stepper for the weighted sum; the
+// exponents differ from the ones taken at those points by rounding only.
+struct WilsonCowanRK4 {
+    static constexpr int D = 2;
+    float h1, h2, h6;
+    float aE, bE, cE, aI, bI, cI;  // exponent of the E (I) logistic: aE E + bE I + cE (aI E + bI I + cI)
+    float iE, iI;                  // 1 / tau
+    float uE, vE, uI, vI;          // exponent change per unit of S: aE / tauE, bE / tauI, aI / tauE, bI / tauI
+    __device__ __forceinline__ void init(float h, const float* p) {
+        const float g2 = p[8] * kLog2e;
+        aE = -g2 * p[0];
+        bE = g2 * p[1];
+        cE = g2 * (p[9] - p[4]);
+        aI = -g2 * p[2];
+        bI = g2 * p[3];
+        cI = g2 * (p[9] - p[5]);
+        iE = __fdividef(1.0f, p[6]);
+        iI = __fdividef(1.0f, p[7]);
+        uE = aE * iE;
+        vE = bE * iI;
+        uI = aI * iE;
+        vI = bI * iI;
+        h1 = h;
+        h2 = 0.5f * h;
+        h6 = h * (1.0f / 6.0f);
+    }
+    __device__ __forceinline__ void to_internal(float (&)[D]) const {}
+    __device__ __forceinline__ void from_internal(float (&)[D]) const {}
+    __device__ __forceinline__ void acc(const float (&x)[D], float (&a)[D], float (&sc)[D]) const {
+        const float E = x[0], I = x[1];
+        // stage 1: the right-hand side at x
+        const float argE = fmaf(aE, E, fmaf(bE, I, cE)), argI = fmaf(aI, E, fmaf(bI, I, cI));
+        float SE = rcp_ftz(1.0f + ex2_ftz(argE)), SI = rcp_ftz(1.0f + ex2_ftz(argI));
+        float QE = E, QI = I;  // the point the current k is taken at
+        float kE = fmaf(SE, iE, -QE * iE), kI = fmaf(SI, iI, -QI * iI);
+        a[0] = kE;
+        a[1] = kI;
+#pragma unroll
+        for (int st = 2; st <= 4; ++st) {
+            const float c = (st == 4) ? h1 : h2;
+            // beside the chain: the stage point and the part of its exponents known from Q
+            const float PE = fmaf(c, kE, E), PI = fmaf(c, kI, I);
+            const float cuE = c * uE, cvE = c * vE, cuI = c * uI, cvI = c * vI;
+            const float qE = fmaf(-cuE, QE, fmaf(-cvE, QI, argE)), qI = fmaf(-cuI, QE, fmaf(-cvI, QI, argI));
+            // on the chain: two FMAs from the reciprocals to the exponents
+            const float eE = fmaf(cvE, SI, fmaf(cuE, SE, qE)), eI = fmaf(cvI, SI, fmaf(cuI, SE, qI));
+            SE = rcp_ftz(1.0f + ex2_ftz(eE));
+            SI = rcp_ftz(1.0f + ex2_ftz(eI));
+            QE = PE;
+            QI = PI;
+            kE = fmaf(SE, iE, -QE * iE);
+            kI = fmaf(SI, iI, -QI * iI);
+            if (st < 4) {
+                a[0] = fmaf(2.0f, kE, a[0]);
+                a[1] = fmaf(2.0f, kI, a[1]);
+            } else {
+                a[0] = a[0] + kE;
+                a[1] = a[1] + kI;
+            }
+        }
+        sc[0] = h6;
+        sc[1] = h6;
+    }
+};
+
 template <class R, int METHOD, bool KAHAN> struct StepperFor { using type = GenericRK4<R>; };
+template <bool KAHAN> struct StepperFor<WilsonCowan, FF_RK4, KAHAN> { using type = WilsonCowanRK4; };
 template <class R, bool KAHAN> struct StepperFor<R, FF_EULER, KAHAN> { using type = GenericEuler<R>; };
 // the compensated variant keeps z unshifted so that no rounding escapes the compensation
 template <> struct StepperFor<Lorenz, FF_RK4, true> { using type = LorenzRK4; };

@@ -8,7 +8,7 @@
 // then per sub-segment (in reverse) to put its <= M states in registers (shared
 // memory for the packed Lorenz sweep), which the reverse RK4 steps consume from
 // last to first.  The 15-dimensional system is recomputed once per chunk into a
-// per-thread scratch area in global memory instead (the staged sweep).  Parameter gradients are
+// per-thread scratch area in global memory instead (ff_adjoint_hh3.cu).  Parameter gradients are
 // summed per particle in FP32 within a chunk, added to FP64 per chunk, and
 // reduced over particles through per-block FP64 partials in fixed order.
 //

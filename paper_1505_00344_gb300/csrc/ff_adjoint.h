@@ -34,7 +34,7 @@ struct AdjointArgs {
     int n_groups;
     int max_chunk;           // steps of the longest chunk (the tape's checkpoint spacing)
     int64_t gstart[FF_MAX_GROUPS];
-    float* scratch;           // staged sweep (15-dimensional system): one chunk of states per thread
+    float* scratch;           // HH x 3 sweep: one chunk of states per thread (a neuron of two particles)
     int64_t scratch_threads;  // threads the scratch has room for (floats = threads * chunk steps * dim)
 };
 
@@ -54,21 +54,23 @@ struct BatchAdjointArgs {
     int n_tiles;
     int np_stride;           // doubles per partial row
     double* partial;         // n_tiles rows
-    float* scratch;          // staged sweep: one chunk of states per thread (as AdjointArgs)
+    float* scratch;          // HH x 3 sweep: one chunk of states per thread (as AdjointArgs)
     int64_t scratch_threads;
 };
 
 bool adjoint_supported(int rhs_id);
 int adjoint_sub_steps(int64_t checkpoint_every);  // M >= K up to 16, else M * M >= K (K at most 256)
 int64_t adjoint_partial_rows(int num_sms);
-// Threads of the staged sweep (the 15-dimensional system's adjoint, standalone or
-// batched): each needs a scratch area of (largest chunk) x dim floats; 0 for the
-// systems whose sweeps keep their states on chip.
+// Threads of the HH x 3 sweep (standalone or batched): each needs a scratch area of
+// (largest chunk) x dim floats (it uses two thirds of it); 0 for the systems whose
+// sweeps keep their states on chip.
 int64_t adjoint_scratch_threads(int rhs_id, int method, bool pp, int num_sms, bool batched);
 int64_t adjoint_scratch_threads_hh3(int method, bool pp, int num_sms, bool batched);
 cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const AdjointArgs& a, int num_sms,
                            cudaStream_t s, double* dL_dp_dev, int n_params_kernel);
-constexpr int kAdjTile = 128;  // particles per batched-adjoint tile = threads per block
+constexpr int kAdjTile = 128;    // particles per batched-adjoint tile = threads per block
+constexpr int kAdjTileHH3 = 80;  // HH x 3: 128 threads, three lanes per pair of particles (20 per warp)
+inline int adjoint_tile_particles(int rhs_id) { return rhs_id == FF_RHS_HH3 ? kAdjTileHH3 : kAdjTile; }
 
 // Per-family launchers (ff_adjoint_lorenz.cu, ff_adjoint_hh3.cu, ff_adjoint_small.cu,
 // ff_adjoint_linear.cu): the sweep

@@ -8,10 +8,11 @@
 // checkpoint twice (once when L <= M): once to place sub-checkpoints every M
 // steps (local memory), then per sub-segment (in reverse) to put its <= M
 // states in registers (shared memory in the packed Lorenz sweep), which the
-// reverse RK4 steps consume from last to first.  The 15-dimensional system runs
-// the staged sweep instead: one recomputation per chunk into a global scratch.  Parameter gradients are summed
+// reverse RK4 steps consume from last to first.  Parameter gradients are summed
 // per particle in FP32 within a chunk, added to FP64 per chunk, and reduced
-// over particles through per-block FP64 partials in fixed order.
+// over particles through per-block FP64 partials in fixed order.  The
+// 15-dimensional system runs a sweep of its own (ff_adjoint_hh3.cu: three lanes
+// per particle pair, one recomputation per chunk into a global scratch).
 #pragma once
 
 #include <cstdint>
@@ -86,41 +87,6 @@ template <> struct Vjp<WilsonCowan> {
     }
 };
 
-// Parameter-derived constants of the HH3 vector-Jacobian product, per lane type.
-template <class O> struct HHVjpConst {
-    typename O::T gNa, gK, gL, ENa, EK, EL, gsyn, Esyn, invC, neg_invC, inv_tr, neg_inv_tr, neg_inv_td,
-        inv_td2, sig, neg_sig, neg_sig2, sig2_theta, theta, gNa3, gK4;
-};
-
-template <class O>
-__device__ __forceinline__ HHVjpConst<O> hh_vjp_const(const float* p) {
-    HHVjpConst<O> c;
-    const float invC = __fdividef(1.0f, p[0]), inv_tr = __fdividef(1.0f, p[12]), inv_td = __fdividef(1.0f, p[13]);
-    const float sig2 = p[14] * kLog2e;
-    c.gNa = O::k(p[1]);
-    c.gK = O::k(p[2]);
-    c.gL = O::k(p[3]);
-    c.ENa = O::k(p[4]);
-    c.EK = O::k(p[5]);
-    c.EL = O::k(p[6]);
-    c.gsyn = O::k(p[7]);
-    c.Esyn = O::k(p[8]);
-    c.invC = O::k(invC);
-    c.neg_invC = O::k(-invC);
-    c.inv_tr = O::k(inv_tr);
-    c.neg_inv_tr = O::k(-inv_tr);
-    c.neg_inv_td = O::k(-inv_td);
-    c.inv_td2 = O::k(inv_td * inv_td);
-    c.sig = O::k(p[14]);
-    c.neg_sig = O::k(-p[14]);
-    c.neg_sig2 = O::k(-sig2);
-    c.sig2_theta = O::k(sig2 * p[15]);
-    c.theta = O::k(p[15]);
-    c.gNa3 = O::k(3.0f * p[1]);
-    c.gK4 = O::k(4.0f * p[2]);
-    return c;
-}
-
 // d/dy of y / (1 - e^-y) by its series 1/2 + y/6 - y^3/180 + y^5/5040 - y^7/151200 (|y| < 0.5).
 template <class O>
 __device__ __forceinline__ typename O::T bernoulli_series_deriv_t(typename O::T y) {
@@ -128,147 +94,6 @@ __device__ __forceinline__ typename O::T bernoulli_series_deriv_t(typename O::T 
     return O::fma(y, O::fma(y2, O::fma(y2, O::fma(y2, O::k(-1.0f / 151200.0f), O::k(1.0f / 5040.0f)),
                                        O::k(-1.0f / 180.0f)), O::k(1.0f / 6.0f)), O::k(0.5f));
 }
-
-// One neuron of the HH3 vector-Jacobian product (Eq. 6-11 differentiated term by
-// term; the gate rates depend on V only), over a lane type.  With u = v_V / C:
-//   jx_V = sum over gates of v_y (a'(1 - y) - b' y) + v_s sig act (1 - act)(1 - s) / tau_r
-//          - u (gL + gNa m^3 h + gK n^4 + gsyn S)
-//   jx_y = (the current term's derivative) u - v_y (a + b)       for y = m, h, n
-//   self = -v_s (act / tau_r + 1 / tau_d)   (the own-s part of jx_s)
-//   syn  = gsyn (Esyn - V) u                 (added to the other neurons' jx_s)
-// and the neuron's contributions cp to dL/dp (indices 0..8, its drive, 12..15).
-template <class O>
-__device__ __forceinline__ void hh_neuron_vjp(typename O::T V, typename O::T m, typename O::T h, typename O::T n,
-                                              typename O::T s, typename O::T others, typename O::T drive,
-                                              typename O::T uV, typename O::T vm, typename O::T vh,
-                                              typename O::T vn, typename O::T vs, const HHVjpConst<O>& c,
-                                              typename O::T (&jx)[4], typename O::T& self, typename O::T& syn,
-                                              typename O::T (&cp)[14]) {
-    using T = typename O::T;
-    constexpr float kE25 = 12.182493960703473f;  // e^2.5
-    constexpr float kE1 = 2.718281828459045f;    // e^1
-    constexpr float kE3 = 20.085536923187668f;   // e^3
-    constexpr float kQ = -kLog2e / 80.0f, kQ0 = 65.0f * (-kLog2e / 80.0f);
-    constexpr float kB = -kLog2e / 18.0f, kB0 = 65.0f * (-kLog2e / 18.0f) + 2.0f;
-    const T one = O::k(1.0f);
-    // rates and their derivatives (the rates as in the forward right-hand side)
-    const T q = O::ex2(O::fma(V, O::k(kQ), O::k(kQ0)));
-    const T q2 = O::mul(q, q), q4 = O::mul(q2, q2), q8 = O::mul(q4, q4);
-    const T bm = O::ex2(O::fma(V, O::k(kB), O::k(kB0)));
-    const T ah = O::mul(O::k(0.07f), q4);
-    const T bn = O::mul(O::k(0.125f), q);
-    const T es = O::ex2(O::fma(c.neg_sig2, V, c.sig2_theta));
-    const T ym = O::fma(V, O::k(0.1f), O::k(4.0f)), yn = O::fma(V, O::k(0.1f), O::k(5.5f));
-    const auto sm = O::small(ym), sn = O::small(yn);
-    const T em = O::mul(O::k(kE25), q8), en = O::mul(O::k(kE1), q8);
-    const T dm = O::sel(sm, one, O::sub(one, em)), dn = O::sel(sn, one, O::sub(one, en));
-    const T rmn = O::rcp(O::mul(dm, dn));
-    const T rm = O::mul(dn, rmn), rn = O::mul(dm, rmn);  // 1 / dm, 1 / dn
-    // g(y) = y / (1 - e^-y), g'(y) = (1 - e^-y (1 + y)) / (1 - e^-y)^2; alpha_m = g(ym), alpha_n = g(yn) / 10
-    // at most one of ym, yn (which differ by 1.5) lies in the series band: one series and one
-    // derivative series serve both
-    const T ys = O::sel(sm, ym, yn);
-    const T ser = bernoulli_series_t<O>(ys), dser = bernoulli_series_deriv_t<O>(ys);
-    const T am = O::sel(sm, ser, O::mul(ym, rm));
-    const T gn = O::sel(sn, ser, O::mul(yn, rn));
-    const T dgm = O::sel(sm, dser, O::mul(O::fms(em, O::add(one, ym), one), O::mul(rm, rm)));
-    const T dgn = O::sel(sn, dser, O::mul(O::fms(en, O::add(one, yn), one), O::mul(rn, rn)));
-    const T anbn = O::fma(O::k(0.1f), gn, bn);  // alpha_n + beta_n (alpha_n = g(yn) / 10), fused
-    const T dam = O::mul(O::k(0.1f), dgm), dan = O::mul(O::k(0.01f), dgn);
-    const T ph = O::fma(O::k(kE3), q8, one), ps = O::add(one, es);
-    const T r = O::rcp(O::mul(ph, ps));
-    const T bh = O::mul(ps, r), act = O::mul(ph, r);
-    const T a1 = O::mul(act, O::sub(one, act));
-    // minus the beta derivatives: beta_m' = -beta_m/18, beta_n' = -beta_n/80, beta_h' = beta_h (1 - beta_h)/10
-    const T nd_bm = O::mul(bm, O::k(1.0f / 18.0f)), nd_bn = O::mul(bn, O::k(1.0f / 80.0f));
-    const T nd_bh = O::mul(O::mul(O::k(0.1f), bh), O::sub(bh, one));
-    const T dah = O::mul(ah, O::k(-1.0f / 20.0f));
-    // currents
-    const T m2 = O::mul(m, m), m3 = O::mul(m2, m), m3h = O::mul(m3, h);
-    const T n2 = O::mul(n, n), n3 = O::mul(n2, n), n4 = O::mul(n2, n2);
-    const T dNa = O::sub(c.ENa, V), dK = O::sub(c.EK, V), dL = O::sub(c.EL, V), dS = O::sub(c.Esyn, V);
-    T I = O::mul(c.gL, dL);
-    I = O::fma(O::mul(c.gNa, m3h), dNa, I);
-    I = O::fma(O::mul(c.gK, n4), dK, I);
-    I = O::fma(O::mul(c.gsyn, others), dS, I);
-    I = O::add(I, drive);
-    const T gtot = O::fma(c.gsyn, others, O::fma(c.gK, n4, O::fma(c.gNa, m3h, c.gL)));
-    // state
-    const T sv = O::mul(O::mul(vs, c.inv_tr), O::sub(one, s));  // v_s (1 - s) / tau_r
-    const T gate_m = O::fma(dam, O::sub(one, m), O::mul(nd_bm, m));
-    const T gate_h = O::fma(dah, O::sub(one, h), O::mul(nd_bh, h));
-    const T gate_n = O::fma(dan, O::sub(one, n), O::mul(nd_bn, n));
-    const T jv = O::fma(vm, gate_m, O::fma(vh, gate_h, O::fma(vn, gate_n, O::mul(O::mul(c.sig, a1), sv))));
-    // x - u w with one rounding (O::fms)
-    jx[0] = O::fms(uV, gtot, jv);
-    jx[1] = O::fms(vm, O::add(am, bm), O::mul(O::mul(O::mul(O::mul(uV, c.gNa3), m2), h), dNa));
-    jx[2] = O::fms(vh, O::add(ah, bh), O::mul(O::mul(O::mul(uV, c.gNa), m3), dNa));
-    jx[3] = O::fms(vn, anbn, O::mul(O::mul(O::mul(uV, c.gK4), n3), dK));
-    self = O::mul(vs, O::fma(act, c.neg_inv_tr, c.neg_inv_td));
-    syn = O::mul(O::mul(c.gsyn, dS), uV);
-    // parameters: C, gNa, gK, gL, ENa, EK, EL, gsyn, Esyn, drive, tau_r, tau_d, sig, theta
-    cp[0] = O::mul(O::mul(I, c.neg_invC), uV);
-    cp[1] = O::mul(O::mul(m3h, dNa), uV);
-    cp[2] = O::mul(O::mul(n4, dK), uV);
-    cp[3] = O::mul(dL, uV);
-    cp[4] = O::mul(O::mul(c.gNa, m3h), uV);
-    cp[5] = O::mul(O::mul(c.gK, n4), uV);
-    cp[6] = O::mul(c.gL, uV);
-    cp[7] = O::mul(O::mul(dS, others), uV);
-    cp[8] = O::mul(O::mul(c.gsyn, others), uV);
-    cp[9] = uV;
-    cp[10] = O::mul(O::mul(act, c.neg_inv_tr), sv);
-    cp[11] = O::mul(O::mul(s, c.inv_td2), vs);
-    cp[12] = O::mul(O::mul(a1, O::sub(V, c.theta)), sv);
-    cp[13] = O::mul(O::mul(c.neg_sig, a1), sv);
-}
-
-template <> struct Vjp<HH3> {
-    // Neurons 0 and 1 run the neuron product above packed in f32x2 registers,
-    // neuron 2 on floats, with the same operations.  The gate rows of jx can still
-    // round one way in f32x2 and another in floats (measured: about a quarter of
-    // random inputs, by one rounding), where the toolchain fuses a different pair
-    // of packed operations than the float form; every kernel runs this same code,
-    // so batched and standalone sweeps agree to the bit.
-    __device__ __forceinline__ static void apply(const float (&x)[15], const float* p, const float (&v)[15],
-                                                 float (&jx)[15], float* jp) {
-        const HHVjpConst<HHPair> c2 = hh_vjp_const<HHPair>(p);
-        const HHVjpConst<HHScalar> c1 = hh_vjp_const<HHScalar>(p);
-        const float s_sum = __fadd_rn(__fadd_rn(x[4], x[9]), x[14]);
-        const f2 S01 = pack2(x[4], x[9]);
-        const f2 uV01 = mul2(pack2(v[0], v[5]), c2.invC);
-        f2 jx01[4], self01, syn01, cp01[14];
-        hh_neuron_vjp<HHPair>(pack2(x[0], x[5]), pack2(x[1], x[6]), pack2(x[2], x[7]), pack2(x[3], x[8]), S01,
-                              sub2(pack2(s_sum, s_sum), S01), pack2(p[9], p[10]), uV01, pack2(v[1], v[6]),
-                              pack2(v[2], v[7]), pack2(v[3], v[8]), pack2(v[4], v[9]), c2, jx01, self01, syn01, cp01);
-        float jx2[4], self2, syn2, cp2[14];
-        hh_neuron_vjp<HHScalar>(x[10], x[11], x[12], x[13], x[14], __fsub_rn(s_sum, x[14]), p[11],
-                                __fmul_rn(v[10], c1.invC), v[11], v[12], v[13], v[14], c1, jx2, self2, syn2, cp2);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            unpack2(jx01[k], jx[k], jx[5 + k]);
-            jx[10 + k] = jx2[k];
-        }
-        float self0, self1, syn0, syn1;
-        unpack2(self01, self0, self1);
-        unpack2(syn01, syn0, syn1);
-        const float syn_sum = __fadd_rn(__fadd_rn(syn0, syn1), syn2);
-        jx[4] = __fadd_rn(self0, __fsub_rn(syn_sum, syn0));
-        jx[9] = __fadd_rn(self1, __fsub_rn(syn_sum, syn1));
-        jx[14] = __fadd_rn(self2, __fsub_rn(syn_sum, syn2));
-        // parameter contributions: neuron 0 + neuron 1 + neuron 2 (drives: one each)
-        float a0[14], a1[14];
-#pragma unroll
-        for (int k = 0; k < 14; ++k) unpack2(cp01[k], a0[k], a1[k]);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) jp[k] = __fadd_rn(jp[k], __fadd_rn(__fadd_rn(a0[k], a1[k]), cp2[k]));
-        jp[9] = __fadd_rn(jp[9], a0[9]);
-        jp[10] = __fadd_rn(jp[10], a1[9]);
-        jp[11] = __fadd_rn(jp[11], cp2[9]);
-#pragma unroll
-        for (int k = 10; k < 14; ++k) jp[k + 2] = __fadd_rn(jp[k + 2], __fadd_rn(__fadd_rn(a0[k], a1[k]), cp2[k]));
-    }
-};
 
 template <> struct Vjp<Linear> {
     // f = A x (A padded to 8x8 row-major)
@@ -466,7 +291,7 @@ __device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[
         return;
     }
     const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
-    static_assert(METHOD == FF_EULER || D <= 8, "the 15-dimensional system's reverse RK4 step is adj_step_staged");
+    static_assert(METHOD == FF_EULER || D <= 8, "the 15-dimensional system has a sweep of its own (ff_adjoint_hh3.cu)");
     float k[D], x2[D], x3[D], x4[D];
     R::f(x, p, k);
 #pragma unroll
@@ -496,7 +321,7 @@ __device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[
 
 // Reverse sweep of one particle i over all chunks: lambda from lam_in to
 // lam_out, parameter contributions added to gacc (FP64, per chunk).  For systems
-// of up to 8 dimensions (the 15-dimensional one runs adjoint_particle_staged).
+// of up to 8 dimensions (the 15-dimensional one has a sweep of its own).
 template <class R, int METHOD, bool PP, int M>
 __device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i, double (&gacc)[R::NP]) {
     constexpr int D = R::DIM, NP = R::NP;
@@ -602,255 +427,6 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ Ad
             if (lane == 0) a.partial[((int64_t)blockIdx.x * nwarps + warp) * a.np_stride + q] = v;
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// Staged sweep for the 15-dimensional system (HH x 3).  Its sub-segment states
-// do not fit in registers, so a chunk is recomputed once from its checkpoint
-// and every state goes to the thread's scratch area in global memory (state
-// variable k of step r at scratch[(r * D + k) * T], T the launch's threads: one
-// coalesced column per warp); the reverse steps read them back from last to
-// first.  The reverse step's three stage points live in shared memory, and the
-// kernels run 4 blocks of 128 threads per SM within the register file.  Against
-// the two-level scheme of adjoint_particle this saves one forward
-// recomputation per step; the states, steps and sums are the same, in the same
-// order, so the gradients agree with it to the bit.
-// ---------------------------------------------------------------------------
-constexpr int kStagedBlock = 128;
-constexpr int kStagedMinBlocks = 3;
-
-// adj_step with the step's state and its RK4 stage points in shared memory:
-// stage + (s * D + i) * bs holds component i of stage point s + 1 (x1 = x) for this
-// thread, and the parameter contributions accumulate in jp + q * bs (shared).
-template <class R, int METHOD>
-__device__ __forceinline__ void adj_step_staged(float (&xs)[R::DIM], float (&lam)[R::DIM], float h, const float* p,
-                                                float* jp, float* stage, int bs) {
-    constexpr int D = R::DIM, NP = R::NP;
-    float jr[NP];
-    if constexpr (METHOD == FF_EULER) {
-#pragma unroll
-        for (int q = 0; q < NP; ++q) jr[q] = jp[q * bs];
-        adj_step<R, METHOD>(xs, lam, h, p, jr);
-#pragma unroll
-        for (int q = 0; q < NP; ++q) jp[q * bs] = jr[q];
-    } else {
-        const float h2 = 0.5f * h, h3 = h * (1.0f / 3.0f), h6 = h * (1.0f / 6.0f);
-        float k[D], l[D], m[D], sum[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) stage[i * bs] = xs[i];
-#pragma unroll 1
-        for (int st = 0; st < 3; ++st) {
-            if constexpr (std::is_same<R, HH3>::value) hh3_f_packed(xs, p, k);  // the bits of HH3::f
-            else R::f(xs, p, k);
-            const float c = (st == 2) ? h : h2;
-#pragma unroll
-            for (int i = 0; i < D; ++i) {
-                xs[i] = fmaf(c, k[i], stage[i * bs]);
-                stage[((st + 1) * D + i) * bs] = xs[i];
-            }
-        }
-#pragma unroll 1
-        for (int st = 3; st >= 0; --st) {
-            if (st == 3) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) l[i] = h6 * lam[i];
-            } else {
-                const float cl = (st == 0) ? h6 : h3, cm = (st == 2) ? h : h2;
-#pragma unroll
-                for (int i = 0; i < D; ++i) l[i] = fmaf(cl, lam[i], cm * m[i]);
-            }
-#pragma unroll
-            for (int i = 0; i < D; ++i) xs[i] = stage[(st * D + i) * bs];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) jr[q] = jp[q * bs];
-            Vjp<R>::apply(xs, p, l, m, jr);
-#pragma unroll
-            for (int q = 0; q < NP; ++q) jp[q * bs] = jr[q];
-            if (st == 3) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) sum[i] = m[i];
-            } else if (st > 0) {
-#pragma unroll
-                for (int i = 0; i < D; ++i) sum[i] = __fadd_rn(sum[i], m[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < D; ++i) lam[i] = __fadd_rn(lam[i], __fadd_rn(sum[i], m[i]));
-    }
-}
-
-// Reverse sweep of particle i with the chunk's states in the thread's scratch
-// (scr = the thread's first float, T = floats between consecutive entries); stage
-// and jp are the thread's shared-memory columns (stride bs).
-template <class R, int METHOD, bool PP>
-__device__ __forceinline__ void adjoint_particle_staged(const AdjointArgs& a, int64_t i, double (&gacc)[R::NP],
-                                                        float* scr, int64_t T, float* stage, float* jp, int bs) {
-    constexpr int D = R::DIM, NP = R::NP;
-    int g = 0;
-#pragma unroll
-    for (int q = 1; q < FF_MAX_GROUPS; ++q)
-        if (q < a.n_groups && i >= a.gstart[q]) g = q;
-    float lam[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) lam[k] = (k < a.dim) ? a.lam_in[k * a.n + i] : 0.0f;
-    const float pv = PP ? a.pparam[i] : 0.0f;
-    for (int c = a.n_chunks - 1; c >= 0; --c) {
-        const AdjChunk& ch = a.chunks[c];
-        // the chunk's parameters: read from the chunk table where they are the same for every
-        // particle (the compiler may load them again where needed instead of holding them)
-        float pl[PP ? NP : 1];
-        if constexpr (PP) {
-#pragma unroll
-            for (int q = 0; q < NP; ++q) pl[q] = (q == a.pidx) ? pv : ch.p[q];
-        }
-        const float* p = PP ? pl : ch.p;
-        const float h = ch.gh[g];
-        const int L = ch.n_steps;
-        const float* ck = a.ckpt + (int64_t)ch.ckpt * a.dim * a.pitch;
-        float x[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) x[k] = (k < a.dim) ? ck[k * a.pitch + i] : 0.0f;
-#pragma unroll 1
-        for (int r = 0; r < L; ++r) {
-#pragma unroll
-            for (int k = 0; k < D; ++k) scr[((int64_t)r * D + k) * T] = x[k];
-            if (r + 1 < L) fwd_step<R, METHOD>(x, h, p);
-        }
-#pragma unroll
-        for (int q = 0; q < NP; ++q) jp[q * bs] = 0.0f;
-#pragma unroll 1
-        for (int r = L - 1; r >= 0; --r) {
-#pragma unroll
-            for (int k = 0; k < D; ++k) x[k] = scr[((int64_t)r * D + k) * T];
-            adj_step_staged<R, METHOD>(x, lam, h, p, jp, stage, bs);
-        }
-#pragma unroll
-        for (int q = 0; q < NP; ++q) gacc[q] += (double)jp[q * bs];
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k)
-        if (k < a.dim) a.lam_out[k * a.n + i] = lam[k];
-}
-
-template <class R, int METHOD, bool PP>
-__global__ void __launch_bounds__(kStagedBlock, kStagedMinBlocks) adjoint_staged_kernel(
-    const __grid_constant__ AdjointArgs a) {
-    constexpr int NP = R::NP, D = R::DIM;
-    __shared__ double red[kStagedBlock / 32][NP];
-    __shared__ float stage[4 * D * kStagedBlock];
-    __shared__ float jp[NP * kStagedBlock];
-    double gacc[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) gacc[q] = 0.0;
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int64_t i = t; i < a.n; i += T)
-        adjoint_particle_staged<R, METHOD, PP>(a, i, gacc, a.scratch + t, T, stage + threadIdx.x, jp + threadIdx.x,
-                                               blockDim.x);
-    block_sum_to_row<NP, kStagedBlock / 32>(gacc, red, a.partial + (int64_t)blockIdx.x * a.np_stride);
-}
-
-// Batched form: tiles of one member's particles, one per thread, round-robin over the blocks.
-template <class R, int METHOD, bool PP>
-__global__ void __launch_bounds__(kAdjTile, kStagedMinBlocks) batch_adjoint_staged_kernel(
-    const __grid_constant__ BatchAdjointArgs b) {
-    constexpr int NP = R::NP, D = R::DIM;
-    static_assert(kAdjTile == kStagedBlock, "one tile per block");
-    __shared__ double red[kAdjTile / 32][NP];
-    __shared__ float stage[4 * D * kAdjTile];
-    __shared__ float jp[NP * kAdjTile];
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
-        const AdjTile tl = b.tiles[tile];
-        const AdjointArgs& a = b.sys[tl.sys];
-        double gacc[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) gacc[q] = 0.0;
-        const int64_t i = tl.first + threadIdx.x;
-        if (i < tl.first + tl.count)
-            adjoint_particle_staged<R, METHOD, PP>(a, i, gacc, b.scratch + t, T, stage + threadIdx.x,
-                                                   jp + threadIdx.x, blockDim.x);
-        block_sum_to_row<NP, kAdjTile / 32>(gacc, red, b.partial + (int64_t)tile * b.np_stride);
-    }
-}
-
-// Resident threads of a staged kernel: the most it launches, and the scratch it needs room for.
-template <class Kernel>
-static int64_t staged_threads(Kernel kernel, int num_sms) {
-    int occ = 0;
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kStagedBlock, 0) != cudaSuccess || occ < 1)
-        return 0;
-    return (int64_t)occ * num_sms * kStagedBlock;
-}
-
-template <class R, bool BATCHED>
-static int64_t staged_threads_for(int method, bool pp, int num_sms) {
-    if constexpr (BATCHED) {
-        if (method == FF_RK4)
-            return pp ? staged_threads(batch_adjoint_staged_kernel<R, FF_RK4, true>, num_sms)
-                      : staged_threads(batch_adjoint_staged_kernel<R, FF_RK4, false>, num_sms);
-        return pp ? staged_threads(batch_adjoint_staged_kernel<R, FF_EULER, true>, num_sms)
-                  : staged_threads(batch_adjoint_staged_kernel<R, FF_EULER, false>, num_sms);
-    } else {
-        if (method == FF_RK4)
-            return pp ? staged_threads(adjoint_staged_kernel<R, FF_RK4, true>, num_sms)
-                      : staged_threads(adjoint_staged_kernel<R, FF_RK4, false>, num_sms);
-        return pp ? staged_threads(adjoint_staged_kernel<R, FF_EULER, true>, num_sms)
-                  : staged_threads(adjoint_staged_kernel<R, FF_EULER, false>, num_sms);
-    }
-}
-
-template <class R, int METHOD, bool PP>
-static cudaError_t launch_staged_one(const AdjointArgs& a, int num_sms, cudaStream_t s, int64_t* rows) {
-    auto kernel = adjoint_staged_kernel<R, METHOD, PP>;
-    const int64_t resident = staged_threads(kernel, num_sms);
-    if (resident < kStagedBlock) return cudaErrorInvalidConfiguration;
-    int64_t cap = resident / kStagedBlock;
-    if (cap > a.scratch_threads / kStagedBlock) cap = a.scratch_threads / kStagedBlock;  // room in the scratch
-    if (cap > 8 * a.max_blocks) cap = 8 * a.max_blocks;  // rows of the partial-sum buffer (one per block here)
-    const int64_t need = (a.n + kStagedBlock - 1) / kStagedBlock;
-    const int grid = (int)(need < cap ? need : cap);
-    if (grid < 1 || !a.scratch) return cudaErrorInvalidConfiguration;
-    kernel<<<grid, kStagedBlock, 0, s>>>(a);
-    *rows = grid;
-    return cudaGetLastError();
-}
-
-template <class R>
-static cudaError_t launch_staged(int method, bool pp, const AdjointArgs& a, int num_sms, cudaStream_t s,
-                                 int64_t* rows) {
-    if (method == FF_RK4)
-        return pp ? launch_staged_one<R, FF_RK4, true>(a, num_sms, s, rows)
-                  : launch_staged_one<R, FF_RK4, false>(a, num_sms, s, rows);
-    return pp ? launch_staged_one<R, FF_EULER, true>(a, num_sms, s, rows)
-              : launch_staged_one<R, FF_EULER, false>(a, num_sms, s, rows);
-}
-
-template <class R, int METHOD, bool PP>
-static cudaError_t launch_batch_staged_one(const BatchAdjointArgs& b, int num_sms, cudaStream_t s) {
-    auto kernel = batch_adjoint_staged_kernel<R, METHOD, PP>;
-    const int64_t resident = staged_threads(kernel, num_sms);
-    if (resident < kAdjTile) return cudaErrorInvalidConfiguration;
-    int64_t cap = resident / kAdjTile;
-    if (cap > b.scratch_threads / kAdjTile) cap = b.scratch_threads / kAdjTile;
-    const int grid = (int)((int64_t)b.n_tiles < cap ? b.n_tiles : cap);
-    if (grid < 1) return cudaSuccess;
-    if (!b.scratch) return cudaErrorInvalidConfiguration;
-    kernel<<<grid, kAdjTile, 0, s>>>(b);
-    return cudaGetLastError();
-}
-
-template <class R>
-static cudaError_t launch_batch_staged(int method, bool pp, const BatchAdjointArgs& b, int num_sms, cudaStream_t s) {
-    if (method == FF_RK4)
-        return pp ? launch_batch_staged_one<R, FF_RK4, true>(b, num_sms, s)
-                  : launch_batch_staged_one<R, FF_RK4, false>(b, num_sms, s);
-    return pp ? launch_batch_staged_one<R, FF_EULER, true>(b, num_sms, s)
-              : launch_batch_staged_one<R, FF_EULER, false>(b, num_sms, s);
 }
 
 // ---------------------------------------------------------------------------

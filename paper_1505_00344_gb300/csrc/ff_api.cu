@@ -692,7 +692,7 @@ ff_status ff_backward(ff_system* s, const float* dL_dxT_dev, float* dL_dx0_dev, 
     a.n_groups = s->n_groups;
     a.max_chunk = (int)s->tape_every;
     for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
-    // the staged sweep (HH x 3) keeps a chunk of states per thread in a scratch area,
+    // the HH x 3 sweep keeps a chunk of states per thread in a scratch area,
     // allocated on first use and kept with the tape
     const int64_t scratch_threads =
         ff::adjoint_scratch_threads(s->rhs_id, s->method, s->pparam_index >= 0, s->num_sms, false);

@@ -147,7 +147,7 @@ struct ff_batch {
         double* d_partial = nullptr;
         double* d_dp = nullptr;
         size_t adj_tiles_cap = 0;
-        float* d_adj_scratch = nullptr;  // staged sweep (HH x 3): one chunk of states per thread
+        float* d_adj_scratch = nullptr;  // HH x 3 adjoint sweep: one chunk of states per thread
         size_t adj_scratch_floats = 0;
     };
     int device = 0, num_sms = 1;
@@ -525,11 +525,12 @@ ff_status ff_batch_backward(ff_batch* b, const float* const* dL_dxT_dev, float* 
             a.max_chunk = (int)s->tape_every;
             for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
             f.row0[m] = (int)f.adj_tiles.size();
-            for (int64_t first = 0; first < s->n_particles; first += ff::kAdjTile) {
+            const int tile = ff::adjoint_tile_particles(f.rhs_id);
+            for (int64_t first = 0; first < s->n_particles; first += tile) {
                 ff::AdjTile t{};
                 t.sys = m;
                 t.first = first;
-                t.count = s->n_particles - first < ff::kAdjTile ? s->n_particles - first : ff::kAdjTile;
+                t.count = s->n_particles - first < tile ? s->n_particles - first : tile;
                 f.adj_tiles.push_back(t);
             }
         }

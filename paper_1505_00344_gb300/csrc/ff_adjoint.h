@@ -34,8 +34,8 @@ struct AdjointArgs {
     int n_groups;
     int max_chunk;           // steps of the longest chunk (the tape's checkpoint spacing)
     int64_t gstart[FF_MAX_GROUPS];
-    float* scratch;           // HH x 3 sweep: one chunk of states per thread (a neuron of two particles)
-    int64_t scratch_threads;  // threads the scratch has room for (floats = threads * chunk steps * dim)
+    float* scratch;           // HH x 3 sweep: one chunk of stage points per thread (a neuron of two particles)
+    int64_t scratch_threads;  // threads the scratch has room for (see adjoint_scratch_floats_per_step)
 };
 
 // Batched adjoint: work tiles of consecutive particles of one member (one
@@ -54,7 +54,7 @@ struct BatchAdjointArgs {
     int n_tiles;
     int np_stride;           // doubles per partial row
     double* partial;         // n_tiles rows
-    float* scratch;          // HH x 3 sweep: one chunk of states per thread (as AdjointArgs)
+    float* scratch;          // HH x 3 sweep: one chunk of stage points per thread (as AdjointArgs)
     int64_t scratch_threads;
 };
 
@@ -62,12 +62,17 @@ bool adjoint_supported(int rhs_id);
 int adjoint_sub_steps(int64_t checkpoint_every);  // M >= K up to 16, else M * M >= K (K at most 256)
 int64_t adjoint_partial_rows(int num_sms);
 // Threads of the HH x 3 sweep (standalone or batched): each needs a scratch area of
-// (largest chunk) x dim floats (it uses two thirds of it); 0 for the systems whose
+// (largest chunk) x adjoint_scratch_floats_per_step floats; 0 for the systems whose
 // sweeps keep their states on chip.
 int64_t adjoint_scratch_threads(int rhs_id, int method, bool pp, int num_sms, bool batched);
 int64_t adjoint_scratch_threads_hh3(int method, bool pp, int num_sms, bool batched);
 cudaError_t launch_adjoint(int rhs_id, int method, bool pp, int m, const AdjointArgs& a, int num_sms,
                            cudaStream_t s, double* dL_dp_dev, int n_params_kernel);
+// Scratch floats per thread and step of the HH x 3 sweep (a thread holds one neuron of two
+// particles): RK4 keeps the four stage points (4 x 5 f32x2), Euler the state (5 f32x2).
+inline int adjoint_scratch_floats_per_step(int rhs_id, int method) {
+    return rhs_id == FF_RHS_HH3 ? (method == FF_RK4 ? 40 : 10) : 0;
+}
 constexpr int kAdjTile = 128;    // particles per batched-adjoint tile = threads per block
 constexpr int kAdjTileHH3 = 80;  // HH x 3: 128 threads, three lanes per pair of particles (20 per warp)
 inline int adjoint_tile_particles(int rhs_id) { return rhs_id == FF_RHS_HH3 ? kAdjTileHH3 : kAdjTile; }

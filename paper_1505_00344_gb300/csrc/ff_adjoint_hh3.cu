@@ -35,7 +35,7 @@ constexpr int kSplitBlockParticles = kSplitBlock / 32 * kWarpParticles;  // 80: 
 // 3 blocks per SM leave 168 registers a thread: no spill (at 4 blocks the 128-register
 // bound spilled, and keeping the parameter sums in shared memory instead cost more time)
 constexpr int kSplitMinBlocks = 3;
-constexpr int kStageSlots = 6;                                 // a stage point: 5 components, the triple's s sum
+constexpr int kStepPoints = 4 * 5;  // f32x2 entries of one RK4 step's stage points (4 points x 5 components)
 static_assert(kSplitBlockParticles == kAdjTileHH3, "one batched tile per block");
 
 __device__ __forceinline__ f2 mulp(f2 a, f2 b) { return mul2(a, b); }
@@ -54,6 +54,15 @@ __device__ __forceinline__ f2 triple_sum(f2 v, int src0) {
     const f2 a = lane_shfl(v, src0), b = lane_shfl(v, src0 + 1), c = lane_shfl(v, src0 + 2);
     return add2(add2(a, b), c);
 }
+
+// 8-byte asynchronous copy global -> shared (the issuing thread reads the copy after
+// cp_async_wait), and the group boundaries of such copies.
+__device__ __forceinline__ void cp_async8(unsigned long long* dst, const unsigned long long* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Per-lane constants of one chunk: the forward right-hand side's (hh_const per
 // particle, as the two-particle integrator forms them: conductances and drive
@@ -78,10 +87,15 @@ __device__ __forceinline__ void lane_consts(LaneC& L, const float* pa, const flo
     L.H6 = pack2(ha * (1.0f / 6.0f), hb * (1.0f / 6.0f));
 }
 
-// One forward step of the lane's neuron (RK4 or Euler): per lane of each register the
-// operations of the integrator's steppers, so the recomputed states are the taped ones.
+// One forward step of the lane's neuron (RK4 or Euler) from X, with its stage points
+// written to out (f32x2 entries T apart: point s, component k at out[(s * 5 + k) * T];
+// Euler: the state only).  Per lane of each register the operations of the
+// integrator's steppers, so the recomputed states and stage points are the taped
+// forward's.
 template <int METHOD>
-__device__ __forceinline__ void lane_fwd(f2 (&X)[5], const LaneC& L, int src0) {
+__device__ __forceinline__ void lane_fwd(f2 (&X)[5], const LaneC& L, int src0, unsigned long long* out, int64_t T) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) out[k * T] = X[k].v;
     if constexpr (METHOD == FF_EULER) {
         f2 K[5];
         hh_neuron<HHPair>(X[0], X[1], X[2], X[3], X[4], sub2(triple_sum(X[4], src0), X[4]), L.driveC, L.c, K);
@@ -106,7 +120,10 @@ __device__ __forceinline__ void lane_fwd(f2 (&X)[5], const LaneC& L, int src0) {
             if (st == 3) break;
             const f2 C = (st == 2) ? L.H1 : L.H2;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) XS[k] = fma2(C, K[k], X[k]);
+            for (int k = 0; k < 5; ++k) {
+                XS[k] = fma2(C, K[k], X[k]);
+                out[((st + 1) * 5 + k) * T] = XS[k].v;
+            }
         }
 #pragma unroll
         for (int k = 0; k < 5; ++k) X[k] = fma2(L.H6, A[k], X[k]);
@@ -230,71 +247,50 @@ __device__ __forceinline__ void lane_product(const f2 (&x)[5], f2 s_sum, const f
     out[4] = add2(self, sub2(triple_sum(syn, src0), syn));
 }
 
-// Reverse of one step of the lane's neuron at state X (RK4 with stages x1 = X,
-// x2 = X + h/2 k1, x3 = X + h/2 k2, x4 = X + h k3):
+// Reverse of one RK4 step of the lane's neuron, from its stage points x1 = x,
+// x2 = x + h/2 k1, x3 = x + h/2 k2, x4 = x + h k3 (pts: the lane's shared-memory
+// column, stride bs, point s and component k at pts[(s * 5 + k) * bs]):
 //   l4 = h/6 lam, l3 = h/3 lam + h m4, l2 = h/3 lam + h/2 m3, l1 = h/6 lam + h/2 m2
 //   with m_s = J(x_s)^T l_s, and lam <- lam + ((m4 + m3) + m2) + m1.
-// stage: the lane's shared-memory column (stride bs): stage point s at slots
-// [s * kStageSlots, s * kStageSlots + 5), the triple's s sum at it in the sixth.
-template <int METHOD>
-__device__ __forceinline__ void lane_adj(const f2 (&X)[5], f2 (&lam)[5], const LaneC& L, LaneAcc& acc,
-                                         unsigned long long* stage, int bs, int src0) {
-    if constexpr (METHOD == FF_EULER) {
-        f2 l[5], m[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) l[k] = mulp(L.H1, lam[k]);
-        lane_product(X, triple_sum(X[4], src0), l, L, m, acc, src0);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) lam[k] = add2(lam[k], m[k]);
-    } else {
-        f2 XS[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            XS[k] = X[k];
-            stage[k * bs] = X[k].v;
-        }
+__device__ __forceinline__ void lane_adj_rk4(const unsigned long long* pts, int bs, f2 (&lam)[5], const LaneC& L,
+                                             LaneAcc& acc, int src0) {
+    const f2 H3 = mulp(L.H1, kp(1.0f / 3.0f));
+    f2 l[5], m[5], sum[5];
 #pragma unroll 1
-        for (int st = 0; st < 3; ++st) {
-            const f2 s_sum = triple_sum(XS[4], src0);
-            stage[(st * kStageSlots + 5) * bs] = s_sum.v;
-            f2 K[5];
-            hh_neuron<HHPair>(XS[0], XS[1], XS[2], XS[3], XS[4], sub2(s_sum, XS[4]), L.driveC, L.c, K);
-            const f2 C = (st == 2) ? L.H1 : L.H2;
+    for (int st = 3; st >= 0; --st) {
+        if (st == 3) {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                XS[k] = fma2(C, K[k], X[k]);
-                stage[((st + 1) * kStageSlots + k) * bs] = XS[k].v;
-            }
+            for (int k = 0; k < 5; ++k) l[k] = mulp(L.H6, lam[k]);
+        } else {
+            const f2 CL = (st == 0) ? L.H6 : H3, CM = (st == 2) ? L.H1 : L.H2;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) l[k] = fma2(CL, lam[k], mulp(CM, m[k]));
         }
-        stage[(3 * kStageSlots + 5) * bs] = triple_sum(XS[4], src0).v;
-        const f2 H3 = mulp(L.H1, kp(1.0f / 3.0f));
-        f2 l[5], m[5], sum[5];
-#pragma unroll 1
-        for (int st = 3; st >= 0; --st) {
-            if (st == 3) {
+        f2 xs[5];
 #pragma unroll
-                for (int k = 0; k < 5; ++k) l[k] = mulp(L.H6, lam[k]);
-            } else {
-                const f2 CL = (st == 0) ? L.H6 : H3, CM = (st == 2) ? L.H1 : L.H2;
+        for (int k = 0; k < 5; ++k) xs[k].v = pts[(st * 5 + k) * bs];
+        lane_product(xs, triple_sum(xs[4], src0), l, L, m, acc, src0);
+        if (st == 3) {
 #pragma unroll
-                for (int k = 0; k < 5; ++k) l[k] = fma2(CL, lam[k], mulp(CM, m[k]));
-            }
-            f2 xs[5], s_sum;
+            for (int k = 0; k < 5; ++k) sum[k] = m[k];
+        } else if (st > 0) {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) xs[k].v = stage[(st * kStageSlots + k) * bs];
-            s_sum.v = stage[(st * kStageSlots + 5) * bs];
-            lane_product(xs, s_sum, l, L, m, acc, src0);
-            if (st == 3) {
-#pragma unroll
-                for (int k = 0; k < 5; ++k) sum[k] = m[k];
-            } else if (st > 0) {
-#pragma unroll
-                for (int k = 0; k < 5; ++k) sum[k] = add2(sum[k], m[k]);
-            }
+            for (int k = 0; k < 5; ++k) sum[k] = add2(sum[k], m[k]);
         }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) lam[k] = add2(lam[k], add2(sum[k], m[k]));
     }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) lam[k] = add2(lam[k], add2(sum[k], m[k]));
+}
+
+// Reverse of one Euler step at state X: lam <- lam + J(X)^T (h lam).
+__device__ __forceinline__ void lane_adj_euler(const f2 (&X)[5], f2 (&lam)[5], const LaneC& L, LaneAcc& acc,
+                                               int src0) {
+    f2 l[5], m[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) l[k] = mulp(L.H1, lam[k]);
+    lane_product(X, triple_sum(X[4], src0), l, L, m, acc, src0);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) lam[k] = add2(lam[k], m[k]);
 }
 
 // The lane's parameter vector for particle i (the per-particle parameter in place).
@@ -349,6 +345,7 @@ template <int METHOD, bool PP>
 __device__ __forceinline__ void lane_sweep(const AdjointArgs& a, int64_t first, int64_t end,
                                            unsigned long long* scr, int64_t T, unsigned long long* stage,
                                            double* gacc, int bs) {
+    constexpr int kPer = (METHOD == FF_EULER) ? 5 : kStepPoints;  // scratch entries per step
     const int lane = threadIdx.x & 31;
     const int j = lane / 3, n = lane - 3 * j, src0 = 3 * j;
     const int64_t i0 = first + 2 * j, i1 = i0 + 1;
@@ -377,27 +374,44 @@ __device__ __forceinline__ void lane_sweep(const AdjointArgs& a, int64_t first, 
             const float* plane = ck + (int64_t)(5 * n + k) * a.pitch;
             X[k] = pack2(plane[c0], plane[c1]);
         }
+        // the chunk's recomputation: every step's stage points (Euler: states) to the scratch
 #pragma unroll 1
-        for (int r = 0; r < Ls; ++r) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k) scr[((int64_t)r * 5 + k) * T] = X[k].v;
-            if (r + 1 < Ls) lane_fwd<METHOD>(X, L, src0);
-        }
+        for (int r = 0; r < Ls; ++r) lane_fwd<METHOD>(X, L, src0, scr + (int64_t)r * kPer * T, T);
         LaneAcc acc;
         acc.zero();
-        // each step's state is loaded one step ahead, so the load's latency overlaps a step
-        f2 Xn[5];
+        if constexpr (METHOD == FF_EULER) {
+            // each step's state is loaded one step ahead, so the load's latency overlaps a step
+            f2 Xn[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) Xn[k].v = scr[((int64_t)(Ls - 1) * 5 + k) * T];
+            for (int k = 0; k < 5; ++k) Xn[k].v = scr[((int64_t)(Ls - 1) * 5 + k) * T];
 #pragma unroll 1
-        for (int r = Ls - 1; r >= 0; --r) {
+            for (int r = Ls - 1; r >= 0; --r) {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) X[k] = Xn[k];
-            if (r > 0) {
+                for (int k = 0; k < 5; ++k) X[k] = Xn[k];
+                if (r > 0) {
 #pragma unroll
-                for (int k = 0; k < 5; ++k) Xn[k].v = scr[((int64_t)(r - 1) * 5 + k) * T];
+                    for (int k = 0; k < 5; ++k) Xn[k].v = scr[((int64_t)(r - 1) * 5 + k) * T];
+                }
+                lane_adj_euler(X, lam, L, acc, src0);
             }
-            lane_adj<METHOD>(X, lam, L, acc, stage, bs, src0);
+        } else {
+            // a step's 20 stage-point entries are copied into one half of the lane's
+            // shared-memory column while the step after it (in reverse) runs on the other
+            auto fetch = [&](int r, int half) {
+                const unsigned long long* src = scr + (int64_t)r * kStepPoints * T;
+                unsigned long long* dst = stage + half * kStepPoints * bs;
+#pragma unroll
+                for (int q = 0; q < kStepPoints; ++q) cp_async8(dst + q * bs, src + q * T);
+                cp_async_commit();
+            };
+            fetch(Ls - 1, 0);
+#pragma unroll 1
+            for (int r = Ls - 1, half = 0; r >= 0; --r, half ^= 1) {
+                if (r > 0) fetch(r - 1, half ^ 1);
+                else cp_async_commit();  // an empty group: the wait below still leaves step r's copies done
+                cp_async_wait1();
+                lane_adj_rk4(stage + half * kStepPoints * bs, bs, lam, L, acc, src0);
+            }
         }
         float u[2], cur[2], na[2], na_e[2], kk[2], k_e[2], l[2], syn[2], syn_e[2], tr[2], td[2], sg[2], th[2];
         unpack2(acc.get(A_U), u[0], u[1]);
@@ -435,7 +449,7 @@ __device__ __forceinline__ void lane_sweep(const AdjointArgs& a, int64_t first, 
 
 // Shared memory of a block: the stage points and FP64 parameter sums of every lane.
 struct SplitShared {
-    unsigned long long stage[4 * kStageSlots * kSplitBlock];
+    unsigned long long stage[2 * kStepPoints * kSplitBlock];  // two steps' stage points per lane
     double gacc[HH3::NP * kSplitBlock];
     double red[kSplitBlock / 32][HH3::NP];
 };
@@ -514,8 +528,7 @@ cudaError_t launch_split(const AdjointArgs& a, int num_sms, cudaStream_t s, int6
     const int64_t resident = split_threads(kernel, num_sms);
     if (resident < kSplitBlock) return cudaErrorInvalidConfiguration;
     int64_t cap = resident / kSplitBlock;
-    // room in the scratch: each thread holds a chunk of 5 f32x2 (10 floats) per step, the
-    // allocation gives it 15 per step
+    // room in the scratch: adjoint_scratch_floats_per_step floats per thread and step
     if (cap > a.scratch_threads / kSplitBlock) cap = a.scratch_threads / kSplitBlock;
     if (cap > 8 * a.max_blocks) cap = 8 * a.max_blocks;  // rows of the partial-sum buffer (one per block)
     const int64_t need = (a.n + kSplitBlockParticles - 1) / kSplitBlockParticles;

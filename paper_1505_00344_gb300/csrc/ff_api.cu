@@ -692,12 +692,13 @@ ff_status ff_backward(ff_system* s, const float* dL_dxT_dev, float* dL_dx0_dev, 
     a.n_groups = s->n_groups;
     a.max_chunk = (int)s->tape_every;
     for (int g = 0; g < s->n_groups; ++g) a.gstart[g] = s->groups[g].start;
-    // the HH x 3 sweep keeps a chunk of states per thread in a scratch area,
+    // the HH x 3 sweep keeps a chunk of stage points per thread in a scratch area,
     // allocated on first use and kept with the tape
     const int64_t scratch_threads =
         ff::adjoint_scratch_threads(s->rhs_id, s->method, s->pparam_index >= 0, s->num_sms, false);
     if (scratch_threads > 0) {
-        const size_t need = (size_t)scratch_threads * (size_t)s->tape_every * (size_t)s->dim;
+        const size_t need = (size_t)scratch_threads * (size_t)s->tape_every *
+                            (size_t)ff::adjoint_scratch_floats_per_step(s->rhs_id, s->method);
         if (need > s->adj_scratch_floats) {
             cudaFree(s->d_adj_scratch);  // waits for any sweep still reading it
             s->d_adj_scratch = nullptr;

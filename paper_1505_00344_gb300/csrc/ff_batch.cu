@@ -147,7 +147,7 @@ struct ff_batch {
         double* d_partial = nullptr;
         double* d_dp = nullptr;
         size_t adj_tiles_cap = 0;
-        float* d_adj_scratch = nullptr;  // HH x 3 adjoint sweep: one chunk of states per thread
+        float* d_adj_scratch = nullptr;  // HH x 3 adjoint sweep: one chunk of stage points per thread
         size_t adj_scratch_floats = 0;
     };
     int device = 0, num_sms = 1;
@@ -568,7 +568,8 @@ ff_status ff_batch_backward(ff_batch* b, const float* const* dL_dxT_dev, float* 
                 const ff_system* s = b->systems[f.members[m]];
                 if (s->tape_every > longest) longest = s->tape_every;
             }
-            const size_t need = (size_t)scratch_threads * (size_t)longest * (size_t)s0->dim;
+            const size_t need = (size_t)scratch_threads * (size_t)longest *
+                                (size_t)ff::adjoint_scratch_floats_per_step(f.rhs_id, f.method);
             if (need > f.adj_scratch_floats) {
                 cudaFree(f.d_adj_scratch);  // waits for any sweep still reading it
                 f.d_adj_scratch = nullptr;

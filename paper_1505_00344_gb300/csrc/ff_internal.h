@@ -100,7 +100,7 @@ struct ff_system {
     ff::AdjChunk* d_chunks = nullptr;
     double* d_partial = nullptr;
     double* d_dp = nullptr;
-    float* d_adj_scratch = nullptr;  // HH x 3 adjoint sweep: one chunk of states per thread
+    float* d_adj_scratch = nullptr;  // HH x 3 adjoint sweep: one chunk of stage points per thread
     size_t adj_scratch_floats = 0;
     int64_t partial_blocks = 0;
     std::vector<ff::AdjChunk> chunks;

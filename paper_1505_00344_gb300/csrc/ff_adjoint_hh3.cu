@@ -15,10 +15,11 @@
 //
 // Sweep.  Per chunk (in reverse): the chunk is recomputed once from its
 // checkpoint with the integrator's own packed step (hh_neuron over f32x2, the bits
-// of the taped forward), every state going to the lane's scratch column in global
-// memory; then the reverse steps read them back from last to first.  A reverse RK4
-// step puts its stage points (and the triple sums of s at them) in shared memory
-// and applies the four vector-Jacobian products, hand-differentiated from Eq. 6-11.
+// of the taped forward), every RK4 step's four stage points (Euler: its state)
+// going to the lane's scratch column in global memory; then the reverse steps run
+// from last to first, each on stage points that cp.async copies brought into the
+// lane's shared-memory column while the step before ran, and apply the four
+// vector-Jacobian products, hand-differentiated from Eq. 6-11.
 // The parameter gradient is carried in thirteen FP32 sums per neuron and particle
 // over the chunk, from which the sixteen components are formed in FP64 at the
 // chunk's end (each a sum times a parameter constant); the FP64 sums are reduced

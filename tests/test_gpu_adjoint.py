@@ -121,6 +121,47 @@ def test_hh3_adjoint_through_spikes():
     assert worst <= 1.0, worst
 
 
+@pytest.mark.parametrize("pidx,lo,hi,method", [
+    (7, 0.0, 1.0, "rk4"),     # g_syn per particle: its FP64 scaling of the E_syn sums is per particle
+    (0, 0.8, 1.2, "rk4"),     # C per particle: every 1/C factor of the products and the sums
+    (9, 5.0, 15.0, "euler"),  # neuron 0's drive per particle
+])
+def test_hh3_adjoint_per_particle_parameter(pidx, lo, hi, method):
+    """The HH3 sweep with one parameter taken per particle (a linspace), against the
+    oracle's forward sensitivities with the same values; its dL/dp entry is the sum
+    over particles of the derivatives with respect to their own values."""
+    groups = [G(200, *HHB, 1, 61), G(57, *HHB, 1, 62)]
+    P, dt, n, K = 257, (0.01 if method == "rk4" else 0.005), 100, 50
+    s = build("hh3", HH3_BASE, groups, 15, method)
+    s.set_particle_param(pidx, lo, hi)
+    s.tape_begin(K, n)
+    s.step(n, dt)
+    target = random_states(15, P, HHB[0], HHB[1], seed=5).astype(np.float64)
+    dx0, dp = gpu_grads(s, 15, P, target, 16)
+    pv = oracle.linspace_param(P, lo, hi).astype(np.float64)
+    _, dx0_ref, dp_ref = oracle.mse_gradients(oracle.HH3, x0_of(groups, 15), HH3_BASE, dt, n, target,
+                                              pparam_index=pidx, pparam=pv,
+                                              method=oracle.RK4 if method == "rk4" else oracle.EULER)
+    check(dx0, dx0_ref)
+    check(dp, dp_ref)
+
+
+@pytest.mark.parametrize("P", [1, 3, 21])
+def test_hh3_adjoint_small_counts(P):
+    """Fewer particles than a warp's 20 (three lanes per particle pair), and one more:
+    lanes without a particle, a half-filled last pair and a second warp with one particle."""
+    groups = [G(P, *HHB, 1, 63)]
+    dt, n = 0.01, 40
+    s = build("hh3", HH3_BASE, groups, 15)
+    s.tape_begin(16, n)
+    s.step(n, dt)
+    target = random_states(15, P, HHB[0], HHB[1], seed=7).astype(np.float64)
+    dx0, dp = gpu_grads(s, 15, P, target, 16)
+    _, dx0_ref, dp_ref = oracle.mse_gradients(oracle.HH3, x0_of(groups, 15), HH3_BASE, dt, n, target)
+    check(dx0, dx0_ref)
+    check(dp, dp_ref)
+
+
 def test_adjoint_across_parameter_change_and_per_particle_r():
     # r per particle over [0, 40]; beta switched to 2 half-way: two taped segments
     groups = [G(1500, [-20, -20, 0], [20, 20, 40], 1, 71)]

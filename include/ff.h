@@ -474,14 +474,14 @@ ff_status ff_pipe_rate(int op, int device, double* lane_ops_per_s);
  *                 with the escape test of ff_stats (a component non-finite or
  *                 above 1e30 in magnitude).
  * The call synchronises the stream before returning, and it copies the
- * counts to pageable host memory: it cannot be called while its stream (or
- * the legacy default stream) is being captured into a CUDA graph, on any
- * call.  It calls no cudaMalloc or cudaFree: its only scratch is a fixed
- * device array of FF_NOALLOC_MAX_GROUPS counters in the library, present on
- * every GPU that loads the library until the process exits.  The first call
- * on each device looks up that array's device address (cudaGetSymbolAddress)
- * and keeps it for the process; after cudaDeviceReset on a device the kept
- * address is stale, so do not call this entry point on that device again.
+ * counts to pageable host memory.  It calls no cudaMalloc or cudaFree: its
+ * only scratch is a fixed device array of FF_NOALLOC_MAX_GROUPS counters in
+ * the library, present on every GPU that loads the library until the process
+ * exits.  The first call on each device does a one-time set-up: it looks up
+ * that array's device address (cudaGetSymbolAddress) and keeps it for the
+ * process, so make that first call on a device before any stream capture
+ * begins.  After cudaDeviceReset on a device the kept address is stale, so do
+ * not call this entry point on that device again.
  * All calls on a device share the array and each clears the counters it
  * uses: calls that overlap on the GPU (concurrent streams or threads) race
  * and give wrong counts.

@@ -391,12 +391,19 @@ __device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[
     for (int i = 0; i < D; ++i) lam[i] = __fadd_rn(lam[i], __fadd_rn(sum[i], m[i]));
 }
 
+// Whether a sweep keeps the sub-segment's M states in shared memory (one column per
+// thread, M * D floats: at most 32 KB for a block of 128) rather than in a register
+// array, which needs the step loops unrolled M times.
+template <class R, int M> struct StatesInShared { static constexpr bool value = M * R::DIM <= 64; };
+
 // Reverse sweep of one particle i over all chunks: lambda from lam_in to
 // lam_out, parameter contributions added to gacc (FP64, per chunk).  For systems
 // of up to 8 dimensions (the 15-dimensional one has a sweep of its own).
 template <class R, int METHOD, bool PP, int M>
-__device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i, double (&gacc)[R::NP]) {
+__device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i, double (&gacc)[R::NP],
+                                                 float* sts = nullptr, int bs = 0) {
     constexpr int D = R::DIM, NP = R::NP;
+    constexpr bool SM = StatesInShared<R, M>::value;
     int g = 0;
 #pragma unroll
     for (int q = 1; q < FF_MAX_GROUPS; ++q)
@@ -433,20 +440,39 @@ __device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i
         for (int q = 0; q < NP; ++q) jp[q] = 0.0f;
         for (int sq = nsub - 1; sq >= 0; --sq) {
             const int nq = min(M, L - sq * M);
-            float st[M][D];
 #pragma unroll
             for (int k = 0; k < D; ++k) x[k] = cp[sq][k];
+            if constexpr (SM) {
+                // the sub-segment's states in the thread's shared-memory column (state r,
+                // component k at sts[(r * D + k) * bs]): the step loops stay rolled, so the
+                // kernel keeps one copy of each step in the instruction cache
+#pragma unroll 1
+                for (int r = 0; r < nq; ++r) {
 #pragma unroll
-            for (int r = 0; r < M; ++r) {
-                if (r < nq) {
-#pragma unroll
-                    for (int k = 0; k < D; ++k) st[r][k] = x[k];
+                    for (int k = 0; k < D; ++k) sts[(r * D + k) * bs] = x[k];
                     if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
                 }
-            }
+#pragma unroll 1
+                for (int r = nq - 1; r >= 0; --r) {
+                    float xr[D];
 #pragma unroll
-            for (int r = M - 1; r >= 0; --r)
-                if (r < nq) adj_step<R, METHOD>(st[r], lam, h, p, jp);
+                    for (int k = 0; k < D; ++k) xr[k] = sts[(r * D + k) * bs];
+                    adj_step<R, METHOD>(xr, lam, h, p, jp);
+                }
+            } else {
+                float st[M][D];
+#pragma unroll
+                for (int r = 0; r < M; ++r) {
+                    if (r < nq) {
+#pragma unroll
+                        for (int k = 0; k < D; ++k) st[r][k] = x[k];
+                        if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
+                    }
+                }
+#pragma unroll
+                for (int r = M - 1; r >= 0; --r)
+                    if (r < nq) adj_step<R, METHOD>(st[r], lam, h, p, jp);
+            }
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q) gacc[q] += (double)jp[q];
@@ -481,12 +507,13 @@ template <class R, int METHOD, bool PP, int M>
 __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ AdjointArgs a) {
     constexpr int NP = R::NP;
     __shared__ double red[8][NP > 16 ? 1 : NP];  // per-warp partials (blocks of at most 256 threads)
+    extern __shared__ float sts[];               // StatesInShared: M * D floats per thread
     double gacc[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) gacc[q] = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
-        adjoint_particle<R, METHOD, PP, M>(a, i, gacc);
+        adjoint_particle<R, METHOD, PP, M>(a, i, gacc, sts + threadIdx.x, blockDim.x);
     // per-block partial sums of the parameter gradient, in a fixed order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     if constexpr (NP <= 16) {
@@ -879,6 +906,7 @@ template <class R, int METHOD, bool PP, int M>
 __global__ void __launch_bounds__(kAdjTile) batch_adjoint_kernel(const __grid_constant__ BatchAdjointArgs b) {
     constexpr int NP = R::NP;
     __shared__ double red[kAdjTile / 32][NP];
+    __shared__ float sts[StatesInShared<R, M>::value ? M * R::DIM * kAdjTile : 1];
     for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
         const AdjTile T = b.tiles[tile];
         const AdjointArgs& a = b.sys[T.sys];
@@ -886,7 +914,7 @@ __global__ void __launch_bounds__(kAdjTile) batch_adjoint_kernel(const __grid_co
 #pragma unroll
         for (int q = 0; q < NP; ++q) gacc[q] = 0.0;
         const int64_t i = T.first + threadIdx.x;
-        if (i < T.first + T.count) adjoint_particle<R, METHOD, PP, M>(a, i, gacc);
+        if (i < T.first + T.count) adjoint_particle<R, METHOD, PP, M>(a, i, gacc, sts + threadIdx.x, kAdjTile);
         block_sum_to_row<NP, kAdjTile / 32>(gacc, red, b.partial + (int64_t)tile * b.np_stride);
     }
 }
@@ -926,8 +954,9 @@ template <class R, int METHOD, bool PP, int M>
 static cudaError_t launch_one(const AdjointArgs& a0, int block, int num_sms, cudaStream_t s, int64_t* rows) {
     AdjointArgs a = a0;
     auto kernel = adjoint_kernel<R, METHOD, PP, M>;
+    const size_t smem = StatesInShared<R, M>::value ? sizeof(float) * M * R::DIM * block : 0;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int64_t need = (a.n + block - 1) / block;
@@ -935,7 +964,7 @@ static cudaError_t launch_one(const AdjointArgs& a0, int block, int num_sms, cud
     if (cap > a.max_blocks) cap = a.max_blocks;  // rows of the partial-sum buffer
     const int grid = (int)(need < cap ? need : cap);
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    kernel<<<grid, block, 0, s>>>(a);
+    kernel<<<grid, block, smem, s>>>(a);
     *rows = R::NP <= 16 ? grid : (int64_t)grid * (block / 32);
     return cudaGetLastError();
 }

@@ -178,14 +178,15 @@ __device__ __forceinline__ void lane_vjp(const f2 (&x)[5], f2 others, const f2 (
     const f2 dm = O::sel(sm, one, sub2(one, em)), dn = O::sel(sn, one, sub2(one, en));
     const f2 rmn = O::rcp(mulp(dm, dn));
     const f2 rm = mulp(dn, rmn), rn = mulp(dm, rmn);  // 1 / dm, 1 / dn
-    // g(y) = y / (1 - e^-y), g'(y) = (1 - e^-y (1 + y)) / (1 - e^-y)^2; alpha_m = g(ym),
-    // alpha_n = g(yn) / 10; at most one of ym, yn lies in the series band
+    // g(y) = y r with r = 1 / (1 - e^-y), and g'(y) = (1 - e^-y - y e^-y) r^2 = r (1 - e^-y g);
+    // alpha_m = g(ym), alpha_n = g(yn) / 10; at most one of ym, yn lies in the series band
     const f2 ys = O::sel(sm, ym, yn);
     const f2 ser = bernoulli_series_t<O>(ys), dser = bernoulli_series_deriv_t<O>(ys);
-    const f2 am = O::sel(sm, ser, mulp(ym, rm));
-    const f2 gn = O::sel(sn, ser, mulp(yn, rn));
-    const f2 dgm = O::sel(sm, dser, mulp(O::fms(em, add2(one, ym), one), mulp(rm, rm)));
-    const f2 dgn = O::sel(sn, dser, mulp(O::fms(en, add2(one, yn), one), mulp(rn, rn)));
+    const f2 gmc = mulp(ym, rm), gnc = mulp(yn, rn);  // the closed forms
+    const f2 am = O::sel(sm, ser, gmc);
+    const f2 gn = O::sel(sn, ser, gnc);
+    const f2 dgm = O::sel(sm, dser, mulp(O::fms(em, gmc, one), rm));
+    const f2 dgn = O::sel(sn, dser, mulp(O::fms(en, gnc, one), rn));
     const f2 anbn = fma2(kp(0.1f), gn, bn);
     const f2 dam = mulp(kp(0.1f), dgm), dan = mulp(kp(0.01f), dgn);
     const f2 ph = fma2(kp(kE3), q8, one), ps = add2(one, es);
@@ -209,9 +210,10 @@ __device__ __forceinline__ void lane_vjp(const f2 (&x)[5], f2 others, const f2 (
     // state
     const f2 vV = v[0];
     const f2 ws = mulp(mulp(v[4], L.c.inv_tr), sub2(one, s));  // v_s (1 - s) / tau_r
-    const f2 gate_m = fma2(dam, sub2(one, m), mulp(nd_bm, m));
-    const f2 gate_h = fma2(dah, sub2(one, h), mulp(nd_bh, h));
-    const f2 gate_n = fma2(dan, sub2(one, n), mulp(nd_bn, n));
+    // a' (1 - y) - b' y = a' + y (-b' - a')
+    const f2 gate_m = fma2(m, sub2(nd_bm, dam), dam);
+    const f2 gate_h = fma2(h, sub2(nd_bh, dah), dah);
+    const f2 gate_n = fma2(n, sub2(nd_bn, dan), dan);
     const f2 a1ws = mulp(a1, ws);
     const f2 jv = fma2(v[1], gate_m, fma2(v[2], gate_h, fma2(v[3], gate_n, mulp(L.sig, a1ws))));
     jx[0] = O::fms(vV, gtot, jv);

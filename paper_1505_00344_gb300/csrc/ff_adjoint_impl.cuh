@@ -446,13 +446,13 @@ __device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i
                 // the sub-segment's states in the thread's shared-memory column (state r,
                 // component k at sts[(r * D + k) * bs]): the step loops stay rolled, so the
                 // kernel keeps one copy of each step in the instruction cache
-#pragma unroll 1
+#pragma unroll 2
                 for (int r = 0; r < nq; ++r) {
 #pragma unroll
                     for (int k = 0; k < D; ++k) sts[(r * D + k) * bs] = x[k];
                     if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
                 }
-#pragma unroll 1
+#pragma unroll 2
                 for (int r = nq - 1; r >= 0; --r) {
                     float xr[D];
 #pragma unroll
@@ -846,9 +846,10 @@ __global__ void __launch_bounds__(kLx2Block, 8) adjoint_lorenz_x2s_kernel(const 
             for (int base = 0; base < L; base += MS, ++nsub) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) cpt[nsub][k] = x[k];
-                const int nq = (base + MS < L) ? MS : 0;
-#pragma unroll 1
-                for (int r = 0; r < nq; ++r) lorenz_fwd2(x, cp2);
+                if (base + MS < L) {
+#pragma unroll
+                    for (int r = 0; r < MS; ++r) lorenz_fwd2(x, cp2);
+                }
             }
             f2 jp[3] = {pack2(0.f, 0.f), pack2(0.f, 0.f), pack2(0.f, 0.f)};
             for (int sq = nsub - 1; sq >= 0; --sq) {

@@ -370,8 +370,13 @@ ff_status ff_tape_end(ff_system* sys);
  * sum over particles of the derivatives with respect to their own values.
  * The recomputation runs plain FP32 steps from the checkpoints; the
  * per-particle parameter sums are FP64 and reduced in a fixed order.
+ * Memory: for the 15-dimensional system the first call allocates a scratch
+ * area for one recomputed chunk per resident thread, (resident threads) x
+ * checkpoint_every x 40 floats for RK4 (10 for Euler): about 0.9 GB at
+ * checkpoint_every = 100 on a 152-SM GPU; it is kept with the tape and
+ * released by ff_tape_end.  The other systems' sweeps need none.
  * Synchronises.  Errors: FF_ERR_STATE without a tape or after it ended,
- * FF_ERR_INVALID_ARG for NULL buffers, FF_ERR_CUDA. */
+ * FF_ERR_INVALID_ARG for NULL buffers, FF_ERR_OOM, FF_ERR_CUDA. */
 ff_status ff_backward(ff_system* sys, const float* dL_dxT_dev, float* dL_dx0_dev, double* dL_dp_host);
 
 /* Batched stepping (not part of the paper): several systems -- each with its
@@ -409,7 +414,9 @@ ff_status ff_backward(ff_system* sys, const float* dL_dxT_dev, float* dL_dx0_dev
  * chunk ends (every checkpoint_every steps, or where its parameters or dt
  * changed); the first launch of a chunk stores the member's checkpoint from the
  * state it loads.  ff_batch_backward then runs one reverse-sweep launch per
- * family over tiles of 128 particles of one member, with the arithmetic of
+ * family over tiles of 128 particles of one member (80 for the 15-dimensional
+ * system, whose family keeps one scratch area as ff_backward's, sized for its
+ * longest chunk and released by ff_batch_destroy), with the arithmetic of
  * ff_backward (dL/dx0 bit-identical to it), and reduces each member's
  * parameter gradient over its tiles in a fixed order:
  *   dL_dxT_dev[i], dL_dx0_dev[i]: device SoA [dim_i][P_i] buffers of member i

@@ -11,7 +11,7 @@ attractor-density statistics instead of trajectories):
   after the full 100 frames x 200 steps, the forward group's coarse density
   matches the oracle's (total variation <= 0.05 and <= 3x the distance between
   two independent oracle samples), every backward particle has escaped, and the
-  escape flags of the backward group after 1000 steps agree on >= 99% of
+  escape flags of the backward group after 1000 steps agree on >= 99.9% of
   sampled particles.  The compensated (Kahan) integrator's error against FP64
   is stated at 100 and 1000 steps (median not above the plain one) and, after
   the decorrelation of the chaotic trajectories, at 20,000 steps as the same
@@ -174,7 +174,10 @@ def test_lorenz_4M_full_job_statistics(capsys):
             st = state(s)
             idx = n_fwd + np.arange(0, w["groups"][1]["count"], 256)
             want, _ = oracle_sample(w, idx, 1000)
-            assert (escaped(st[:, idx]) == escaped(want)).mean() >= 0.99
+            agree = float((escaped(st[:, idx]) == escaped(want)).mean())
+            report(capsys, f"[lorenz_4M backward group, step 1000] escape flags agree on {agree:.4%} of "
+                           f"{idx.size} sampled particles ({escaped(want).mean():.1%} escaped in the oracle)")
+            assert agree >= 0.999
     torch.cuda.synchronize()
     n_esc, t_fwd, t_bwd = s.stats()
     assert n_esc == w["groups"][1]["count"]  # every backward particle escaped, no forward one

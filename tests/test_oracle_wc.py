@@ -5,7 +5,9 @@ special values (S(threshold) = 1/2, the symmetry S(th+d) + S(th-d) = 1, slope
 gain/4 at the threshold, saturation to 0 and 1).  Each coupling weight is pinned
 by its sign and by the population it enters.  With all weights zero the system is
 linear with a constant drive, and RK4 is then exactly
-E_n = S* + (E_0 - S*) T(-h/tau)^n with T the RK4 stability polynomial.
+E_n = S* + (E_0 - S*) T(-h/tau)^n with T the RK4 stability polynomial.  At the
+workload's parameters the one equilibrium (Newton on Eq. 1-2) is a stable focus, and
+the oracle's trajectories from the unit square spiral into it at its eigenvalues' rate.
 """
 import math
 
@@ -102,3 +104,57 @@ def test_unit_square_forward_invariant_backward_leaves():
     bwd = oracle.integrate(oracle.WILSON_COWAN, x0, p, -0.01, 1000)
     outside = (bwd < 0.0).any(axis=0) | (bwd > 1.0).any(axis=0)
     assert outside.mean() > 0.9
+
+
+def test_config_fixed_point_is_the_attractor():
+    # The workload's parameters (wEE=16, wEI=12, wIE=15, wII=3, P=1.25, Q=0, tau=1, gain 1,
+    # threshold 4).  Its equilibria are the zeros of Eq. 1-2, found here by Newton's method on
+    # the equations as the paper states them (not through the oracle), from a grid of starts in
+    # the unit square: there is exactly one, and the trace and determinant of its Jacobian make
+    # it a stable focus.  The oracle's forward trajectories from the whole square must then
+    # spiral into it, their distance shrinking at the rate of the eigenvalues' real part.
+    p = [16.0, 12.0, 15.0, 3.0, 1.25, 0.0, 1.0, 1.0, 1.0, 4.0]
+    wEE, wEI, wIE, wII, P, Q = p[:6]
+
+    def S(a):
+        return 1.0 / (1.0 + math.exp(-(a - 4.0)))
+
+    def F(x):
+        E, I = x
+        return np.array([-E + S(wEE * E - wEI * I + P), -I + S(wIE * E - wII * I + Q)])
+
+    def J(x):
+        E, I = x
+        sE = S(wEE * E - wEI * I + P)
+        sI = S(wIE * E - wII * I + Q)
+        dE, dI = sE * (1.0 - sE), sI * (1.0 - sI)
+        return np.array([[-1.0 + dE * wEE, -dE * wEI], [dI * wIE, -1.0 - dI * wII]])
+
+    roots = []
+    for E0 in np.linspace(0.0, 1.0, 11):
+        for I0 in np.linspace(0.0, 1.0, 11):
+            x = np.array([E0, I0])
+            for _ in range(60):
+                dx = np.linalg.solve(J(x), -F(x))
+                x = x + dx
+                if np.abs(dx).max() < 1e-14:
+                    break
+            if np.abs(F(x)).max() < 1e-13 and not any(np.abs(x - r).max() < 1e-9 for r in roots):
+                roots.append(x)
+    assert len(roots) == 1
+    xs = roots[0]
+    M = J(xs)
+    tr, det = np.trace(M), np.linalg.det(M)
+    assert tr < 0 and det > 0 and tr * tr < 4 * det  # stable focus
+    re = tr / 2.0  # real part of both eigenvalues
+
+    x0 = oracle.seed_group(2, [0, 0], [1, 1], 17, count=256).astype(np.float64)
+    x1 = oracle.integrate(oracle.WILSON_COWAN, x0, p, 0.01, 3000)  # t = 30
+    x2 = oracle.integrate(oracle.WILSON_COWAN, x1, p, 0.01, 3000)  # t = 60
+    d1 = np.abs(x1 - xs[:, None]).max()
+    d2 = np.abs(x2 - xs[:, None]).max()
+    assert d2 < 2e-3
+    # near the focus the distance shrinks by exp(re * 30) per 30 time units (the rotation
+    # makes the max-norm ratio wander by a bounded factor)
+    ratio = d2 / d1
+    assert 0.5 * math.exp(re * 30.0) < ratio < 2.0 * math.exp(re * 30.0), (ratio, math.exp(re * 30.0))

@@ -559,9 +559,12 @@ def cpu_baseline(w):
     steps = w["steps_per_frame"]
     particles = int(min(4_194_304, max(threads * 4096, 15.0 * rate1 / steps)))
     work, t, used = oracle_sample_run(w, particles, steps, threads=threads)
+    job = total_particles(w) * w["frames"] * w["steps_per_frame"]  # particle-steps of the whole job
     return {"value": work / t, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": f"{particles} particles of {w['name']} (groups in proportion) x {steps} RK4 steps "
-                      f"+ x-z splat, FP64 oracle, {used} threads on disjoint particle ranges"}
+                      f"+ x-z splat, FP64 oracle, {used} threads on disjoint particle ranges",
+            "per_core": rate1, "per_core_sample": "4096 particles x 200 RK4 steps + splat, one thread",
+            "full_job_s": job / (work / t)}
 
 
 def run_reference(args, rank, world):

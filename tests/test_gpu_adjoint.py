@@ -146,6 +146,24 @@ def test_hh3_adjoint_per_particle_parameter(pidx, lo, hi, method):
     check(dp, dp_ref)
 
 
+def test_hh3_adjoint_forward_and_backward_groups_in_one_pair():
+    """HH3 with a backward-time group over a short horizon (0.2 ms from near the resting
+    state; backward HH runs away from most of the box, and from rest within 0.4 ms).
+    201 forward + 56 backward particles: particles 200 and 201 share a lane's f32x2
+    registers with step sizes of opposite sign."""
+    rest = ([-70, 0.02, 0.5, 0.28, 0.0] * 3, [-60, 0.08, 0.65, 0.35, 0.1] * 3)
+    groups = [G(201, *HHB, 1, 64), G(56, *rest, -1, 65)]
+    P, dt, n = 257, 0.01, 20
+    s = build("hh3", HH3_BASE, groups, 15)
+    s.tape_begin(8, n)
+    s.step(n, dt)
+    target = random_states(15, P, HHB[0], HHB[1], seed=8).astype(np.float64)
+    dx0, dp = gpu_grads(s, 15, P, target, 16)
+    _, dx0_ref, dp_ref = oracle.mse_gradients(oracle.HH3, x0_of(groups, 15), HH3_BASE, h_of(groups, dt), n, target)
+    check(dx0, dx0_ref)
+    check(dp, dp_ref)
+
+
 @pytest.mark.parametrize("P", [1, 3, 21])
 def test_hh3_adjoint_small_counts(P):
     """Fewer particles than a warp's 20 (three lanes per particle pair), and one more:

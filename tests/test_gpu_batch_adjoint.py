@@ -114,6 +114,34 @@ def test_batch_backward_matches_members_alone():
     b.close()
 
 
+def test_hh3_members_with_per_particle_parameter_match_alone():
+    # the HH3 family's sweep with a per-particle parameter (g_syn linspace; the two members
+    # differ in their range and sizes, the second not a multiple of the 80-particle tile)
+    spec = [(HH3_BASE, [(150, 1, 21)], (7, 0.0, 1.0)), (HH3_BASE, [(97, 1, 22)], (7, 0.2, 0.6))]
+    batched = [make("hh3", p, g, HHB, pp) for p, g, pp in spec]
+    alone = [make("hh3", p, g, HHB, pp) for p, g, pp in spec]
+    b = ff.Batch(batched, stream=stream())
+    b.tape_begin(25, 60)
+    for s in alone:
+        s.tape_begin(25, 60)
+    b.step(60, [0.01, 0.01])
+    for s in alone:
+        s.step(60, 0.01)
+    gb = [loss_grad(s, targets(s, 40 + i)) for i, s in enumerate(batched)]
+    ga = [loss_grad(s, targets(s, 40 + i)) for i, s in enumerate(alone)]
+    out_b = [torch.empty_like(g) for g in gb]
+    dp_b = b.backward(gb, out_b)
+    for i, (s, g) in enumerate(zip(alone, ga)):
+        torch.testing.assert_close(gb[i], g, rtol=0, atol=0, msg=f"state of member {i}")
+        out = torch.empty_like(g)
+        dp = s.backward(g, out, 16)
+        torch.testing.assert_close(out_b[i], out, rtol=0, atol=0, msg=f"dL/dx0 of member {i}")
+        np.testing.assert_allclose(dp_b[i, :16], dp, rtol=1e-8, atol=1e-11 * np.abs(dp).max(),
+                                   err_msg=f"dL/dp of member {i}")
+    b.tape_end()
+    b.close()
+
+
 def test_parameter_change_between_checkpoints():
     # member 0 (Lorenz, per-particle r) changes beta after 70 steps, off the K = 40 grid:
     # a new chunk for member 0 only, while the others' chunks run on

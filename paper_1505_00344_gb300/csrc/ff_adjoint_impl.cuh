@@ -1017,21 +1017,4 @@ static cudaError_t launch_lorenz_x2_one(const AdjointArgs& a, int num_sms, cudaS
     return launch_lorenz_x2_kernel(adjoint_lorenz_x2_kernel<PP, M>, a, num_sms, s, rows);
 }
 
-static cudaError_t launch_lorenz_x2(bool pp, int m, const AdjointArgs& a, int num_sms, cudaStream_t s,
-                                    int64_t* rows) {
-    // chunks of up to 16 steps are one sub-segment (one recomputation); longer ones take the
-    // sweep with 4-step sub-segments that keep their stage points
-    if (a.max_chunk > 16) {
-        if (a.max_chunk > kLx2sSub * kLx2sMaxSub) return cudaErrorInvalidValue;
-        return pp ? launch_lorenz_x2_kernel(adjoint_lorenz_x2s_kernel<true>, a, num_sms, s, rows)
-                  : launch_lorenz_x2_kernel(adjoint_lorenz_x2s_kernel<false>, a, num_sms, s, rows);
-    }
-    switch (m) {
-    case 4: return pp ? launch_lorenz_x2_one<true, 4>(a, num_sms, s, rows) : launch_lorenz_x2_one<false, 4>(a, num_sms, s, rows);
-    case 8: return pp ? launch_lorenz_x2_one<true, 8>(a, num_sms, s, rows) : launch_lorenz_x2_one<false, 8>(a, num_sms, s, rows);
-    case 16: return pp ? launch_lorenz_x2_one<true, 16>(a, num_sms, s, rows) : launch_lorenz_x2_one<false, 16>(a, num_sms, s, rows);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
 }  // namespace ff

@@ -391,19 +391,25 @@ __device__ __forceinline__ void adj_step(const float (&x)[R::DIM], float (&lam)[
     for (int i = 0; i < D; ++i) lam[i] = __fadd_rn(lam[i], __fadd_rn(sum[i], m[i]));
 }
 
-// Whether a sweep keeps the sub-segment's M states in shared memory (one column per
-// thread, M * D floats: at most 32 KB for a block of 128) rather than in a register
-// array, which needs the step loops unrolled M times.
-template <class R, int M> struct StatesInShared { static constexpr bool value = M * R::DIM <= 64; };
+// Shared memory of a sweep's block: the sub-segment's M states of every thread (one column
+// per thread, M * D floats; up to 64 KB for 128 threads of the 8-dimensional system).
+template <class R, int M>
+constexpr size_t sweep_smem(int block) { return sizeof(float) * M * R::DIM * (size_t)block; }
+
+// Lets a kernel take more than the default 48 KB of dynamic shared memory where it needs to.
+template <class Kernel>
+static cudaError_t allow_smem(Kernel kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 // Reverse sweep of one particle i over all chunks: lambda from lam_in to
 // lam_out, parameter contributions added to gacc (FP64, per chunk).  For systems
 // of up to 8 dimensions (the 15-dimensional one has a sweep of its own).
 template <class R, int METHOD, bool PP, int M>
 __device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i, double (&gacc)[R::NP],
-                                                 float* sts = nullptr, int bs = 0) {
+                                                 float* sts, int bs) {
     constexpr int D = R::DIM, NP = R::NP;
-    constexpr bool SM = StatesInShared<R, M>::value;
     int g = 0;
 #pragma unroll
     for (int q = 1; q < FF_MAX_GROUPS; ++q)
@@ -442,36 +448,22 @@ __device__ __forceinline__ void adjoint_particle(const AdjointArgs& a, int64_t i
             const int nq = min(M, L - sq * M);
 #pragma unroll
             for (int k = 0; k < D; ++k) x[k] = cp[sq][k];
-            if constexpr (SM) {
-                // the sub-segment's states in the thread's shared-memory column (state r,
-                // component k at sts[(r * D + k) * bs]): the step loops stay rolled, so the
-                // kernel keeps one copy of each step in the instruction cache
+            // the sub-segment's states in the thread's shared-memory column (state r,
+            // component k at sts[(r * D + k) * bs]): the step loops stay rolled, so the
+            // kernel keeps one copy of each step in the instruction cache (a register array
+            // would need them unrolled M times)
 #pragma unroll 2
-                for (int r = 0; r < nq; ++r) {
+            for (int r = 0; r < nq; ++r) {
 #pragma unroll
-                    for (int k = 0; k < D; ++k) sts[(r * D + k) * bs] = x[k];
-                    if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
-                }
+                for (int k = 0; k < D; ++k) sts[(r * D + k) * bs] = x[k];
+                if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
+            }
 #pragma unroll 2
-                for (int r = nq - 1; r >= 0; --r) {
-                    float xr[D];
+            for (int r = nq - 1; r >= 0; --r) {
+                float xr[D];
 #pragma unroll
-                    for (int k = 0; k < D; ++k) xr[k] = sts[(r * D + k) * bs];
-                    adj_step<R, METHOD>(xr, lam, h, p, jp);
-                }
-            } else {
-                float st[M][D];
-#pragma unroll
-                for (int r = 0; r < M; ++r) {
-                    if (r < nq) {
-#pragma unroll
-                        for (int k = 0; k < D; ++k) st[r][k] = x[k];
-                        if (r + 1 < nq) fwd_step<R, METHOD>(x, h, p);
-                    }
-                }
-#pragma unroll
-                for (int r = M - 1; r >= 0; --r)
-                    if (r < nq) adj_step<R, METHOD>(st[r], lam, h, p, jp);
+                for (int k = 0; k < D; ++k) xr[k] = sts[(r * D + k) * bs];
+                adj_step<R, METHOD>(xr, lam, h, p, jp);
             }
         }
 #pragma unroll
@@ -507,7 +499,7 @@ template <class R, int METHOD, bool PP, int M>
 __global__ void __launch_bounds__(256) adjoint_kernel(const __grid_constant__ AdjointArgs a) {
     constexpr int NP = R::NP;
     __shared__ double red[8][NP > 16 ? 1 : NP];  // per-warp partials (blocks of at most 256 threads)
-    extern __shared__ float sts[];               // StatesInShared: M * D floats per thread
+    extern __shared__ float sts[];               // sweep_smem: M * D floats per thread
     double gacc[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) gacc[q] = 0.0;
@@ -907,7 +899,7 @@ template <class R, int METHOD, bool PP, int M>
 __global__ void __launch_bounds__(kAdjTile) batch_adjoint_kernel(const __grid_constant__ BatchAdjointArgs b) {
     constexpr int NP = R::NP;
     __shared__ double red[kAdjTile / 32][NP];
-    __shared__ float sts[StatesInShared<R, M>::value ? M * R::DIM * kAdjTile : 1];
+    extern __shared__ float sts[];  // sweep_smem: M * D floats per thread
     for (int tile = blockIdx.x; tile < b.n_tiles; tile += gridDim.x) {
         const AdjTile T = b.tiles[tile];
         const AdjointArgs& a = b.sys[T.sys];
@@ -923,14 +915,17 @@ __global__ void __launch_bounds__(kAdjTile) batch_adjoint_kernel(const __grid_co
 template <class R, int METHOD, bool PP, int M>
 static cudaError_t launch_batch_one(const BatchAdjointArgs& b, int num_sms, cudaStream_t s) {
     auto kernel = batch_adjoint_kernel<R, METHOD, PP, M>;
+    const size_t smem = sweep_smem<R, M>(kAdjTile);
+    cudaError_t e = allow_smem(kernel, smem);
+    if (e != cudaSuccess) return e;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kAdjTile, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kAdjTile, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int64_t cap = (int64_t)occ * num_sms;
     const int grid = (int)((int64_t)b.n_tiles < cap ? b.n_tiles : cap);
     if (grid < 1) return cudaSuccess;
-    kernel<<<grid, kAdjTile, 0, s>>>(b);
+    kernel<<<grid, kAdjTile, smem, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -955,9 +950,11 @@ template <class R, int METHOD, bool PP, int M>
 static cudaError_t launch_one(const AdjointArgs& a0, int block, int num_sms, cudaStream_t s, int64_t* rows) {
     AdjointArgs a = a0;
     auto kernel = adjoint_kernel<R, METHOD, PP, M>;
-    const size_t smem = StatesInShared<R, M>::value ? sizeof(float) * M * R::DIM * block : 0;
+    const size_t smem = sweep_smem<R, M>(block);
+    cudaError_t e = allow_smem(kernel, smem);
+    if (e != cudaSuccess) return e;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int64_t need = (a.n + block - 1) / block;

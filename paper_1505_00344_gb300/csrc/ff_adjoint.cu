@@ -5,8 +5,8 @@
 // One thread per particle walks the chunks in reverse with the adjoint state
 // lambda = dL/dx in registers.  A chunk of L <= M*M steps is recomputed from its
 // checkpoint twice (once when L <= M): once to place sub-checkpoints every M steps (local memory),
-// then per sub-segment (in reverse) to put its <= M states in registers (shared
-// memory for the packed Lorenz sweep), which the reverse RK4 steps consume from
+// then per sub-segment (in reverse) to put its <= M states in a shared-memory
+// column per thread, which the reverse RK4 steps consume from
 // last to first.  The 15-dimensional system is recomputed once per chunk into a
 // per-thread scratch area in global memory instead (ff_adjoint_hh3.cu).  Parameter gradients are
 // summed per particle in FP32 within a chunk, added to FP64 per chunk, and

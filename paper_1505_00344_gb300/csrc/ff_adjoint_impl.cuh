@@ -7,8 +7,9 @@
 // lambda = dL/dx in registers.  A chunk of L <= M*M steps is recomputed from its
 // checkpoint twice (once when L <= M): once to place sub-checkpoints every M
 // steps (local memory), then per sub-segment (in reverse) to put its <= M
-// states in registers (shared memory in the packed Lorenz sweep), which the
-// reverse RK4 steps consume from last to first.  Parameter gradients are summed
+// states in a shared-memory column per thread (the packed Lorenz sweep for
+// chunks over 16 steps keeps its stage points there too), which the reverse
+// RK4 steps consume from last to first.  Parameter gradients are summed
 // per particle in FP32 within a chunk, added to FP64 per chunk, and reduced
 // over particles through per-block FP64 partials in fixed order.  The
 // 15-dimensional system runs a sweep of its own (ff_adjoint_hh3.cu: three lanes
